@@ -1,0 +1,96 @@
+"""Physical systems u_t + f(u)_x [+ g(u)_y] + B(w) grad w = 0 with a static
+coefficient field c (test infrastructure only).
+
+Sec. 3, Eq. flux.and.non.cons; Sec. 5.1.3 (variable-coefficient advection cast
+with B depending on the coefficient, "B(u, x)"); Sec. 5, Eq. time.step.2d for
+the 2D form.  The state is w = (u, c) where u holds the M evolved variables
+and c the static coefficient (a(x) for advection, the bathymetry b(x) for
+shallow water).  ``ncprod(u, c, du, dc)`` returns the M evolved rows of the
+matrix-vector product B(w) (du, dc); the row of c is zero because c is static.
+
+Array convention: the variable index is the leading axis of ``u``/``du``;
+``c``/``dc`` have no variable axis.
+"""
+import numpy as np
+
+
+class VarCoeffAdvection:
+    """v_t + a(x) v_x = 0 (Sec. 5.1.3, Eq. var.coeff.adv): u = (v), c = a,
+    f = 0, B(w)(du, dc) = a du, spectral radius of f' + B is |a|."""
+    M = 1
+    name = "varadv"
+
+    def flux(self, u, c):
+        return np.zeros_like(u)
+
+    def ncprod(self, u, c, du, dc):
+        return c[None] * du
+
+    def speed(self, u, c):
+        return np.abs(c) * np.ones_like(u[0])
+
+
+class ShallowWater1D:
+    """Shallow water with bathymetry as a non-conservative product:
+    h_t + m_x = 0,  m_t + (m^2/h + g h^2/2)_x + g h b_x = 0.
+    u = (h, m), c = b, f = (m, m^2/h + g h^2/2), B(w)(du, db) = (0, g h db).
+    Eigenvalues of f' + B on (h, m, b): v - sqrt(g h), 0, v + sqrt(g h)
+    with v = m / h, so the spectral radius is |v| + sqrt(g h)."""
+    M = 2
+    name = "swe1d"
+
+    def __init__(self, g=9.81):
+        self.g = g
+
+    def flux(self, u, c):
+        h, m = u[0], u[1]
+        return np.stack([m, m * m / h + 0.5 * self.g * h * h])
+
+    def ncprod(self, u, c, du, dc):
+        h = u[0]
+        return np.stack([np.zeros_like(h * dc), self.g * h * dc])
+
+    def speed(self, u, c):
+        h, m = u[0], u[1]
+        return np.abs(m / h) + np.sqrt(self.g * h)
+
+
+class ShallowWater2D:
+    """2D shallow water with bathymetry: u = (h, hu, hv), c = b,
+    f = (hu, (hu)^2/h + g h^2/2, (hu)(hv)/h),
+    g = (hv, (hu)(hv)/h, (hv)^2/h + g h^2/2),
+    B1(w)(du, db) = (0, g h db, 0), B2(w)(du, db) = (0, 0, g h db).
+    Spectral radii: |u| + sqrt(g h) in x, |v| + sqrt(g h) in y."""
+    M = 3
+    name = "swe2d"
+
+    def __init__(self, g=9.81):
+        self.g = g
+
+    def flux_x(self, u, c):
+        h, mx, my = u[0], u[1], u[2]
+        p = 0.5 * self.g * h * h
+        return np.stack([mx, mx * mx / h + p, mx * my / h])
+
+    def flux_y(self, u, c):
+        h, mx, my = u[0], u[1], u[2]
+        p = 0.5 * self.g * h * h
+        return np.stack([my, mx * my / h, my * my / h + p])
+
+    def ncprod_x(self, u, c, du, dc):
+        h = u[0]
+        z = np.zeros_like(h * dc)
+        return np.stack([z, self.g * h * dc, z])
+
+    def ncprod_y(self, u, c, du, dc):
+        h = u[0]
+        z = np.zeros_like(h * dc)
+        return np.stack([z, z, self.g * h * dc])
+
+    def speed_x(self, u, c):
+        h, mx = u[0], u[1]
+        return np.abs(mx / h) + np.sqrt(self.g * h)
+
+    def speed_y(self, u, c):
+        h, my = u[0], u[2]
+        return np.abs(my / h) + np.sqrt(self.g * h)
