@@ -1,0 +1,410 @@
+"""Benchmark of the cRK-FR hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload swe2d|swe1d]
+
+A step is one cRK-FR time step (element-local inner stages, time averages,
+face Riemann problems with non-conservative fluctuations, FR corrections,
+update, and the device-side time step of Eq. time.step.2d for the next step)
+over the whole mesh.  Default workload: 2D shallow water with bathymetry on a
+periodic 1024 x 1024 quad mesh, N = 3 (16 nodes, 3 variables per element),
+32 seeded Gaussians of bathymetry, a seeded Gaussian bump on the free
+surface, zero velocity, FP64, CFL 0.5 of the von Neumann limit.
+
+Prints one JSON line.  `value` is DoF-updates/s with the state resident in
+HBM (state + work buffers are about 3 GB, far larger than the 129 MB L2, so
+no L2 flush is needed between steps); `e2e` repeats the measurement through
+the C ABI's host-buffer entry point with the host<->device copies inside the
+timed region.  `--impl reference` times the CPU oracle instead (the only
+reference this method has), on a bounded periodic patch of the same
+workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cRK-FR DoF-updates/s per step (FP64), % HBM roofline; adjoint/forward cost"
+G = 9.81
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA lanes per
+# SM per cycle x 2 flop x 2070 MHz (the lane count is what an FMA-chain probe
+# measures: 1.19 TFLOP/s = 1.9 FMA/clk/SM).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+class Workload:
+    def __init__(self, name):
+        self.name = name
+        if name == "swe2d":
+            self.system, self.N, self.E, self.L = "swe2d", 3, (1024, 1024), 100.0
+            self.M, self.dim = 3, 2
+        elif name == "swe1d":
+            self.system, self.N, self.E, self.L = "swe1d", 4, (100000,), 100.0
+            self.M, self.dim = 2, 1
+        else:
+            raise ValueError(name)
+        n = self.N + 1
+        self.n = n
+        self.elements = int(np.prod(self.E))
+        self.nodes_per_elem = n ** self.dim
+        self.dof = self.elements * self.nodes_per_elem * self.M
+        # minimal HBM traffic per step: read u and the bathymetry, write u
+        self.min_bytes = self.elements * self.nodes_per_elem * (2 * self.M + 1) * 8
+
+    def label(self):
+        e = "x".join(str(v) for v in self.E)
+        return f"{self.system}-{e}-N{self.N}"
+
+    def inputs(self, positions, seed=0):
+        from paper_2512_08611_gb300.workloads import SWE1DInput, SWE2DInput, accept_seed
+        if self.dim == 2:
+            inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=self.L), positions, seed)
+        else:
+            inp, _ = accept_seed(lambda s: SWE1DInput(seed=s, L=self.L), positions, seed)
+        return inp.state(*positions)
+
+    def local_flops_per_element(self):
+        """FP64 flops (FMA = 2) of the element-local kernel per element, from
+        the operation count of its formulation."""
+        from paper_2512_08611_gb300.flops import local_flops_per_element
+        return local_flops_per_element(self.system, self.N)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# profiles/ summary of the dominant kernel: dram traffic, valid only while the
+# kernel source is unchanged
+# ---------------------------------------------------------------------------
+def kernel_source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2512_08611_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(summary, files, scale):
+    """dram bytes per launch from a profiles/ summary, scaled to the bench
+    launch, or None if absent or taken on another version of the sources."""
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(files):
+        return None
+    return float(m_bytes.group(1)) * scale
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing on a bounded periodic patch of the workload
+# ---------------------------------------------------------------------------
+def oracle_patch(wl, side):
+    from oracle.basis import Basis
+    from oracle.crkfr import Scheme1D, Scheme2D
+    from oracle.systems import ShallowWater1D, ShallowWater2D
+    bs = Basis(wl.N)
+    if wl.dim == 2:
+        dx = wl.L / wl.E[0]
+        x = (np.arange(side)[None, :, None, None] + bs.xi[None, None, None, :]) * dx
+        y = (np.arange(side)[:, None, None, None] + bs.xi[None, None, :, None]) * dx
+        x, y = np.broadcast_arrays(x, y)
+        u, b = wl.inputs((x, y))
+        sch = Scheme2D(ShallowWater2D(G), wl.N, dx, dx)
+        dof = side * side * wl.nodes_per_elem * wl.M
+    else:
+        dx = wl.L / wl.E[0]
+        x = (np.arange(side)[:, None] + bs.xi[None, :]) * dx
+        u, b = wl.inputs((x,))
+        sch = Scheme1D(ShallowWater1D(G), wl.N, dx)
+        dof = side * wl.nodes_per_elem * wl.M
+    return sch, u, b, dof
+
+
+def time_oracle(wl, budget_s, max_steps):
+    """Oracle steps on a periodic patch cut from the workload (same per-element
+    work), sized so that max_steps steps take about budget_s seconds."""
+    import oracle.fourier  # noqa: F401  (imports numpy-only modules)
+    probe = 32 if wl.dim == 2 else 4096
+    sch, u, b, dof = oracle_patch(wl, probe)
+    t0 = time.perf_counter()
+    sch.step(u, b, 1e-4)
+    per_dof = (time.perf_counter() - t0) / dof
+    target = budget_s / max(max_steps, 1) / per_dof
+    if wl.dim == 2:
+        side = int(np.clip(np.sqrt(target / (wl.nodes_per_elem * wl.M)) // 8 * 8, 16, wl.E[0]))
+    else:
+        side = int(np.clip(target / (wl.nodes_per_elem * wl.M) // 128 * 128, 512, wl.E[0]))
+    sch, u, b, dof = oracle_patch(wl, side)
+    return sch, u, b, dof, side
+
+
+def cpu_threads():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    return 1
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, wl):
+    cpu_threads()
+    budget = 90.0
+    sch, u, b, dof, side = time_oracle(wl, budget, args.steps + args.warmup)
+    cfl = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")))["cfl"][f"{wl.N}_gl"]
+    v = u
+    for _ in range(args.warmup):
+        v = sch.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v = sch.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
+    el = time.perf_counter() - t0
+    value = dof * args.steps / el
+    patch = f"{side}x{side}" if wl.dim == 2 else f"{side}"
+    sample = (f"oracle step on a periodic {patch}-element patch cut from the "
+              f"{wl.label()} workload (same per-element work), {args.steps} steps")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DoF-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.label(), "sample": patch, "dof_per_step": dof},
+        "cpu_baseline": {"value": value, "unit": "DoF-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "DoF-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2512_08611_gb300.build import build_library
+    build_library()
+    from paper_2512_08611_gb300 import crkfr
+
+    s = crkfr.Solver(wl.system, wl.N, gravity=G, cfl_safety=0.5)
+    s.set_mesh(list(wl.E), [0.0] * wl.dim, [wl.L] * wl.dim)
+    pos = s.positions()
+    u0, b = wl.inputs(pos if wl.dim == 2 else (pos,))
+    u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    s.set_coefficients(torch.tensor(b, dtype=torch.float64, device="cuda"))
+    u_init = u.clone()
+
+    # warm-up
+    s.step(u, 0.0, args.warmup)
+    torch.cuda.synchronize()
+    s.status()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.profile(True)
+    n0 = s.launch_count()
+    ev0.record(stream)
+    s.step(u, 0.0, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = s.launch_count() - n0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    clk = clocks.stop()
+    s.status()
+    t_sim, dt_last = s.time()
+
+    el = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(el, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(el.item())
+    value = wl.dof * args.steps * world / (elapsed_ms / 1e3)
+    ms_per_step = elapsed_ms / args.steps
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    host = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
+    host.copy_(u_init.cpu())
+    h = host.numpy()
+    e2e_steps = max(3, min(args.steps, 20))
+    s.step_host(h, h, dt=0.0, nsteps=1)   # warm the host path (allocates its device copy)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.step_host(h, h, dt=0.0, nsteps=1)
+    e2e_s = time.perf_counter() - t0
+    state_bytes = wl.dof * 8
+
+    # roofline of the dominant kernel
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    if wl.dim == 2:
+        kname, files, summary = "local_2d", ["kernels_2d.cu", "device_common.cuh", "tableau.h"], \
+            "k_local_2d__swe2d_N3.md"
+    else:
+        kname, files, summary = "step_1d", ["kernels_1d.cu", "device_common.cuh", "tableau.h"], \
+            "k_step_1d__swe1d_N4.md"
+    nk, ms_k = prof.get(kname, (0, float("nan")))
+    avg_ms = ms_k / max(nk, 1)
+    flops = wl.local_flops_per_element() * wl.elements
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    traffic = profiled_traffic(summary, files, 1.0)
+    shares = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-30), 4) for k, v in prof.items()}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.label(), "elements": wl.elements,
+                   "nodes_per_element": wl.nodes_per_elem, "vars": wl.M, "dof": wl.dof,
+                   "cfl_safety": 0.5, "cfl": s.cfl(), "dt_last": dt_last, "t_sim": t_sim,
+                   "l2": "no flush: state + work buffers ~3 GB >> 129 MB L2",
+                   "parallelism": "single GPU" if world == 1 else f"{world} independent replicas"},
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": traffic, "avg_launch_ms": avg_ms,
+                     "flops_per_launch": flops,
+                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"},
+        "hbm": {"min_bytes_per_step": wl.min_bytes,
+                "achieved_gbs": wl.min_bytes / (ms_per_step / 1e3) / 1e9,
+                "peak_gbs": hbm_peak,
+                "frac": wl.min_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+        "kernel_shares": shares,
+        "e2e": {"value": wl.dof * e2e_steps / e2e_s, "unit": "DoF-updates/s",
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1:
+        cpu_threads()
+        sch, uu, bb, dof, side = time_oracle(wl, 15.0, 2)
+        cfl = s.cfl()
+        t0 = time.perf_counter()
+        nst = 2
+        v = uu
+        for _ in range(nst):
+            v = sch.step(v, bb, sch.compute_dt(v, bb, cfl, 0.5))
+        el_cpu = time.perf_counter() - t0
+        patch = f"{side}x{side}" if wl.dim == 2 else f"{side}"
+        out["cpu_baseline"] = {
+            "value": dof * nst / el_cpu, "unit": "DoF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{nst} oracle steps on a periodic {patch}-element patch cut from the "
+                      f"{wl.label()} workload (same per-element work), numpy FP64 single thread"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="swe2d", choices=["swe2d", "swe1d"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = Workload(args.workload)
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

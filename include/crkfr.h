@@ -1,0 +1,195 @@
+/*
+ * crkfr.h - C ABI of the GB300 (sm_103a) compact Runge-Kutta flux
+ * reconstruction library for non-conservative hyperbolic systems
+ * (Babbar & Ranocha, "Admissibility preserving compact Runge-Kutta flux
+ * reconstruction for non-conservative hyperbolic equations with stiff
+ * source terms", arXiv 2512.08611).
+ *
+ * One time step of the method (Sec. 3, Eqs. crkfr.non.cons.final,
+ * total.F.non.cons, local.time.avg.non.cons, good.numflux.non.cons) for
+ *
+ *     u_t + f(u)_x [+ g(u)_y] + B(w) grad w = 0,   w = (u, c),
+ *
+ * where c is a static coefficient field (a(x) for variable-coefficient
+ * advection, Sec. 5.1.3; the bathymetry b for shallow water).  The inner
+ * Runge-Kutta stages use only the element-local derivative; only the final
+ * stage couples neighbours through one time-averaged numerical flux per face,
+ * the non-conservative fluctuation B(w^{n,+-}) (W^num - W^{+-}) and the FR
+ * correction-function derivatives (App. B, Eq. correction.identities).
+ *
+ * Conventions
+ * -----------
+ * - Arithmetic is IEEE FP64 throughout.
+ * - Meshes are uniform and periodic: dim 1 with E elements on [lo, hi], or
+ *   dim 2 with Ex x Ey quads on [lo0, hi0] x [lo1, hi1].
+ * - Nodal layout (row-major, contiguous, FP64):
+ *     1D: u[var][elem][p]            c[elem][p]
+ *     2D: u[var][ey][ex][q][p]       c[ey][ex][q][p]
+ *   p is the x node index, q the y node index, 0..N, at the solution points
+ *   returned by crkfr_get_nodes (position of node p of element e:
+ *   lo + (e + xi_p) * dx).
+ * - Variables: advection (v); 1D shallow water (h, hu); 2D shallow water
+ *   (h, hu, hv).  Degree N is 0..4 (1D) or 1..4 (2D).
+ * - Pointers named *_dev are device pointers on the current CUDA device;
+ *   *_host are host pointers.  The caller owns every pointer it passes; the
+ *   library never frees them and keeps none of them past the call.
+ *   Buffers the method needs between kernels (face traces, a second state,
+ *   the static coefficient terms, a device status word) are owned by the
+ *   context and sized at crkfr_set_mesh.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *   asynchronous on that stream unless they return a host value, in which
+ *   case they synchronise that stream only.
+ * - Errors: every entry point returns a crkfr_status; nothing traps or
+ *   throws across the ABI.  crkfr_last_error gives the context's last error
+ *   text.  A context is not thread-safe; use one context per host thread.
+ */
+#ifndef CRKFR_H
+#define CRKFR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crkfr_ctx crkfr_ctx;
+
+typedef enum {
+  CRKFR_OK = 0,
+  CRKFR_ERR_ARG = -1,          /* invalid argument or size                     */
+  CRKFR_ERR_UNSUPPORTED = -2,  /* system / degree / node family not built      */
+  CRKFR_ERR_CUDA = -3,         /* a CUDA runtime call failed                    */
+  CRKFR_ERR_NONPHYSICAL = -4,  /* h <= 0 or a non-finite value was produced    */
+  CRKFR_ERR_STATE = -6,        /* call out of order (e.g. no mesh set yet)      */
+  CRKFR_ERR_ALLOC = -7         /* device or host allocation failed             */
+} crkfr_status;
+
+typedef enum {
+  CRKFR_SYS_VARADV_1D = 0,     /* v_t + a(x) v_x = 0, c = a (Sec. 5.1.3)        */
+  CRKFR_SYS_SWE_1D = 1,        /* shallow water, c = b, B(w)(du,db) = (0, g h db) */
+  CRKFR_SYS_SWE_2D = 2         /* 2D shallow water, B1 = (0,g h db,0), B2 = (0,0,g h db) */
+} crkfr_system;
+
+typedef enum {
+  CRKFR_NODES_GL = 0,          /* Gauss-Legendre points, Radau correction (Sec. 2) */
+  CRKFR_NODES_GLL = 1          /* Gauss-Lobatto-Legendre points, g_2 correction   */
+} crkfr_nodes;
+
+typedef struct {
+  int32_t system;      /* crkfr_system                                               */
+  int32_t degree;      /* polynomial degree N                                        */
+  int32_t nodes;       /* crkfr_nodes                                                */
+  int32_t reserved;    /* must be 0                                                  */
+  double gravity;      /* g for shallow water; ignored for advection                */
+  double cfl_safety;   /* C_s of Sec. 5, Eq. time.step.2d; 0 < C_s <= 1             */
+  double cfl_number;   /* CFL(N) of Eq. time.step.2d; <= 0 selects the library's own
+                          von Neumann value (crkfr_get_cfl)                          */
+} crkfr_config;
+
+/* Create a context for one system / degree / node family.  Runs the
+ * library's von Neumann analysis of the scheme for linear advection when
+ * cfg->cfl_number <= 0 (Sec. 5, under Eq. time.step.2d).  *out is set to NULL
+ * on failure. */
+crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg);
+
+/* Free the context and every device buffer it owns (synchronises the device). */
+void crkfr_destroy(crkfr_ctx* ctx);
+
+/* Uniform periodic mesh (Sec. 2, Eqs. reference.element, ref.map).
+ * dim must match the system (1 or 2); n_elem[dim] > 0 (Ex first, then Ey);
+ * lo[dim] < hi[dim].  Allocates the context's device buffers (about
+ * 6x the state size in 1D, 5x in 2D).  Invalidates the coefficients. */
+crkfr_status crkfr_set_mesh(crkfr_ctx* ctx, int32_t dim, const int64_t* n_elem,
+                            const double* lo, const double* hi);
+
+/* Number of FP64 values of the state u (vars x nodes) and of the coefficient
+ * field c, for the mesh that is set. */
+crkfr_status crkfr_sizes(const crkfr_ctx* ctx, int64_t* n_state, int64_t* n_coef);
+
+/* Solution points xi_p in [0, 1] and quadrature weights w_p (N+1 values each,
+ * host arrays) of the context's node family (Sec. 2, Eq. soln.points). */
+crkfr_status crkfr_get_nodes(const crkfr_ctx* ctx, double* xi_host, double* w_host);
+
+/* CFL(N) the context uses (given or computed). */
+crkfr_status crkfr_get_cfl(const crkfr_ctx* ctx, double* cfl_host);
+
+/* Static coefficient field c at the solution points (device, layout above):
+ * a(x) for advection, the bathymetry b for shallow water.  The library
+ * derives and stores what the scheme needs from it (the local
+ * non-conservative factor B(c) dloc c per node and the face traces of c). */
+crkfr_status crkfr_set_coefficients(crkfr_ctx* ctx, const double* c_dev, void* stream);
+
+/* Time step of Sec. 5, Eq. time.step.2d for the state u_dev:
+ * C_s CFL(N) / max_e (sigma(f' + B_1)(ubar_e)/dx + sigma(g' + B_2)(ubar_e)/dy)
+ * with element means ubar_e = sum_p w_p u_ep.  Synchronises the stream. */
+crkfr_status crkfr_compute_dt(crkfr_ctx* ctx, const double* u_dev, double* dt_host,
+                              void* stream);
+
+/* Time-averaged residual of one cRK-FR step of size dt > 0:
+ * r = (u^{n+1} - u^n) / dt, evaluated directly (not by differencing) as
+ * -(dloc F + Bloc + face corrections) of Eq. crkfr.non.cons.final.
+ * u_dev and r_dev must not overlap. */
+crkfr_status crkfr_residual(crkfr_ctx* ctx, const double* u_dev, double dt, double* r_dev,
+                            void* stream);
+
+/* Advance u_dev in place by nsteps >= 0 cRK-FR steps.  dt > 0: that fixed
+ * step; dt <= 0: the step of Eq. time.step.2d recomputed on the device from
+ * the current state before every step (no host synchronisation).  The
+ * context accumulates simulated time on the device (crkfr_get_time). */
+crkfr_status crkfr_step(crkfr_ctx* ctx, double* u_dev, double dt, int64_t nsteps,
+                        void* stream);
+
+/* Advance with the step of Eq. time.step.2d until time t_end, shortening the
+ * last step to land on t_end exactly (steps after that are no-ops).  Runs
+ * chunks of device steps and reads the time back between chunks.  At most
+ * max_steps steps; *steps_taken (may be NULL) receives the number of steps
+ * that advanced the state.  Returns CRKFR_ERR_ARG if t_end is not reached
+ * within max_steps. */
+crkfr_status crkfr_advance(crkfr_ctx* ctx, double* u_dev, double t_end, int64_t max_steps,
+                           int64_t* steps_taken, void* stream);
+
+/* Same as crkfr_step on host memory: copies u_in_host to a context-owned
+ * device state, steps, and copies the result to u_out_host (the two may be
+ * the same buffer).  Synchronises the stream. */
+crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_out_host,
+                             double dt, int64_t nsteps, void* stream);
+
+/* Simulated time and the size of the last step taken (synchronises). */
+crkfr_status crkfr_get_time(crkfr_ctx* ctx, double* t_host, double* last_dt_host, void* stream);
+
+/* Reset the simulated time to t (asynchronous). */
+crkfr_status crkfr_set_time(crkfr_ctx* ctx, double t, void* stream);
+
+/* Read and clear the device status word: CRKFR_OK, or CRKFR_ERR_NONPHYSICAL
+ * if any step since the last call produced h <= 0 or a non-finite value
+ * (shallow water) or a non-finite value (advection).  Synchronises. */
+crkfr_status crkfr_get_status(crkfr_ctx* ctx, void* stream);
+
+/* Number of kernel launches the context has issued (for accounting). */
+int64_t crkfr_launch_count(const crkfr_ctx* ctx);
+
+/* Kernel timing.  While enabled, the context records a CUDA event pair on
+ * the launch stream around every kernel it launches; crkfr_profile_read
+ * synchronises on the recorded events and returns, for one kernel kind, the
+ * launches and summed device time (ms) since profiling was enabled.
+ * Enabling (again) clears the accumulated values. */
+typedef enum {
+  CRKFR_KERNEL_STEP_1D = 0,    /* fused 1D step                              */
+  CRKFR_KERNEL_LOCAL_2D = 1,   /* 2D element-local stages and face traces    */
+  CRKFR_KERNEL_FACE_2D = 2,    /* 2D face Riemann problems, corrections, update */
+  CRKFR_KERNEL_RATE = 3,       /* wave-speed rate of a state (time step)     */
+  CRKFR_KERNEL_COEF = 4,       /* static coefficient terms                   */
+  CRKFR_KERNEL_KINDS = 5
+} crkfr_kernel_kind;
+crkfr_status crkfr_profile_enable(crkfr_ctx* ctx, int32_t enable);
+crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms);
+
+/* Static strings. */
+const char* crkfr_error_string(crkfr_status status);
+const char* crkfr_last_error(const crkfr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRKFR_H */

@@ -1,0 +1,258 @@
+"""Thin ctypes binding of libcrkfr (include/crkfr.h).
+
+Only argument marshalling lives here: every step of the method runs in the
+library's CUDA kernels.  Device memory and streams come from PyTorch: state
+and coefficient arrays are contiguous float64 CUDA tensors in the library's
+nodal layout, and calls go to ``torch.cuda.current_stream()``.
+
+The functions of the C ABI are reachable under their own names through
+``lib()``; ``Solver`` wraps one context.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import library_path
+
+CRKFR_OK = 0
+STATUS = {0: "CRKFR_OK", -1: "CRKFR_ERR_ARG", -2: "CRKFR_ERR_UNSUPPORTED", -3: "CRKFR_ERR_CUDA",
+          -4: "CRKFR_ERR_NONPHYSICAL", -6: "CRKFR_ERR_STATE", -7: "CRKFR_ERR_ALLOC"}
+SYSTEMS = {"varadv1d": 0, "swe1d": 1, "swe2d": 2}
+NODES = {"gl": 0, "gll": 1}
+NVARS = {"varadv1d": 1, "swe1d": 2, "swe2d": 3}
+DIM = {"varadv1d": 1, "swe1d": 1, "swe2d": 2}
+
+
+class CrkfrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("system", ctypes.c_int32), ("degree", ctypes.c_int32),
+                ("nodes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gravity", ctypes.c_double), ("cfl_safety", ctypes.c_double),
+                ("cfl_number", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes); mirrors include/crkfr.h
+SIGNATURES = {
+    "crkfr_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(Config)]),
+    "crkfr_destroy": (None, [_P]),
+    "crkfr_set_mesh": (_I32, [_P, _I32, _PI64, _PD, _PD]),
+    "crkfr_sizes": (_I32, [_P, _PI64, _PI64]),
+    "crkfr_get_nodes": (_I32, [_P, _PD, _PD]),
+    "crkfr_get_cfl": (_I32, [_P, _PD]),
+    "crkfr_set_coefficients": (_I32, [_P, _P, _P]),
+    "crkfr_compute_dt": (_I32, [_P, _P, _PD, _P]),
+    "crkfr_residual": (_I32, [_P, _P, _D, _P, _P]),
+    "crkfr_step": (_I32, [_P, _P, _D, _I64, _P]),
+    "crkfr_advance": (_I32, [_P, _P, _D, _I64, _PI64, _P]),
+    "crkfr_step_host": (_I32, [_P, _P, _P, _D, _I64, _P]),
+    "crkfr_get_time": (_I32, [_P, _PD, _PD, _P]),
+    "crkfr_set_time": (_I32, [_P, _D, _P]),
+    "crkfr_get_status": (_I32, [_P, _P]),
+    "crkfr_launch_count": (_I64, [_P]),
+    "crkfr_profile_enable": (_I32, [_P, _I32]),
+    "crkfr_profile_read": (_I32, [_P, _I32, _PI64, _PD]),
+    "crkfr_error_string": (ctypes.c_char_p, [_I32]),
+    "crkfr_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_LIB = None
+
+
+def lib():
+    """The loaded library (loaded on first use; raises if it was not built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_2512_08611_gb300.build`")
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = handle
+    return _LIB
+
+
+def _stream():
+    import torch
+    if not torch.cuda.is_available():
+        return ctypes.c_void_p(0)   # calls that reach CUDA report the error themselves
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """One library context: a system, degree and node family on one mesh.
+
+    ``system``: 'varadv1d', 'swe1d' or 'swe2d'; ``nodes``: 'gl' (Radau
+    correction) or 'gll' (g_2 correction).  ``cfl_number`` <= 0 takes the
+    library's own von Neumann CFL(N)."""
+
+    def __init__(self, system, degree, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0):
+        self.system, self.degree, self.family = system, degree, nodes
+        self.M = NVARS[system]
+        self.dim = DIM[system]
+        self.n = degree + 1
+        cfg = Config(SYSTEMS[system], degree, NODES[nodes], 0, gravity, cfl_safety, cfl_number)
+        h = ctypes.c_void_p()
+        self._check(lib().crkfr_create(ctypes.byref(h), ctypes.byref(cfg)), None)
+        self.h = h
+        self.shape = None
+
+    def _check(self, status, h="self"):
+        if status != CRKFR_OK:
+            handle = self.h if h == "self" else h
+            msg = lib().crkfr_last_error(handle).decode() if handle else \
+                lib().crkfr_error_string(status).decode()
+            raise CrkfrError(status, msg or lib().crkfr_error_string(status).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().crkfr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up ----------------------------------------------------------------
+    def set_mesh(self, n_elem, lo, hi):
+        n_elem = [int(v) for v in np.atleast_1d(n_elem)]
+        lo = [float(v) for v in np.atleast_1d(lo)]
+        hi = [float(v) for v in np.atleast_1d(hi)]
+        d = len(n_elem)
+        arr = (ctypes.c_int64 * d)(*n_elem)
+        self._check(lib().crkfr_set_mesh(self.h, d, arr, (ctypes.c_double * d)(*lo),
+                                         (ctypes.c_double * d)(*hi)))
+        self.n_elem, self.lo, self.hi = n_elem, lo, hi
+        n = self.n
+        if self.dim == 1:
+            self.shape = (self.M, n_elem[0], n)
+            self.coef_shape = (n_elem[0], n)
+        else:
+            self.shape = (self.M, n_elem[1], n_elem[0], n, n)
+            self.coef_shape = (n_elem[1], n_elem[0], n, n)
+        return self
+
+    def nodes(self):
+        n = self.n
+        xi, w = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        self._check(lib().crkfr_get_nodes(self.h, xi, w))
+        return np.array(xi[:]), np.array(w[:])
+
+    def cfl(self):
+        v = ctypes.c_double()
+        self._check(lib().crkfr_get_cfl(self.h, ctypes.byref(v)))
+        return v.value
+
+    def positions(self):
+        """Coordinates of the solution points in the library's layout:
+        1D x[elem, p]; 2D (x, y) each [ey, ex, q, p]."""
+        xi, _ = self.nodes()
+        if self.dim == 1:
+            dx = (self.hi[0] - self.lo[0]) / self.n_elem[0]
+            return self.lo[0] + (np.arange(self.n_elem[0])[:, None] + xi[None, :]) * dx
+        Ex, Ey = self.n_elem
+        dx = (self.hi[0] - self.lo[0]) / Ex
+        dy = (self.hi[1] - self.lo[1]) / Ey
+        x = self.lo[0] + (np.arange(Ex)[None, :, None, None] + xi[None, None, None, :]) * dx
+        y = self.lo[1] + (np.arange(Ey)[:, None, None, None] + xi[None, None, :, None]) * dy
+        return np.broadcast_arrays(x, y)
+
+    def _dev(self, t, shape):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError("expected a CUDA tensor")
+        if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+            raise ValueError(f"expected contiguous float64 of shape {shape}, got "
+                             f"{t.dtype} {tuple(t.shape)}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def set_coefficients(self, c):
+        self._check(lib().crkfr_set_coefficients(self.h, self._dev(c, self.coef_shape), _stream()))
+
+    # -- compute -----------------------------------------------------------------
+    def compute_dt(self, u):
+        v = ctypes.c_double()
+        self._check(lib().crkfr_compute_dt(self.h, self._dev(u, self.shape), ctypes.byref(v),
+                                           _stream()))
+        return v.value
+
+    def residual(self, u, dt, out=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(u)
+        self._check(lib().crkfr_residual(self.h, self._dev(u, self.shape), float(dt),
+                                         self._dev(out, self.shape), _stream()))
+        return out
+
+    def step(self, u, dt=0.0, nsteps=1):
+        self._check(lib().crkfr_step(self.h, self._dev(u, self.shape), float(dt), int(nsteps),
+                                     _stream()))
+        return u
+
+    def advance(self, u, t_end, max_steps=10 ** 7):
+        k = ctypes.c_int64()
+        self._check(lib().crkfr_advance(self.h, self._dev(u, self.shape), float(t_end),
+                                        int(max_steps), ctypes.byref(k), _stream()))
+        return k.value
+
+    def step_host(self, u_in, u_out=None, dt=0.0, nsteps=1):
+        """Steps a host (numpy float64, C-contiguous) state; the copies to and
+        from the device happen inside the library call."""
+        if u_in.dtype != np.float64 or not u_in.flags["C_CONTIGUOUS"] or u_in.shape != self.shape:
+            raise ValueError("expected C-contiguous float64 host array of the state shape")
+        if u_out is None:
+            u_out = np.empty_like(u_in)
+        self._check(lib().crkfr_step_host(self.h, u_in.ctypes.data_as(ctypes.c_void_p),
+                                          u_out.ctypes.data_as(ctypes.c_void_p), float(dt),
+                                          int(nsteps), _stream()))
+        return u_out
+
+    def time(self):
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().crkfr_get_time(self.h, ctypes.byref(t), ctypes.byref(dt), _stream()))
+        return t.value, dt.value
+
+    def set_time(self, t):
+        self._check(lib().crkfr_set_time(self.h, float(t), _stream()))
+
+    def status(self):
+        """Raises CrkfrError(CRKFR_ERR_NONPHYSICAL) if a non-physical state was
+        produced since the last call."""
+        self._check(lib().crkfr_get_status(self.h, _stream()))
+
+    def launch_count(self):
+        return lib().crkfr_launch_count(self.h)
+
+    KERNELS = {"step_1d": 0, "local_2d": 1, "face_2d": 2, "rate": 3, "coef": 4}
+
+    def profile(self, enable=True):
+        """Start (clearing earlier values) or stop per-kernel event timing."""
+        self._check(lib().crkfr_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel: (launches, total ms)} since profiling was enabled."""
+        out = {}
+        for name, k in self.KERNELS.items():
+            n, ms = ctypes.c_int64(), ctypes.c_double()
+            self._check(lib().crkfr_profile_read(self.h, k, ctypes.byref(n), ctypes.byref(ms)))
+            if n.value:
+                out[name] = (n.value, ms.value)
+        return out

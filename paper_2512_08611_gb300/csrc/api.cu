@@ -1,0 +1,618 @@
+// C ABI of libcrkfr (declared in include/crkfr.h): context, mesh, static
+// coefficient terms, time-step control and the stepping entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "crkfr.h"
+#include "crkfr_internal.h"
+
+using namespace crkfr;
+
+struct crkfr_ctx {
+  crkfr_config cfg{};
+  HostBasis basis;
+  Tables tab{};
+  double cfl = 0.0;
+  int M = 1;
+  int dim = 0;
+  int64_t Ex = 0, Ey = 1;
+  double lo[2] = {0, 0}, hi[2] = {1, 1};
+  int64_t n_state = 0, n_coef = 0;
+  double* d_snode = nullptr;
+  double* d_sface = nullptr;
+  double* d_work = nullptr;
+  double* d_trx = nullptr;
+  double* d_try = nullptr;
+  double* d_stage = nullptr;  // device copy of host state for crkfr_step_host
+  DevState* d_state = nullptr;
+  bool coef_set = false;
+  int64_t nstep = 0;
+  int64_t launches = 0;
+  int device = -1;
+  std::string err;
+  // kernel timing (crkfr_profile_*)
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t prof_n[CRKFR_KERNEL_KINDS] = {};
+  double prof_ms[CRKFR_KERNEL_KINDS] = {};
+};
+
+namespace {
+
+crkfr_status fail(crkfr_ctx* c, crkfr_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+crkfr_status cuda_fail(crkfr_ctx* c, int e, const char* where) {
+  return fail(c, CRKFR_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString((cudaError_t)e));
+}
+
+#define CK(ctx, call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+void free_buffers(crkfr_ctx* c) {
+  cudaFree(c->d_snode);
+  cudaFree(c->d_sface);
+  cudaFree(c->d_work);
+  cudaFree(c->d_trx);
+  cudaFree(c->d_try);
+  cudaFree(c->d_stage);
+  cudaFree(c->d_state);
+  c->d_snode = c->d_sface = c->d_work = c->d_trx = c->d_try = c->d_stage = nullptr;
+  c->d_state = nullptr;
+}
+
+crkfr_status check_device(crkfr_ctx* c) {
+  int d = -1;
+  CK(c, cudaGetDevice(&d));
+  if (d != c->device) return fail(c, CRKFR_ERR_STATE, "current device differs from the mesh's device");
+  return CRKFR_OK;
+}
+
+cudaEvent_t take_event(crkfr_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Runs `launch` (returns a cudaError_t as int); with profiling on, brackets
+// it with an event pair on the launch stream.
+template <class F>
+int timed(crkfr_ctx* c, int kind, cudaStream_t s, F launch) {
+  if (!c->prof) return launch();
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (!a || !b) return launch();
+  cudaEventRecord(a, s);
+  const int e = launch();
+  cudaEventRecord(b, s);
+  c->pending.push_back({kind, a, b});
+  return e;
+}
+
+// Synchronises on the pending event pairs and accumulates their durations.
+crkfr_status drain_profile(crkfr_ctx* c, bool keep) {
+  crkfr_status st = CRKFR_OK;
+  for (auto& r : c->pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) {
+      st = cuda_fail(c, e, "profile events");
+    } else if (keep) {
+      c->prof_n[r.kind] += 1;
+      c->prof_ms[r.kind] += ms;
+    }
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->pending.clear();
+  return st;
+}
+
+__global__ void k_set_time(DevState* st, int slot, double t) {
+  st->time[slot] = t;
+  st->time[slot ^ 1] = t;
+}
+
+Launch1D make1d(crkfr_ctx* c) {
+  Launch1D L{};
+  L.system = c->cfg.system;
+  L.N = c->cfg.degree;
+  L.gll = c->cfg.nodes == CRKFR_NODES_GLL;
+  L.E = c->Ex;
+  L.snode = c->d_snode;
+  L.sface = c->d_sface;
+  L.st = c->d_state;
+  L.tab = c->tab;
+  return L;
+}
+
+Launch2D make2d(crkfr_ctx* c) {
+  Launch2D L{};
+  L.N = c->cfg.degree;
+  L.gll = c->cfg.nodes == CRKFR_NODES_GLL;
+  L.Ex = c->Ex;
+  L.Ey = c->Ey;
+  L.w = c->d_work;
+  L.trx = c->d_trx;
+  L.try_ = c->d_try;
+  L.snode = c->d_snode;
+  L.sface = c->d_sface;
+  L.st = c->d_state;
+  L.tab = c->tab;
+  return L;
+}
+
+crkfr_status ready(crkfr_ctx* c) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
+  if (!c->coef_set) return fail(c, CRKFR_ERR_STATE, "no coefficients set");
+  return check_device(c);
+}
+
+// rate of state u (max over elements of the wave-speed rate) into `slot`
+crkfr_status launch_rate(crkfr_ctx* c, const double* u, int slot, cudaStream_t s) {
+  CK(c, cudaMemsetAsync(&c->d_state->rate[slot], 0, sizeof(unsigned long long), s));
+  int e;
+  if (c->dim == 1) {
+    Launch1D L = make1d(c);
+    L.u_in = u;
+    e = timed(c, CRKFR_KERNEL_RATE, s, [&] { return launch_rate_1d(L, slot, s); });
+  } else {
+    Launch2D L = make2d(c);
+    L.u_in = u;
+    e = timed(c, CRKFR_KERNEL_RATE, s, [&] { return launch_rate_2d(L, slot, s); });
+  }
+  if (e) return cuda_fail(c, e, "rate kernel");
+  c->launches += 1;
+  return CRKFR_OK;
+}
+
+// nsteps steps of u in place.  dt > 0 fixed, otherwise CFL (clipped to t_end).
+crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, double t_end,
+                       cudaStream_t s) {
+  if (nsteps <= 0) return CRKFR_OK;
+  const bool cfl_mode = !(dt > 0.0);
+  if (cfl_mode) {
+    CK(c, cudaMemsetAsync(c->d_state->rate, 0, sizeof(c->d_state->rate), s));
+    crkfr_status st = launch_rate(c, u, (int)(c->nstep % 3), s);
+    if (st != CRKFR_OK) return st;
+  }
+  StepCtl ctl{};
+  ctl.dt_fixed = cfl_mode ? 0.0 : dt;
+  ctl.cs_cfl = c->cfg.cfl_safety * c->cfl;
+  ctl.t_end = t_end;
+  ctl.want_rate = cfl_mode ? 1 : 0;
+  ctl.residual = 0;
+  if (c->dim == 1) {
+    // ping-pong between u and the work buffer, ending in u
+    double* bufs[2] = {u, c->d_work};
+    int cur = 0;
+    if (nsteps % 2 == 1) {
+      CK(c, cudaMemcpyAsync(c->d_work, u, sizeof(double) * c->n_state, cudaMemcpyDeviceToDevice, s));
+      cur = 1;
+    }
+    Launch1D L = make1d(c);
+    for (int64_t k = 0; k < nsteps; ++k) {
+      ctl.slot_read = (int)(c->nstep % 3);
+      ctl.slot_write = (int)((c->nstep + 1) % 3);
+      ctl.slot_reset = (int)((c->nstep + 2) % 3);
+      ctl.tslot = (int)(c->nstep % 2);
+      L.ctl = ctl;
+      L.u_in = bufs[cur];
+      L.u_out = bufs[cur ^ 1];
+      int e = timed(c, CRKFR_KERNEL_STEP_1D, s, [&] { return launch_step_1d(L, s); });
+      if (e) return cuda_fail(c, e, "1D step kernel");
+      c->launches += 1;
+      c->nstep += 1;
+      cur ^= 1;
+    }
+  } else {
+    Launch2D L = make2d(c);
+    for (int64_t k = 0; k < nsteps; ++k) {
+      ctl.slot_read = (int)(c->nstep % 3);
+      ctl.slot_write = (int)((c->nstep + 1) % 3);
+      ctl.slot_reset = (int)((c->nstep + 2) % 3);
+      ctl.tslot = (int)(c->nstep % 2);
+      L.ctl = ctl;
+      L.u_in = u;
+      L.u_out = u;
+      int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
+      if (!e) e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+      if (e) return cuda_fail(c, e, "2D step kernels");
+      c->launches += 2;
+      c->nstep += 1;
+    }
+  }
+  return CRKFR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* crkfr_error_string(crkfr_status s) {
+  switch (s) {
+    case CRKFR_OK: return "ok";
+    case CRKFR_ERR_ARG: return "invalid argument";
+    case CRKFR_ERR_UNSUPPORTED: return "unsupported system, degree or node family";
+    case CRKFR_ERR_CUDA: return "CUDA runtime error";
+    case CRKFR_ERR_NONPHYSICAL: return "non-physical state (h <= 0 or non-finite value)";
+    case CRKFR_ERR_STATE: return "call out of order";
+    case CRKFR_ERR_ALLOC: return "allocation failed";
+  }
+  return "unknown status";
+}
+
+const char* crkfr_last_error(const crkfr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t crkfr_launch_count(const crkfr_ctx* c) { return c ? c->launches : 0; }
+
+crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg) {
+  if (!out) return CRKFR_ERR_ARG;
+  *out = nullptr;
+  if (!cfg) return CRKFR_ERR_ARG;
+  if (cfg->reserved != 0) return CRKFR_ERR_ARG;
+  if (cfg->system < CRKFR_SYS_VARADV_1D || cfg->system > CRKFR_SYS_SWE_2D)
+    return CRKFR_ERR_UNSUPPORTED;
+  if (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL) return CRKFR_ERR_UNSUPPORTED;
+  const int minN = (cfg->system == CRKFR_SYS_SWE_2D || cfg->nodes == CRKFR_NODES_GLL) ? 1 : 0;
+  if (cfg->degree < minN || cfg->degree > kMaxN) return CRKFR_ERR_UNSUPPORTED;
+  if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
+  if (cfg->system != CRKFR_SYS_VARADV_1D && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
+  crkfr_ctx* c = new (std::nothrow) crkfr_ctx();
+  if (!c) return CRKFR_ERR_ALLOC;
+  c->cfg = *cfg;
+  c->M = cfg->system == CRKFR_SYS_VARADV_1D ? 1 : cfg->system == CRKFR_SYS_SWE_1D ? 2 : 3;
+  if (!build_basis(cfg->degree, cfg->nodes == CRKFR_NODES_GLL, &c->basis)) {
+    delete c;
+    return CRKFR_ERR_UNSUPPORTED;
+  }
+  c->cfl = cfg->cfl_number > 0.0 ? cfg->cfl_number : von_neumann_cfl(c->basis);
+  *out = c;
+  return CRKFR_OK;
+}
+
+void crkfr_destroy(crkfr_ctx* c) {
+  if (!c) return;
+  if (c->dim != 0) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_buffers(c);
+    for (auto& r : c->pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : c->pool) cudaEventDestroy(e);
+    if (prev != c->device && prev >= 0) cudaSetDevice(prev);
+  }
+  delete c;
+}
+
+crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, const double* lo,
+                            const double* hi) {
+  if (!c || !n_elem || !lo || !hi) return fail(c, CRKFR_ERR_ARG, "null argument");
+  const int want = c->cfg.system == CRKFR_SYS_SWE_2D ? 2 : 1;
+  if (dim != want) return fail(c, CRKFR_ERR_ARG, "dimension does not match the system");
+  for (int d = 0; d < dim; ++d) {
+    if (n_elem[d] <= 0) return fail(c, CRKFR_ERR_ARG, "element count must be positive");
+    if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
+      return fail(c, CRKFR_ERR_ARG, "need lo < hi, finite");
+  }
+  const int n = c->basis.n;
+  const int64_t Ex = n_elem[0], Ey = dim == 2 ? n_elem[1] : 1;
+  const int64_t Ne = Ex * Ey;
+  if (Ne > (int64_t)1 << 31 || Ne * n * n * c->M > ((int64_t)1 << 40))
+    return fail(c, CRKFR_ERR_ARG, "mesh too large");
+  if (c->dim != 0) {
+    cudaDeviceSynchronize();
+    free_buffers(c);
+  }
+  c->dim = 0;
+  c->coef_set = false;
+  CK(c, cudaGetDevice(&c->device));
+  const int64_t nodes = dim == 2 ? Ne * n * n : Ne * n;
+  c->Ex = Ex;
+  c->Ey = Ey;
+  c->n_state = nodes * c->M;
+  c->n_coef = nodes;
+  for (int d = 0; d < 2; ++d) {
+    c->lo[d] = d < dim ? lo[d] : 0.0;
+    c->hi[d] = d < dim ? hi[d] : 1.0;
+  }
+  const double dx = (c->hi[0] - c->lo[0]) / (double)Ex;
+  const double dy = (c->hi[1] - c->lo[1]) / (double)Ey;
+  Tables& T = c->tab;
+  std::memset(&T, 0, sizeof(T));
+  const HostBasis& b = c->basis;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      T.Dx[i][j] = b.D[i][j] / dx;
+      T.Dy[i][j] = b.D[i][j] / dy;
+    }
+    T.l0[i] = b.l0[i];
+    T.l1[i] = b.l1[i];
+    T.gRx[i] = 0.5 * b.gR[i] / dx;
+    T.gLx[i] = 0.5 * b.gL[i] / dx;
+    T.gRy[i] = 0.5 * b.gR[i] / dy;
+    T.gLy[i] = 0.5 * b.gL[i] / dy;
+    T.w[i] = b.w[i];
+  }
+  T.inv_dx = 1.0 / dx;
+  T.inv_dy = dim == 2 ? 1.0 / dy : 0.0;
+  T.gravity = c->cfg.system == CRKFR_SYS_VARADV_1D ? 0.0 : c->cfg.gravity;
+  T.half_gravity = 0.5 * T.gravity;
+
+  size_t sn, sf;
+  if (dim == 1) {
+    sn = (size_t)Ne * n;
+    sf = (size_t)Ne * 2;
+  } else {
+    sn = (size_t)2 * Ne * n * n;
+    sf = (size_t)2 * Ne * n;
+  }
+  if (cudaMalloc(&c->d_snode, sizeof(double) * sn) != cudaSuccess ||
+      cudaMalloc(&c->d_sface, sizeof(double) * sf) != cudaSuccess ||
+      cudaMalloc(&c->d_work, sizeof(double) * c->n_state) != cudaSuccess ||
+      cudaMalloc(&c->d_state, sizeof(DevState)) != cudaSuccess) {
+    free_buffers(c);
+    cudaGetLastError();
+    return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+  }
+  if (dim == 2) {
+    const size_t tr = (size_t)7 * 2 * Ne * n;
+    if (cudaMalloc(&c->d_trx, sizeof(double) * tr) != cudaSuccess ||
+        cudaMalloc(&c->d_try, sizeof(double) * tr) != cudaSuccess) {
+      free_buffers(c);
+      cudaGetLastError();
+      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+    }
+  }
+  CK(c, cudaMemset(c->d_state, 0, sizeof(DevState)));
+  c->nstep = 0;
+  c->dim = dim;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_sizes(const crkfr_ctx* c, int64_t* n_state, int64_t* n_coef) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim == 0) return CRKFR_ERR_STATE;
+  if (n_state) *n_state = c->n_state;
+  if (n_coef) *n_coef = c->n_coef;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_get_nodes(const crkfr_ctx* c, double* xi, double* w) {
+  if (!c || !xi || !w) return CRKFR_ERR_ARG;
+  for (int i = 0; i < c->basis.n; ++i) {
+    xi[i] = c->basis.xi[i];
+    w[i] = c->basis.w[i];
+  }
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_get_cfl(const crkfr_ctx* c, double* cfl) {
+  if (!c || !cfl) return CRKFR_ERR_ARG;
+  *cfl = c->cfl;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_set_coefficients(crkfr_ctx* c, const double* coef, void* stream) {
+  if (!c || !coef) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
+  crkfr_status st = check_device(c);
+  if (st != CRKFR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int e;
+  e = timed(c, CRKFR_KERNEL_COEF, s, [&] {
+    if (c->dim == 1)
+      return launch_coef_1d(c->cfg.system, c->cfg.degree, c->Ex, coef, c->d_snode, c->d_sface,
+                            c->tab, s);
+    return launch_coef_2d(c->cfg.degree, c->cfg.nodes == CRKFR_NODES_GLL, c->Ex, c->Ey, coef,
+                          c->d_snode, c->d_sface, c->tab, s);
+  });
+  if (e) return cuda_fail(c, e, "coefficient kernel");
+  c->launches += 1;
+  c->coef_set = true;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_compute_dt(crkfr_ctx* c, const double* u, double* dt_host, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (!u || !dt_host) return fail(c, CRKFR_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  // slot 0 is free between calls: every stepping call re-initialises its slots
+  st = launch_rate(c, u, 0, s);
+  if (st != CRKFR_OK) return st;
+  unsigned long long bits = 0;
+  CK(c, cudaMemcpyAsync(&bits, &c->d_state->rate[0], sizeof(bits), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  double rate;
+  std::memcpy(&rate, &bits, sizeof(rate));
+  if (!(rate > 0.0) || !std::isfinite(rate)) {
+    *dt_host = 0.0;
+    return fail(c, CRKFR_ERR_NONPHYSICAL, "wave-speed rate is not positive and finite");
+  }
+  *dt_host = (c->cfg.cfl_safety * c->cfl) / rate;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_residual(crkfr_ctx* c, const double* u, double dt, double* r, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (!u || !r) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
+  const size_t bytes = sizeof(double) * c->n_state;
+  const char *a = (const char*)u, *b = (const char*)r;
+  if (a < b + bytes && b < a + bytes) return fail(c, CRKFR_ERR_ARG, "u and r overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  StepCtl ctl{};
+  ctl.dt_fixed = dt;
+  ctl.residual = 1;
+  int e;
+  if (c->dim == 1) {
+    Launch1D L = make1d(c);
+    L.ctl = ctl;
+    L.u_in = u;
+    L.u_out = r;
+    e = timed(c, CRKFR_KERNEL_STEP_1D, s, [&] { return launch_step_1d(L, s); });
+    c->launches += 1;
+  } else {
+    Launch2D L = make2d(c);
+    L.ctl = ctl;
+    L.u_in = u;
+    L.u_out = r;
+    e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
+    if (!e) e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+    c->launches += 2;
+  }
+  if (e) return cuda_fail(c, e, "residual kernels");
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_step(crkfr_ctx* c, double* u, double dt, int64_t nsteps, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (nsteps < 0) return fail(c, CRKFR_ERR_ARG, "nsteps must be >= 0");
+  if (!std::isfinite(dt) && dt > 0.0) return fail(c, CRKFR_ERR_ARG, "dt must be finite");
+  return run_steps(c, u, dt, nsteps, std::numeric_limits<double>::infinity(),
+                   (cudaStream_t)stream);
+}
+
+crkfr_status crkfr_advance(crkfr_ctx* c, double* u, double t_end, int64_t max_steps,
+                           int64_t* steps_taken, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (!u || !std::isfinite(t_end) || max_steps < 0) return fail(c, CRKFR_ERR_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t done = 0;
+  double t = 0.0;
+  unsigned long long nadv0 = 0, nadv = 0;
+  const int64_t chunk = 16;
+  for (int first = 1;; first = 0) {
+    DevState h;
+    CK(c, cudaMemcpyAsync(&h, c->d_state, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    t = h.time[c->nstep % 2];
+    nadv = h.nadv;
+    if (first) nadv0 = nadv;
+    if (t >= t_end) break;
+    if (done >= max_steps) break;
+    const int64_t k = (max_steps - done) < chunk ? (max_steps - done) : chunk;
+    st = run_steps(c, u, 0.0, k, t_end, s);
+    if (st != CRKFR_OK) return st;
+    done += k;
+  }
+  if (steps_taken) *steps_taken = (int64_t)(nadv - nadv0);
+  if (t < t_end) return fail(c, CRKFR_ERR_ARG, "t_end not reached within max_steps");
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, double dt,
+                             int64_t nsteps, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (!u_in || !u_out || nsteps < 0) return fail(c, CRKFR_ERR_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * c->n_state;
+  if (!c->d_stage) {
+    if (cudaMalloc(&c->d_stage, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+    }
+  }
+  CK(c, cudaMemcpyAsync(c->d_stage, u_in, bytes, cudaMemcpyHostToDevice, s));
+  st = run_steps(c, c->d_stage, dt, nsteps, std::numeric_limits<double>::infinity(), s);
+  if (st != CRKFR_OK) return st;
+  CK(c, cudaMemcpyAsync(u_out, c->d_stage, bytes, cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_get_time(crkfr_ctx* c, double* t_host, double* last_dt_host, void* stream) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
+  crkfr_status st = check_device(c);
+  if (st != CRKFR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevState h;
+  CK(c, cudaMemcpyAsync(&h, c->d_state, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaStreamSynchronize(s));
+  if (t_host) *t_host = h.time[c->nstep % 2];
+  if (last_dt_host) *last_dt_host = h.dt_last;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_set_time(crkfr_ctx* c, double t, void* stream) {
+  if (!c || !std::isfinite(t)) return CRKFR_ERR_ARG;
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
+  crkfr_status st = check_device(c);
+  if (st != CRKFR_OK) return st;
+  k_set_time<<<1, 1, 0, (cudaStream_t)stream>>>(c->d_state, (int)(c->nstep % 2), t);
+  CK(c, cudaGetLastError());
+  c->launches += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_profile_enable(crkfr_ctx* c, int32_t enable) {
+  if (!c) return CRKFR_ERR_ARG;
+  crkfr_status st = drain_profile(c, false);
+  for (int k = 0; k < CRKFR_KERNEL_KINDS; ++k) {
+    c->prof_n[k] = 0;
+    c->prof_ms[k] = 0.0;
+  }
+  c->prof = enable != 0;
+  return st;
+}
+
+crkfr_status crkfr_profile_read(crkfr_ctx* c, int32_t kind, int64_t* launches, double* total_ms) {
+  if (!c || kind < 0 || kind >= CRKFR_KERNEL_KINDS) return CRKFR_ERR_ARG;
+  crkfr_status st = drain_profile(c, true);
+  if (launches) *launches = c->prof_n[kind];
+  if (total_ms) *total_ms = c->prof_ms[kind];
+  return st;
+}
+
+crkfr_status crkfr_get_status(crkfr_ctx* c, void* stream) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
+  crkfr_status st = check_device(c);
+  if (st != CRKFR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned int flag = 0;
+  CK(c, cudaMemcpyAsync(&flag, &c->d_state->status, sizeof(flag), cudaMemcpyDeviceToHost, s));
+  CK(c, cudaMemsetAsync(&c->d_state->status, 0, sizeof(flag), s));
+  CK(c, cudaStreamSynchronize(s));
+  if (flag) return fail(c, CRKFR_ERR_NONPHYSICAL, "non-physical state produced");
+  return CRKFR_OK;
+}
+
+}  // extern "C"

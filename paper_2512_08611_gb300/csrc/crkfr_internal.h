@@ -1,0 +1,109 @@
+// Internal declarations shared by the host API and the kernels of libcrkfr.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "crkfr.h"
+
+namespace crkfr {
+
+constexpr int kMaxN = 4;
+constexpr int kMaxNodes = kMaxN + 1;
+
+// Reference-element and mesh tables passed to every kernel by value, so they
+// live in the kernel parameter bank (read through the constant cache) and
+// several contexts with different degrees or meshes can coexist.
+struct Tables {
+  double Dx[kMaxNodes][kMaxNodes];  // D / dx   (Eq. diff.matrix, d/dx = (1/dx) d/dxi)
+  double Dy[kMaxNodes][kMaxNodes];  // D / dy
+  double l0[kMaxNodes];             // l_p(0)
+  double l1[kMaxNodes];             // l_p(1)
+  double gRx[kMaxNodes];            // 0.5 g_R'(xi_p) / dx, g_R'(xi_p) = l_p(1)/w_p
+  double gLx[kMaxNodes];            // 0.5 g_L'(xi_p) / dx, g_L'(xi_p) = -l_p(0)/w_p
+  double gRy[kMaxNodes];            // 0.5 g_R'(xi_p) / dy
+  double gLy[kMaxNodes];            // 0.5 g_L'(xi_p) / dy
+  double w[kMaxNodes];              // quadrature weights
+  double inv_dx, inv_dy;
+  double gravity, half_gravity;
+};
+
+// Device-resident stepping state of a context.
+struct DevState {
+  unsigned long long rate[3];  // max_e of the wave-speed rate, IEEE bits of a
+                               // non-negative double (bit order = value order)
+  double time[2];              // simulated time, double buffered
+  double dt_cur;               // step size of the step in flight
+  double dt_last;              // step size of the last completed step
+  unsigned long long nadv;     // number of steps with dt > 0
+  unsigned int status;         // bit 0: non-physical state seen
+  unsigned int pad;
+};
+
+// Per-launch stepping parameters.
+struct StepCtl {
+  double dt_fixed;   // > 0: fixed step; otherwise CFL step from rate[slot_read]
+  double cs_cfl;     // C_s * CFL(N)
+  double t_end;      // CFL mode: clip the step to land on t_end (inf: none)
+  int slot_read;     // rate slot of the current state
+  int slot_write;    // rate slot for the new state
+  int slot_reset;    // rate slot zeroed by this step
+  int tslot;         // time slot read by this step
+  int want_rate;     // compute the rate of the new state
+  int residual;      // 1: write r = (u^{n+1}-u^n)/dt instead of u^{n+1}
+};
+
+struct HostBasis {
+  int N = 0, n = 1;
+  bool gll = false;
+  double xi[kMaxNodes] = {}, w[kMaxNodes] = {};
+  double D[kMaxNodes][kMaxNodes] = {};
+  double l0[kMaxNodes] = {}, l1[kMaxNodes] = {};
+  double gL[kMaxNodes] = {}, gR[kMaxNodes] = {};
+};
+
+// basis.cpp
+bool build_basis(int N, bool gll, HostBasis* out);
+double von_neumann_cfl(const HostBasis& b);
+
+// Launchers (kernels_1d.cu / kernels_2d.cu).  Return cudaError_t as int.
+struct Launch1D {
+  int system;  // crkfr_system
+  int N;
+  bool gll;
+  int64_t E;
+  const double* u_in;
+  double* u_out;
+  const double* snode;   // [E][n]
+  const double* sface;   // [E][2]
+  DevState* st;
+  Tables tab;
+  StepCtl ctl;
+};
+int launch_step_1d(const Launch1D& L, void* stream);
+int launch_rate_1d(const Launch1D& L, int slot, void* stream);
+int launch_coef_1d(int system, int N, int64_t E, const double* c, double* snode, double* sface,
+                   const Tables& tab, void* stream);
+
+struct Launch2D {
+  int N;
+  bool gll;
+  int64_t Ex, Ey;
+  const double* u_in;
+  double* u_out;         // step: may equal u_in
+  double* w;             // [3][Ey][Ex][n][n] scratch
+  double* trx;           // x-face traces [7][2][Ey][Ex][n]
+  double* try_;          // y-face traces [7][2][Ey][Ex][n]
+  const double* snode;   // [2][Ey][Ex][n][n]: g dx b, g dy b
+  const double* sface;   // [2][Ey][Ex][n]: g (b+ - b-) at the left x-face / bottom y-face
+  DevState* st;
+  Tables tab;
+  StepCtl ctl;
+};
+int launch_local_2d(const Launch2D& L, void* stream);
+int launch_face_2d(const Launch2D& L, void* stream);
+int launch_rate_2d(const Launch2D& L, int slot, void* stream);
+int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, double* snode,
+                   double* sface, const Tables& tab, void* stream);
+
+}  // namespace crkfr

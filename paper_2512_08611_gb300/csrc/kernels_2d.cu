@@ -1,0 +1,566 @@
+// 2D shallow-water cRK-FR step on a periodic quad mesh (sm_103a, FP64).
+//
+// The step is two kernels (Sec. 3, Eq. crkfr.non.cons.final, in its
+// tensor-product, line-by-line 2D form):
+//
+//  k_local_2d  element-local part.  n = N+1 threads own one element, one row
+//              (fixed y-node q) each, so x-derivatives are register-resident
+//              FMA chains and y-derivatives read the other rows through
+//              shared memory.  All inner stages stay on chip; the kernel
+//              writes W = u^n - dt (dloc F + Bloc) (Eqs. disc.avg.flux,
+//              local.time.avg.non.cons) and, for every face node, the traces
+//              the Riemann problem needs: the time-averaged solution U, the
+//              time-averaged normal flux and h^n and the normal momentum at
+//              t^n (Eqs. time.avg.soln, combined.wave.speed,
+//              good.numflux.non.cons).
+//  k_face_2d   the only inter-element coupling: per face node the
+//              time-averaged Rusanov flux (Eq. numflux.cons) with the
+//              wave-speed estimate of the full system at u^n, the frozen
+//              non-conservative fluctuation B(w^{n,+-})(W^num - W^{+-}), and
+//              the FR corrections g_L', g_R' (App. B, Eq. correction.identities)
+//              applied along the rows and columns of the element.
+//
+// Two kernels rather than one with halo recomputation: on GB300 FP64
+// arithmetic, not HBM traffic, bounds this path (about 1.2 TFLOP/s against
+// 6.7 TB/s), and recomputing a ring of halo elements would cost 13-56% more
+// FP64 for tiles of 32^2 to 8^2 elements, while the trace round trip costs
+// bandwidth the step does not otherwise use.
+//
+// Face terms are carried doubled, T' = 2 (F^num - F^tot) with the 0.5 folded
+// into the correction tables.  Variables: (h, hu, hv); B_1 acts on the hu
+// equation with g h b_x, B_2 on the hv equation with g h b_y.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace crkfr {
+namespace {
+
+constexpr int kBlock2D = 256;
+constexpr int kWarps2D = kBlock2D / 32;
+constexpr int kTrFields = 7;
+// x-face trace fields: U_h, U_hu, U_hv, F_hu, F_hv (time-averaged x fluxes of
+// hu and hv), h^n, hu^n.  y-face trace fields: U_h, U_hu, U_hv, G_hu, G_hv,
+// h^n, hv^n.  (The time-averaged h fluxes are U_hu and U_hv.)
+
+__device__ __forceinline__ double swe_speed(double h, double m, double g) {
+  return fabs(m * drcp(h)) + sqrt(g * h);
+}
+
+template <int N, bool GLL, bool RES>
+__global__ void __launch_bounds__(kBlock2D) k_local_2d(const Launch2D L) {
+  constexpr int n = N + 1;
+  constexpr int nn = n * n;
+  constexpr int EPW = 32 / n;          // elements per warp
+  constexpr int S = tab_stages(N);
+  constexpr int NB = 4;                // fields per shared-memory exchange round
+  const Tables& T = L.tab;
+  __shared__ double sm[kWarps2D][EPW][NB][n][n];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int le = lane / n, q = lane - le * n;
+  const int64_t Ne = L.Ex * L.Ey;
+  const int64_t g = ((int64_t)blockIdx.x * kWarps2D + warp) * EPW + le;
+  // lanes past EPW*n (n = 3, 5) and lanes past the last element compute on
+  // element 0 and store nothing, neither to memory nor to shared memory
+  const bool lane_ok = le < EPW;
+  const bool active = lane_ok && (g < Ne);
+  const int64_t ge = active ? g : 0;
+  const int lec = lane_ok ? le : 0;
+  double (*X)[n][n] = sm[warp][lec];
+
+  const double dt = RES ? L.ctl.dt_fixed : step_dt(L.ctl, L.st);
+  if (!RES && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(L.ctl, L.st, dt);
+
+  // ---- load row q of u^n and of the static terms g b_x, g b_y ---------------
+  double u0[3][n], gbx[n], gby[n];
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int p = 0; p < n; ++p) u0[v][p] = L.u_in[(v * Ne + ge) * nn + q * n + p];
+#pragma unroll
+  for (int p = 0; p < n; ++p) {
+    gbx[p] = L.snode[ge * nn + q * n + p];
+    gby[p] = L.snode[(Ne + ge) * nn + q * n + p];
+  }
+
+  double Ls[S][3][n];
+  double V[3][n], U[3][n], F2[n], F3[n], G3[n];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double cur[3][n];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+        double acc = u0[v][p];
+#pragma unroll
+        for (int j = 0; j < i; ++j)
+          if (tab_a(N, i, j) != 0.0) acc = fma(-(dt * tab_a(N, i, j)), Ls[j][v][p], acc);
+        cur[v][p] = acc;
+      }
+    // fluxes at this row's nodes
+    double f2[n], f3[n], g3[n];
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+      const double h = cur[0][p], mx = cur[1][p], my = cur[2][p];
+      const double r = drcp(h);
+      const double vx = mx * r, vy = my * r;
+      const double ph = (h * h) * T.half_gravity;
+      f2[p] = fma(mx, vx, ph);
+      f3[p] = mx * vy;
+      g3[p] = fma(my, vy, ph);
+    }
+    // y-fluxes (hv, hu hv / h, hv^2/h + g h^2/2) go through shared memory
+    __syncwarp();
+    if (lane_ok) {
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+        X[0][q][p] = cur[2][p];
+        X[1][q][p] = f3[p];
+        X[2][q][p] = g3[p];
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+      double a0 = T.Dy[q][0] * X[0][0][p];
+      double a1 = fma(cur[0][p], gbx[p], T.Dy[q][0] * X[1][0][p]);
+      double a2 = fma(cur[0][p], gby[p], T.Dy[q][0] * X[2][0][p]);
+#pragma unroll
+      for (int j = 1; j < n; ++j) {
+        a0 = fma(T.Dy[q][j], X[0][j][p], a0);
+        a1 = fma(T.Dy[q][j], X[1][j][p], a1);
+        a2 = fma(T.Dy[q][j], X[2][j][p], a2);
+      }
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        a0 = fma(T.Dx[p][j], cur[1][j], a0);
+        a1 = fma(T.Dx[p][j], f2[j], a1);
+        a2 = fma(T.Dx[p][j], f3[j], a2);
+      }
+      Ls[i][0][p] = a0;
+      Ls[i][1][p] = a1;
+      Ls[i][2][p] = a2;
+    }
+    const double bi = tab_b(N, i);
+    if (bi != 0.0) {
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          V[v][p] = (i == 0) ? bi * Ls[i][v][p] : fma(bi, Ls[i][v][p], V[v][p]);
+          U[v][p] = (i == 0) ? bi * cur[v][p] : fma(bi, cur[v][p], U[v][p]);
+        }
+        F2[p] = (i == 0) ? bi * f2[p] : fma(bi, f2[p], F2[p]);
+        F3[p] = (i == 0) ? bi * f3[p] : fma(bi, f3[p], F3[p]);
+        G3[p] = (i == 0) ? bi * g3[p] : fma(bi, g3[p], G3[p]);
+      }
+    }
+  }
+  static_assert(tab_b(N, 0) != 0.0, "accumulators are initialised by the first stage");
+
+  // ---- W = u^n - dt (dloc F + Bloc)  (or -(dloc F + Bloc) for the residual) --
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p)
+        L.w[(v * Ne + ge) * nn + q * n + p] = RES ? -V[v][p] : fma(-dt, V[v][p], u0[v][p]);
+  }
+
+  // ---- x-face traces of row q -------------------------------------------------
+  const int64_t tstride = Ne * n;  // one (field, side) plane of a trace array
+  // field f of the x-face traces at node p of this row (f, p constant after unrolling)
+  auto fx = [&](int f, int p) -> double {
+    switch (f) {
+      case 0: return U[0][p];
+      case 1: return U[1][p];
+      case 2: return U[2][p];
+      case 3: return F2[p];
+      case 4: return F3[p];
+      case 5: return u0[0][p];
+      default: return u0[1][p];
+    }
+  };
+  auto fy = [&](int f, int p) -> double {
+    switch (f) {
+      case 0: return U[0][p];
+      case 1: return U[1][p];
+      case 2: return U[2][p];
+      case 3: return F3[p];
+      case 4: return G3[p];
+      case 5: return u0[0][p];
+      default: return u0[2][p];
+    }
+  };
+  {
+    if (active) {
+#pragma unroll
+      for (int f = 0; f < kTrFields; ++f) {
+        double tl, tr;
+        if (GLL) {
+          tl = fx(f, 0);
+          tr = fx(f, N);
+        } else {
+          tl = T.l0[0] * fx(f, 0);
+          tr = T.l1[0] * fx(f, 0);
+#pragma unroll
+          for (int p = 1; p < n; ++p) {
+            tl = fma(T.l0[p], fx(f, p), tl);
+            tr = fma(T.l1[p], fx(f, p), tr);
+          }
+        }
+        L.trx[(2 * f + 0) * tstride + ge * n + q] = tl;
+        L.trx[(2 * f + 1) * tstride + ge * n + q] = tr;
+      }
+    }
+  }
+  // ---- y-face traces of column p = q (two shared-memory rounds) -------------
+  {
+#pragma unroll
+    for (int r0 = 0; r0 < kTrFields; r0 += NB) {
+      __syncwarp();
+      if (lane_ok) {
+#pragma unroll
+        for (int f = r0; f < r0 + NB && f < kTrFields; ++f)
+#pragma unroll
+          for (int p = 0; p < n; ++p) X[f - r0][q][p] = fy(f, p);
+      }
+      __syncwarp();
+      if (active) {
+#pragma unroll
+        for (int f = r0; f < r0 + NB && f < kTrFields; ++f) {
+          double tb, tt;
+          if (GLL) {
+            tb = X[f - r0][0][q];
+            tt = X[f - r0][N][q];
+          } else {
+            tb = T.l0[0] * X[f - r0][0][q];
+            tt = T.l1[0] * X[f - r0][0][q];
+#pragma unroll
+            for (int j = 1; j < n; ++j) {
+              tb = fma(T.l0[j], X[f - r0][j][q], tb);
+              tt = fma(T.l1[j], X[f - r0][j][q], tt);
+            }
+          }
+          L.try_[(2 * f + 0) * tstride + ge * n + q] = tb;
+          L.try_[(2 * f + 1) * tstride + ge * n + q] = tt;
+        }
+      }
+    }
+  }
+}
+
+// Doubled face term on one side of a face from both sides' traces.
+// tr[f] fields: 0..2 U, 3..4 time-averaged normal fluxes of the two momenta,
+// 5 h^n, 6 normal momentum at t^n.  `nv` is the index (1 or 2) of the
+// normal momentum; `gdb` = g (b+ - b-).  Returns T'^- (minus side) when
+// MINUS, else T'^+.
+template <bool MINUS>
+__device__ __forceinline__ void face_term(const double* tm, const double* tp, int nv, double gdb,
+                                          double g, double out[3]) {
+  const double lam = max_nonneg(swe_speed(tm[5], tm[6], g), swe_speed(tp[5], tp[6], g));
+  // time-averaged normal fluxes: h -> U of the normal momentum; momenta -> fields 3, 4
+  const double dF0 = tp[nv] - tm[nv];
+  const double dF1 = tp[3] - tm[3];
+  const double dF2 = tp[4] - tm[4];
+  const double dU0 = tp[0] - tm[0], dU1 = tp[1] - tm[1], dU2 = tp[2] - tm[2];
+  if (MINUS) {
+    out[0] = fma(-lam, dU0, dF0);
+    out[1] = fma(-lam, dU1, dF1);
+    out[2] = fma(-lam, dU2, dF2);
+    out[nv] = fma(tm[5], gdb, out[nv]);
+  } else {
+    out[0] = -fma(lam, dU0, dF0);
+    out[1] = -fma(lam, dU1, dF1);
+    out[2] = -fma(lam, dU2, dF2);
+    out[nv] = fma(-tp[5], gdb, out[nv]);
+  }
+}
+
+template <int N, bool GLL, bool RES>
+__global__ void __launch_bounds__(kBlock2D) k_face_2d(const Launch2D L) {
+  constexpr int n = N + 1;
+  constexpr int nn = n * n;
+  constexpr int EPW = 32 / n;
+  const Tables& T = L.tab;
+  __shared__ double smT[kWarps2D][EPW][2][3][n];   // y-face terms of each column
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int le = lane / n, q = lane - le * n;
+  const int64_t Ne = L.Ex * L.Ey;
+  const int64_t g = ((int64_t)blockIdx.x * kWarps2D + warp) * EPW + le;
+  const bool lane_ok = le < EPW;
+  const bool active = lane_ok && (g < Ne);
+  const int64_t ge = active ? g : 0;
+  const int lec = lane_ok ? le : 0;
+  const int64_t ey = ge / L.Ex, ex = ge - ey * L.Ex;
+  const int64_t exl = ex == 0 ? L.Ex - 1 : ex - 1, exr = ex == L.Ex - 1 ? 0 : ex + 1;
+  const int64_t eyb = ey == 0 ? L.Ey - 1 : ey - 1, eyt = ey == L.Ey - 1 ? 0 : ey + 1;
+  const int64_t eL = ey * L.Ex + exl, eR = ey * L.Ex + exr;
+  const int64_t eB = eyb * L.Ex + ex, eT = eyt * L.Ex + ex;
+  const int64_t ts = Ne * n;
+  const double dt = RES ? 1.0 : L.st->dt_cur;
+
+  // ---- x faces of row q --------------------------------------------------------
+  double Txl[3], Txr[3];
+  {
+    double a[kTrFields], b[kTrFields];
+    // left face: minus = left neighbour's right side, plus = own left side
+#pragma unroll
+    for (int f = 0; f < kTrFields; ++f) {
+      a[f] = L.trx[(2 * f + 1) * ts + eL * n + q];
+      b[f] = L.trx[(2 * f + 0) * ts + ge * n + q];
+    }
+    face_term<false>(a, b, 1, L.sface[ge * n + q], T.gravity, Txl);
+    // right face: minus = own right side, plus = right neighbour's left side
+#pragma unroll
+    for (int f = 0; f < kTrFields; ++f) {
+      a[f] = L.trx[(2 * f + 1) * ts + ge * n + q];
+      b[f] = L.trx[(2 * f + 0) * ts + eR * n + q];
+    }
+    face_term<true>(a, b, 1, L.sface[eR * n + q], T.gravity, Txr);
+  }
+  // ---- y faces of column q -------------------------------------------------------
+  {
+    double a[kTrFields], b[kTrFields], Tb[3], Tt[3];
+#pragma unroll
+    for (int f = 0; f < kTrFields; ++f) {
+      a[f] = L.try_[(2 * f + 1) * ts + eB * n + q];
+      b[f] = L.try_[(2 * f + 0) * ts + ge * n + q];
+    }
+    face_term<false>(a, b, 2, L.sface[(Ne + ge) * n + q], T.gravity, Tb);
+#pragma unroll
+    for (int f = 0; f < kTrFields; ++f) {
+      a[f] = L.try_[(2 * f + 1) * ts + ge * n + q];
+      b[f] = L.try_[(2 * f + 0) * ts + eT * n + q];
+    }
+    face_term<true>(a, b, 2, L.sface[(Ne + eT) * n + q], T.gravity, Tt);
+    if (lane_ok) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        smT[warp][lec][0][v][q] = Tb[v];
+        smT[warp][lec][1][v][q] = Tt[v];
+      }
+    }
+  }
+  __syncwarp();
+
+  // ---- corrections and update of row q ---------------------------------------
+  double out[3][n];
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+      double R = 0.0;
+      bool any = false;
+      if (!GLL || p == N) { R = Txr[v] * T.gRx[p]; any = true; }
+      if (!GLL || p == 0) { R = any ? fma(Txl[v], T.gLx[p], R) : Txl[v] * T.gLx[p]; any = true; }
+      if (!GLL || q == N) { R = any ? fma(smT[warp][lec][1][v][p], T.gRy[q], R)
+                                    : smT[warp][lec][1][v][p] * T.gRy[q]; any = true; }
+      if (!GLL || q == 0) { R = any ? fma(smT[warp][lec][0][v][p], T.gLy[q], R)
+                                    : smT[warp][lec][0][v][p] * T.gLy[q]; any = true; }
+      const double w = L.w[(v * Ne + ge) * nn + q * n + p];
+      out[v][p] = any ? fma(-dt, R, w) : w;
+    }
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) L.u_out[(v * Ne + ge) * nn + q * n + p] = out[v][p];
+  }
+  if (RES) return;
+
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < n; ++p)
+    bad |= !positive_finite(out[0][p]) || !finite(out[1][p]) || !finite(out[2][p]);
+  if (active && bad) atomicOr(&L.st->status, 1u);
+
+  if (L.ctl.want_rate) {
+    // element means (Definition admissibility.preserving.means), then
+    // sigma_x/dx + sigma_y/dy (Sec. 5, Eq. time.step.2d)
+    double m[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      double s = T.w[0] * out[v][0];
+#pragma unroll
+      for (int p = 1; p < n; ++p) s = fma(T.w[p], out[v][p], s);
+      m[v] = T.w[q] * s;
+    }
+    // sum over the n rows of the element (lanes le*n .. le*n+n-1)
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      double s = m[v];
+#pragma unroll
+      for (int k = 1; k < n; ++k) {
+        const int src = le * n + ((q + k) % n);
+        s += __shfl_sync(0xffffffffu, m[v], src < 32 ? src : lane);
+      }
+      m[v] = s;
+    }
+    double rate = 0.0;
+    if (active && q == 0) {
+      const double r = drcp(m[0]);
+      const double c = sqrt(T.gravity * m[0]);
+      rate = fma(fabs(m[1] * r) + c, T.inv_dx, (fabs(m[2] * r) + c) * T.inv_dy);
+    }
+    block_max_atomic<kBlock2D>(rate, &L.st->rate[L.ctl.slot_write]);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBlock2D) k_rate_2d(const Launch2D L, int slot) {
+  constexpr int n = N + 1;
+  constexpr int nn = n * n;
+  const Tables& T = L.tab;
+  const int64_t Ne = L.Ex * L.Ey;
+  const int64_t e = (int64_t)blockIdx.x * kBlock2D + threadIdx.x;
+  double rate = 0.0;
+  if (e < Ne) {
+    double m[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      double s = 0.0;
+#pragma unroll
+      for (int qq = 0; qq < n; ++qq) {
+        double r = 0.0;
+#pragma unroll
+        for (int p = 0; p < n; ++p) r = fma(T.w[p], L.u_in[(v * Ne + e) * nn + qq * n + p], r);
+        s = fma(T.w[qq], r, s);
+      }
+      m[v] = s;
+    }
+    const double r = drcp(m[0]);
+    const double c = sqrt(T.gravity * m[0]);
+    rate = fma(fabs(m[1] * r) + c, T.inv_dx, (fabs(m[2] * r) + c) * T.inv_dy);
+  }
+  block_max_atomic<kBlock2D>(rate, &L.st->rate[slot]);
+}
+
+// Static terms from the bathymetry: g b_x, g b_y at the nodes and
+// g (b+ - b-) at the left x-face and bottom y-face of each element.
+template <int N, bool GLL>
+__global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c,
+                          double* __restrict__ snode, double* __restrict__ sface, const Tables T) {
+  constexpr int n = N + 1;
+  constexpr int nn = n * n;
+  const int64_t Ne = Ex * Ey;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Ne) return;
+  const int64_t ey = e / Ex, ex = e - ey * Ex;
+  const int64_t eL = ey * Ex + (ex == 0 ? Ex - 1 : ex - 1);
+  const int64_t eB = (ey == 0 ? Ey - 1 : ey - 1) * Ex + ex;
+  double b[n][n];
+#pragma unroll
+  for (int q = 0; q < n; ++q)
+#pragma unroll
+    for (int p = 0; p < n; ++p) b[q][p] = c[e * nn + q * n + p];
+#pragma unroll
+  for (int q = 0; q < n; ++q)
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+      double dx = 0.0, dy = 0.0;
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        dx = fma(T.Dx[p][j], b[q][j], dx);
+        dy = fma(T.Dy[q][j], b[j][p], dy);
+      }
+      snode[e * nn + q * n + p] = T.gravity * dx;
+      snode[(Ne + e) * nn + q * n + p] = T.gravity * dy;
+    }
+  // own left/bottom traces and the neighbours' right/top traces
+#pragma unroll
+  for (int k = 0; k < n; ++k) {
+    double own_l = 0.0, own_b = 0.0, nb_r = 0.0, nb_t = 0.0;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      own_l = fma(T.l0[j], b[k][j], own_l);
+      own_b = fma(T.l0[j], b[j][k], own_b);
+      nb_r = fma(T.l1[j], c[eL * nn + k * n + j], nb_r);
+      nb_t = fma(T.l1[j], c[eB * nn + j * n + k], nb_t);
+    }
+    sface[e * n + k] = T.gravity * (own_l - nb_r);
+    sface[(Ne + e) * n + k] = T.gravity * (own_b - nb_t);
+  }
+}
+
+template <int N, bool GLL>
+unsigned blocks_2d(const Launch2D& L) {
+  constexpr int per_block = kWarps2D * (32 / (N + 1));
+  return (unsigned)((L.Ex * L.Ey + per_block - 1) / per_block);
+}
+
+template <int N, bool GLL>
+int launch_local_t(const Launch2D& L, cudaStream_t s) {
+  if (L.ctl.residual)
+    k_local_2d<N, GLL, true><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+  else
+    k_local_2d<N, GLL, false><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+  return (int)cudaGetLastError();
+}
+
+template <int N, bool GLL>
+int launch_face_t(const Launch2D& L, cudaStream_t s) {
+  if (L.ctl.residual)
+    k_face_2d<N, GLL, true><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+  else
+    k_face_2d<N, GLL, false><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+#define CRKFR_DISPATCH_2D(FN)                              \
+  switch (L.N * 2 + (L.gll ? 1 : 0)) {                     \
+    case 2: return FN<1, false>(L, s);                     \
+    case 3: return FN<1, true>(L, s);                      \
+    case 4: return FN<2, false>(L, s);                     \
+    case 5: return FN<2, true>(L, s);                      \
+    case 6: return FN<3, false>(L, s);                     \
+    case 7: return FN<3, true>(L, s);                      \
+    case 8: return FN<4, false>(L, s);                     \
+    case 9: return FN<4, true>(L, s);                      \
+  }                                                        \
+  return (int)cudaErrorInvalidValue;
+
+int launch_local_2d(const Launch2D& L, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  CRKFR_DISPATCH_2D(launch_local_t)
+}
+
+int launch_face_2d(const Launch2D& L, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  CRKFR_DISPATCH_2D(launch_face_t)
+}
+
+int launch_rate_2d(const Launch2D& L, int slot, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned blocks = (unsigned)((L.Ex * L.Ey + kBlock2D - 1) / kBlock2D);
+  switch (L.N) {
+    case 1: k_rate_2d<1><<<blocks, kBlock2D, 0, s>>>(L, slot); break;
+    case 2: k_rate_2d<2><<<blocks, kBlock2D, 0, s>>>(L, slot); break;
+    case 3: k_rate_2d<3><<<blocks, kBlock2D, 0, s>>>(L, slot); break;
+    case 4: k_rate_2d<4><<<blocks, kBlock2D, 0, s>>>(L, slot); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, double* snode,
+                   double* sface, const Tables& T, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned blocks = (unsigned)((Ex * Ey + 127) / 128);
+  switch (N) {
+    case 1: k_coef_2d<1, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
+    case 2: k_coef_2d<2, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
+    case 3: k_coef_2d<3, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
+    case 4: k_coef_2d<4, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  (void)gll;
+  return (int)cudaGetLastError();
+}
+
+}  // namespace crkfr

@@ -1,0 +1,90 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every entry point include/crkfr.h declares, rejects bad
+configurations, and its host-computed reference element and CFL(N) agree
+with the oracle (Sec. 2, Eq. soln.points; Sec. 5, under Eq. time.step.2d)."""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_08611_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def crk():
+    B.build_library()
+    from paper_2512_08611_gb300 import crkfr
+    crkfr.lib()
+    return crkfr
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "crkfr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(crkfr_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(crk):
+    names = declared_functions()
+    assert len(names) >= 15
+    handle = ctypes.CDLL(B.library_path())
+    for name in names:
+        assert hasattr(handle, name), name
+    # and the binding declares exactly these
+    assert set(names) == set(crk.SIGNATURES)
+
+
+def test_config_struct_layout(crk):
+    assert ctypes.sizeof(crk.Config) == 40
+    assert crk.Config.gravity.offset == 16
+
+
+def test_bad_configs_are_rejected(crk):
+    from paper_2512_08611_gb300.crkfr import CrkfrError, Solver
+    with pytest.raises(CrkfrError) as e:
+        Solver("swe1d", 5)
+    assert e.value.status == -2
+    with pytest.raises(CrkfrError):
+        Solver("swe1d", 0, nodes="gll")
+    with pytest.raises(CrkfrError):
+        Solver("swe2d", 0)
+    with pytest.raises(CrkfrError) as e:
+        Solver("swe1d", 3, cfl_safety=1.5)
+    assert e.value.status == -1
+    with pytest.raises(CrkfrError):
+        Solver("swe1d", 3, gravity=-1.0)
+
+
+def test_calls_before_mesh_are_refused(crk):
+    from paper_2512_08611_gb300.crkfr import CrkfrError, Solver
+    s = Solver("swe1d", 2)
+    with pytest.raises(CrkfrError) as e:
+        s.time()
+    assert e.value.status == -6
+
+
+@pytest.mark.parametrize("N", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("family", ["gl", "gll"])
+def test_nodes_and_cfl_match_oracle(crk, N, family):
+    if family == "gll" and N == 0:
+        pytest.skip("GLL needs N >= 1")
+    from oracle.basis import Basis
+    from paper_2512_08611_gb300.crkfr import Solver
+    s = Solver("swe1d", N, nodes=family)
+    xi, w = s.nodes()
+    bs = Basis(N, family)
+    assert np.max(np.abs(xi - bs.xi)) < 2e-16 * 4
+    assert np.max(np.abs(w - bs.w)) < 2e-16 * 4
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")) as fh:
+        want = json.load(fh)["cfl"][f"{N}_{family}"]
+    assert s.cfl() == pytest.approx(want, rel=1e-8)
+
+
+def test_explicit_cfl_number_is_used(crk):
+    from paper_2512_08611_gb300.crkfr import Solver
+    assert Solver("swe1d", 3, cfl_number=0.05).cfl() == 0.05
