@@ -57,13 +57,14 @@ HBM_FALLBACK_GBS = 6800.0
 # workloads
 # ---------------------------------------------------------------------------
 class Workload:
-    def __init__(self, name):
+    def __init__(self, name, mesh=None):
         self.name = name
         if name == "swe2d":
-            self.system, self.N, self.E, self.L = "swe2d", 3, (1024, 1024), 100.0
+            side = mesh or 1024
+            self.system, self.N, self.E, self.L = "swe2d", 3, (side, side), 100.0
             self.M, self.dim = 3, 2
         elif name == "swe1d":
-            self.system, self.N, self.E, self.L = "swe1d", 4, (100000,), 100.0
+            self.system, self.N, self.E, self.L = "swe1d", 4, (mesh or 100000,), 100.0
             self.M, self.dim = 2, 1
         else:
             raise ValueError(name)
@@ -312,17 +313,21 @@ def run_ours(args, wl):
     ms_per_step = elapsed_ms / args.steps
 
     # end to end through the host-buffer entry point (pinned host memory)
-    host = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
-    host.copy_(u_init.cpu())
-    h = host.numpy()
-    e2e_steps = max(3, min(args.steps, 20))
-    s.step_host(h, h, dt=0.0, nsteps=1)   # warm the host path (allocates its device copy)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s.step_host(h, h, dt=0.0, nsteps=1)
-    e2e_s = time.perf_counter() - t0
     state_bytes = wl.dof * 8
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
+        host.copy_(u_init.cpu())
+        h = host.numpy()
+        e2e_steps = max(3, min(args.steps, 20))
+        s.step_host(h, h, dt=0.0, nsteps=1)   # warm the host path (allocates its device copy)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            s.step_host(h, h, dt=0.0, nsteps=1)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": wl.dof * e2e_steps / e2e_s, "unit": "DoF-updates/s",
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
 
     # roofline of the dominant kernel
     peaks = load_peaks()
@@ -361,12 +366,11 @@ def run_ours(args, wl):
                 "frac": wl.min_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
         "kernel_shares": shares,
-        "e2e": {"value": wl.dof * e2e_steps / e2e_s, "unit": "DoF-updates/s",
-                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         cpu_threads()
         sch, uu, bb, dof, side = time_oracle(wl, 15.0, 2)
         cfl = s.cfl()
@@ -394,10 +398,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="swe2d", choices=["swe2d", "swe1d"])
+    ap.add_argument("--mesh", type=int, default=None,
+                    help="elements per side (2D) or elements (1D); profiling of small cases")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    wl = Workload(args.workload)
+    wl = Workload(args.workload, args.mesh)
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return

@@ -27,6 +27,14 @@ def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
+def residual_close(r, r_want, u, dt, rtol=1e-11, utol=1e-13):
+    """A residual r = (u^{n+1} - u^n)/dt matches if its error, as an error of
+    the update dt r, is below utol of the state, or below rtol of r itself
+    (a zero residual, e.g. of a constant state, is checked the first way)."""
+    err = np.linalg.norm((np.asarray(r) - r_want).ravel())
+    return err <= rtol * np.linalg.norm(np.ravel(r_want)) + utol * np.linalg.norm(np.ravel(u)) / dt
+
+
 def positions_1d(basis, E, lo, hi):
     dx = (hi - lo) / E
     return lo + (np.arange(E)[:, None] + basis.xi[None, :]) * dx, dx
