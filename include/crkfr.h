@@ -184,6 +184,14 @@ typedef enum {
 crkfr_status crkfr_profile_enable(crkfr_ctx* ctx, int32_t enable);
 crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms);
 
+/* Self-check of the two FP64 elementary operations the kernels implement
+ * themselves instead of the IEEE division and square root: out[i] = 1/x[i]
+ * (op 0) or sqrt(x[i]) (op 1) for n values, device arrays, computed by the
+ * same device functions the step uses (FP32 seed built from the bit pattern,
+ * one third-order refinement).  Lets a test bound their error. */
+crkfr_status crkfr_math_check(const double* x_dev, double* out_dev, int64_t n, int32_t op,
+                              void* stream);
+
 /* Static strings. */
 const char* crkfr_error_string(crkfr_status status);
 const char* crkfr_last_error(const crkfr_ctx* ctx);

@@ -64,6 +64,7 @@ SIGNATURES = {
     "crkfr_launch_count": (_I64, [_P]),
     "crkfr_profile_enable": (_I32, [_P, _I32]),
     "crkfr_profile_read": (_I32, [_P, _I32, _PI64, _PD]),
+    "crkfr_math_check": (_I32, [_P, _P, _I64, _I32, _P]),
     "crkfr_error_string": (ctypes.c_char_p, [_I32]),
     "crkfr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -93,6 +94,20 @@ def _stream():
     if not torch.cuda.is_available():
         return ctypes.c_void_p(0)   # calls that reach CUDA report the error themselves
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def math_check(x, op):
+    """out = 1/x (op 'rcp') or sqrt(x) (op 'sqrt') by the kernels' own FP64
+    routines; x a contiguous float64 CUDA tensor."""
+    import torch
+    if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    out = torch.empty_like(x)
+    st = lib().crkfr_math_check(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                x.numel(), {"rcp": 0, "sqrt": 1}[op], _stream())
+    if st != CRKFR_OK:
+        raise CrkfrError(st, lib().crkfr_error_string(st).decode())
+    return out
 
 
 class Solver:

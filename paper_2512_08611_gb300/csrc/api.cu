@@ -11,6 +11,7 @@
 
 #include "crkfr.h"
 #include "crkfr_internal.h"
+#include "device_common.cuh"
 
 using namespace crkfr;
 
@@ -131,6 +132,13 @@ crkfr_status drain_profile(crkfr_ctx* c, bool keep) {
   }
   c->pending.clear();
   return st;
+}
+
+__global__ void k_math_check(const double* __restrict__ x, double* __restrict__ out, int64_t n,
+                             int op) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = op == 0 ? drcp(x[i]) : dsqrt_pos(x[i]);
 }
 
 __global__ void k_set_time(DevState* st, int slot, double t) {
@@ -580,6 +588,15 @@ crkfr_status crkfr_set_time(crkfr_ctx* c, double t, void* stream) {
   CK(c, cudaGetLastError());
   c->launches += 1;
   return CRKFR_OK;
+}
+
+crkfr_status crkfr_math_check(const double* x, double* out, int64_t n, int32_t op, void* stream) {
+  if (!x || !out || n < 0 || (op != 0 && op != 1)) return CRKFR_ERR_ARG;
+  if (n == 0) return CRKFR_OK;
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffff) return CRKFR_ERR_ARG;
+  k_math_check<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, out, n, op);
+  return cudaGetLastError() == cudaSuccess ? CRKFR_OK : CRKFR_ERR_CUDA;
 }
 
 crkfr_status crkfr_profile_enable(crkfr_ctx* c, int32_t enable) {

@@ -40,6 +40,29 @@ __device__ __forceinline__ double drcp(double x) {
   return r;
 }
 
+// sqrt(x) for FP64 x > 0.  Seed: the FP32 reciprocal square root of x
+// rounded down to 24 significant bits, built from and converted back to the
+// FP64 bit pattern with integer operations.  Refinement: with t = x y and
+// e = 1 - t y, sqrt(x) = t (1 - e)^(-1/2); the binomial series to second
+// order, t + t e (1/2 + 3e/8), takes the ~2^-21 seed error to ~2^-63.  Five
+// FP64 instructions.  Non-positive inputs and exponents outside the FP32
+// seed range fall back to the IEEE square root.
+__device__ __forceinline__ double dsqrt_pos(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (hi < 0 || ex < 1023 - 124 || ex > 1023 + 124) return sqrt(x);
+  const int fb = (((hi - ((1023 - 127) << 20)) << 3) | (int)(lo >> 29));
+  const float yf = rsqrtf(__int_as_float(fb));
+  const int yb = __float_as_int(yf);
+  const double y = __hiloint2double((yb >> 3) + ((1023 - 127) << 20), yb << 29);
+  const double t = x * y;
+  const double e = fma(-t, y, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  const double q = t * e;
+  return fma(q, p, t);
+}
+
 // max of two non-negative doubles through their bit patterns (integer pipe)
 __device__ __forceinline__ double max_nonneg(double a, double b) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);

@@ -59,7 +59,7 @@ __device__ __forceinline__ double trace_l(const Tables& T, const double* X) {
 
 // sigma(f' + B) for shallow water: |m/h| + sqrt(g h)
 __device__ __forceinline__ double swe_speed(double h, double m, double g) {
-  return fabs(m * drcp(h)) + sqrt(g * h);
+  return fabs(m * drcp(h)) + dsqrt_pos(g * h);
 }
 
 template <int SYS, int N, bool GLL, bool RES>

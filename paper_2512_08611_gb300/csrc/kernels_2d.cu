@@ -13,7 +13,7 @@
 //              time-averaged normal flux and h^n and the normal momentum at
 //              t^n (Eqs. time.avg.soln, combined.wave.speed,
 //              good.numflux.non.cons).
-//  k_face_2d   the only inter-element coupling: per face node the
+//  k_face_2d   the only inter-element coupling: once per face node the
 //              time-averaged Rusanov flux (Eq. numflux.cons) with the
 //              wave-speed estimate of the full system at u^n, the frozen
 //              non-conservative fluctuation B(w^{n,+-})(W^num - W^{+-}), and
@@ -44,7 +44,7 @@ constexpr int kTrFields = 7;
 // h^n, hv^n.  (The time-averaged h fluxes are U_hu and U_hv.)
 
 __device__ __forceinline__ double swe_speed(double h, double m, double g) {
-  return fabs(m * drcp(h)) + sqrt(g * h);
+  return fabs(m * drcp(h)) + dsqrt_pos(g * h);
 }
 
 template <int N, bool GLL, bool RES>
@@ -252,102 +252,99 @@ __global__ void __launch_bounds__(kBlock2D) k_local_2d(const Launch2D L) {
   }
 }
 
-// Doubled face term on one side of a face from both sides' traces.
-// tr[f] fields: 0..2 U, 3..4 time-averaged normal fluxes of the two momenta,
-// 5 h^n, 6 normal momentum at t^n.  `nv` is the index (1 or 2) of the
-// normal momentum; `gdb` = g (b+ - b-).  Returns T'^- (minus side) when
-// MINUS, else T'^+.
-template <bool MINUS>
-__device__ __forceinline__ void face_term(const double* tm, const double* tp, int nv, double gdb,
-                                          double g, double out[3]) {
+// Doubled face terms of both sides of one face node, T'^- = 2 (F^num,- - F^tot,-)
+// and T'^+ = 2 (F^num,+ - F^tot,+), from the two sides' traces.
+// Trace fields: 0..2 U, 3..4 time-averaged normal fluxes of the two momenta,
+// 5 h^n, 6 normal momentum at t^n.  `nv` (1 or 2) is the index of the normal
+// momentum, whose equation carries the fluctuation; gdb = g (b+ - b-).
+__device__ __forceinline__ void face_terms(const double* tm, const double* tp, int nv, double gdb,
+                                           double g, double Tm[3], double Tp[3]) {
   const double lam = max_nonneg(swe_speed(tm[5], tm[6], g), swe_speed(tp[5], tp[6], g));
-  // time-averaged normal fluxes: h -> U of the normal momentum; momenta -> fields 3, 4
-  const double dF0 = tp[nv] - tm[nv];
-  const double dF1 = tp[3] - tm[3];
-  const double dF2 = tp[4] - tm[4];
-  const double dU0 = tp[0] - tm[0], dU1 = tp[1] - tm[1], dU2 = tp[2] - tm[2];
-  if (MINUS) {
-    out[0] = fma(-lam, dU0, dF0);
-    out[1] = fma(-lam, dU1, dF1);
-    out[2] = fma(-lam, dU2, dF2);
-    out[nv] = fma(tm[5], gdb, out[nv]);
-  } else {
-    out[0] = -fma(lam, dU0, dF0);
-    out[1] = -fma(lam, dU1, dF1);
-    out[2] = -fma(lam, dU2, dF2);
-    out[nv] = fma(-tp[5], gdb, out[nv]);
+  // time-averaged normal flux of h is the time-averaged normal momentum
+  const double dF[3] = {tp[nv] - tm[nv], tp[3] - tm[3], tp[4] - tm[4]};
+  const double dU[3] = {tp[0] - tm[0], tp[1] - tm[1], tp[2] - tm[2]};
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    Tm[v] = fma(-lam, dU[v], dF[v]);
+    Tp[v] = -fma(lam, dU[v], dF[v]);
   }
+  Tm[nv] = fma(tm[5], gdb, Tm[nv]);
+  Tp[nv] = fma(-tp[5], gdb, Tp[nv]);
 }
 
+// Face kernel on tiles of kWarps2D x EPW elements (one tile row per warp).
+// Phase 1 solves every face node of the tile exactly once in a flat loop over
+// the block (warps with no face left issue nothing, so only the last, partial
+// warp of the loop pays for idle lanes) and keeps both sides' terms in shared
+// memory; phase 2 applies them along the rows and columns of each element.
 template <int N, bool GLL, bool RES>
 __global__ void __launch_bounds__(kBlock2D) k_face_2d(const Launch2D L) {
   constexpr int n = N + 1;
   constexpr int nn = n * n;
-  constexpr int EPW = 32 / n;
+  constexpr int TX = 32 / n;        // elements per tile row (= per warp)
+  constexpr int TY = kWarps2D;      // tile rows
+  constexpr int NX = TY * (TX + 1) * n;
+  constexpr int NY = (TY + 1) * TX * n;
   const Tables& T = L.tab;
-  __shared__ double smT[kWarps2D][EPW][2][3][n];   // y-face terms of each column
+  // x faces: [row][face k between elements k-1 and k][node]; y faces:
+  // [face k between rows k-1 and k][column][node]; both sides, 3 variables
+  __shared__ double sxm[TY][TX + 1][n][3], sxp[TY][TX + 1][n][3];
+  __shared__ double sym[TY + 1][TX][n][3], syp[TY + 1][TX][n][3];
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int le = lane / n, q = lane - le * n;
-  const int64_t Ne = L.Ex * L.Ey;
-  const int64_t g = ((int64_t)blockIdx.x * kWarps2D + warp) * EPW + le;
-  const bool lane_ok = le < EPW;
-  const bool active = lane_ok && (g < Ne);
-  const int64_t ge = active ? g : 0;
-  const int lec = lane_ok ? le : 0;
-  const int64_t ey = ge / L.Ex, ex = ge - ey * L.Ex;
-  const int64_t exl = ex == 0 ? L.Ex - 1 : ex - 1, exr = ex == L.Ex - 1 ? 0 : ex + 1;
-  const int64_t eyb = ey == 0 ? L.Ey - 1 : ey - 1, eyt = ey == L.Ey - 1 ? 0 : ey + 1;
-  const int64_t eL = ey * L.Ex + exl, eR = ey * L.Ex + exr;
-  const int64_t eB = eyb * L.Ex + ex, eT = eyt * L.Ex + ex;
-  const int64_t ts = Ne * n;
+  const int64_t Ex = L.Ex, Ey = L.Ey, Ne = Ex * Ey, ts = Ne * n;
+  const int64_t ex0 = (int64_t)blockIdx.x * TX, ey0 = (int64_t)blockIdx.y * TY;
   const double dt = RES ? 1.0 : L.st->dt_cur;
 
-  // ---- x faces of row q --------------------------------------------------------
-  double Txl[3], Txr[3];
-  {
-    double a[kTrFields], b[kTrFields];
-    // left face: minus = left neighbour's right side, plus = own left side
+  // ---- phase 1: every face node of the tile once --------------------------
+  for (int f = threadIdx.x; f < NX + NY; f += kBlock2D) {
+    double a[kTrFields], b[kTrFields], Tm[3], Tp[3];
+    if (f < NX) {
+      const int q = f % n, k = (f / n) % (TX + 1), r = f / (n * (TX + 1));
+      const int64_t ey = ey0 + r;
+      if (ey >= Ey || (k > 0 && ex0 + k - 1 >= Ex)) continue;
+      const int64_t em = ey * Ex + (ex0 + k - 1 + Ex) % Ex;
+      const int64_t ep = ey * Ex + (ex0 + k) % Ex;
 #pragma unroll
-    for (int f = 0; f < kTrFields; ++f) {
-      a[f] = L.trx[(2 * f + 1) * ts + eL * n + q];
-      b[f] = L.trx[(2 * f + 0) * ts + ge * n + q];
-    }
-    face_term<false>(a, b, 1, L.sface[ge * n + q], T.gravity, Txl);
-    // right face: minus = own right side, plus = right neighbour's left side
-#pragma unroll
-    for (int f = 0; f < kTrFields; ++f) {
-      a[f] = L.trx[(2 * f + 1) * ts + ge * n + q];
-      b[f] = L.trx[(2 * f + 0) * ts + eR * n + q];
-    }
-    face_term<true>(a, b, 1, L.sface[eR * n + q], T.gravity, Txr);
-  }
-  // ---- y faces of column q -------------------------------------------------------
-  {
-    double a[kTrFields], b[kTrFields], Tb[3], Tt[3];
-#pragma unroll
-    for (int f = 0; f < kTrFields; ++f) {
-      a[f] = L.try_[(2 * f + 1) * ts + eB * n + q];
-      b[f] = L.try_[(2 * f + 0) * ts + ge * n + q];
-    }
-    face_term<false>(a, b, 2, L.sface[(Ne + ge) * n + q], T.gravity, Tb);
-#pragma unroll
-    for (int f = 0; f < kTrFields; ++f) {
-      a[f] = L.try_[(2 * f + 1) * ts + ge * n + q];
-      b[f] = L.try_[(2 * f + 0) * ts + eT * n + q];
-    }
-    face_term<true>(a, b, 2, L.sface[(Ne + eT) * n + q], T.gravity, Tt);
-    if (lane_ok) {
+      for (int fi = 0; fi < kTrFields; ++fi) {
+        a[fi] = L.trx[(2 * fi + 1) * ts + em * n + q];
+        b[fi] = L.trx[(2 * fi + 0) * ts + ep * n + q];
+      }
+      face_terms(a, b, 1, L.sface[ep * n + q], T.gravity, Tm, Tp);
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        smT[warp][lec][0][v][q] = Tb[v];
-        smT[warp][lec][1][v][q] = Tt[v];
+        sxm[r][k][q][v] = Tm[v];
+        sxp[r][k][q][v] = Tp[v];
+      }
+    } else {
+      const int g = f - NX;
+      const int p = g % n, c = (g / n) % TX, k = g / (n * TX);
+      const int64_t ex = ex0 + c;
+      if (ex >= Ex || (k > 0 && ey0 + k - 1 >= Ey)) continue;
+      const int64_t em = ((ey0 + k - 1 + Ey) % Ey) * Ex + ex;
+      const int64_t ep = ((ey0 + k) % Ey) * Ex + ex;
+#pragma unroll
+      for (int fi = 0; fi < kTrFields; ++fi) {
+        a[fi] = L.try_[(2 * fi + 1) * ts + em * n + p];
+        b[fi] = L.try_[(2 * fi + 0) * ts + ep * n + p];
+      }
+      face_terms(a, b, 2, L.sface[(Ne + ep) * n + p], T.gravity, Tm, Tp);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        sym[k][c][p][v] = Tm[v];
+        syp[k][c][p][v] = Tp[v];
       }
     }
   }
-  __syncwarp();
+  __syncthreads();
 
-  // ---- corrections and update of row q ---------------------------------------
+  // ---- phase 2: corrections and update, one element row per thread -------
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int c = lane / n, q = lane - c * n;
+  const bool lane_ok = c < TX;
+  const int cc = lane_ok ? c : 0;
+  const int64_t ey = ey0 + r, ex = ex0 + cc;
+  const bool active = lane_ok && ey < Ey && ex < Ex;
+  const int64_t ge = active ? ey * Ex + ex : 0;
   double out[3][n];
 #pragma unroll
   for (int v = 0; v < 3; ++v)
@@ -355,12 +352,19 @@ __global__ void __launch_bounds__(kBlock2D) k_face_2d(const Launch2D L) {
     for (int p = 0; p < n; ++p) {
       double R = 0.0;
       bool any = false;
-      if (!GLL || p == N) { R = Txr[v] * T.gRx[p]; any = true; }
-      if (!GLL || p == 0) { R = any ? fma(Txl[v], T.gLx[p], R) : Txl[v] * T.gLx[p]; any = true; }
-      if (!GLL || q == N) { R = any ? fma(smT[warp][lec][1][v][p], T.gRy[q], R)
-                                    : smT[warp][lec][1][v][p] * T.gRy[q]; any = true; }
-      if (!GLL || q == 0) { R = any ? fma(smT[warp][lec][0][v][p], T.gLy[q], R)
-                                    : smT[warp][lec][0][v][p] * T.gLy[q]; any = true; }
+      if (!GLL || p == N) { R = sxm[r][cc + 1][q][v] * T.gRx[p]; any = true; }
+      if (!GLL || p == 0) {
+        R = any ? fma(sxp[r][cc][q][v], T.gLx[p], R) : sxp[r][cc][q][v] * T.gLx[p];
+        any = true;
+      }
+      if (!GLL || q == N) {
+        R = any ? fma(sym[r + 1][cc][p][v], T.gRy[q], R) : sym[r + 1][cc][p][v] * T.gRy[q];
+        any = true;
+      }
+      if (!GLL || q == 0) {
+        R = any ? fma(syp[r][cc][p][v], T.gLy[q], R) : syp[r][cc][p][v] * T.gLy[q];
+        any = true;
+      }
       const double w = L.w[(v * Ne + ge) * nn + q * n + p];
       out[v][p] = any ? fma(-dt, R, w) : w;
     }
@@ -389,22 +393,22 @@ __global__ void __launch_bounds__(kBlock2D) k_face_2d(const Launch2D L) {
       for (int p = 1; p < n; ++p) s = fma(T.w[p], out[v][p], s);
       m[v] = T.w[q] * s;
     }
-    // sum over the n rows of the element (lanes le*n .. le*n+n-1)
+    // sum over the n rows of the element (lanes c*n .. c*n+n-1), rows in order
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
       double s = m[v];
 #pragma unroll
       for (int k = 1; k < n; ++k) {
-        const int src = le * n + ((q + k) % n);
+        const int src = c * n + ((q + k) % n);
         s += __shfl_sync(0xffffffffu, m[v], src < 32 ? src : lane);
       }
       m[v] = s;
     }
     double rate = 0.0;
     if (active && q == 0) {
-      const double r = drcp(m[0]);
-      const double c = sqrt(T.gravity * m[0]);
-      rate = fma(fabs(m[1] * r) + c, T.inv_dx, (fabs(m[2] * r) + c) * T.inv_dy);
+      const double rr = drcp(m[0]);
+      const double cs = dsqrt_pos(T.gravity * m[0]);
+      rate = fma(fabs(m[1] * rr) + cs, T.inv_dx, (fabs(m[2] * rr) + cs) * T.inv_dy);
     }
     block_max_atomic<kBlock2D>(rate, &L.st->rate[L.ctl.slot_write]);
   }
@@ -433,7 +437,7 @@ __global__ void __launch_bounds__(kBlock2D) k_rate_2d(const Launch2D L, int slot
       m[v] = s;
     }
     const double r = drcp(m[0]);
-    const double c = sqrt(T.gravity * m[0]);
+    const double c = dsqrt_pos(T.gravity * m[0]);
     rate = fma(fabs(m[1] * r) + c, T.inv_dx, (fabs(m[2] * r) + c) * T.inv_dy);
   }
   block_max_atomic<kBlock2D>(rate, &L.st->rate[slot]);
@@ -503,10 +507,13 @@ int launch_local_t(const Launch2D& L, cudaStream_t s) {
 
 template <int N, bool GLL>
 int launch_face_t(const Launch2D& L, cudaStream_t s) {
+  constexpr int TX = 32 / (N + 1);
+  const dim3 grid((unsigned)((L.Ex + TX - 1) / TX), (unsigned)((L.Ey + kWarps2D - 1) / kWarps2D));
+  if (grid.y > 65535u) return (int)cudaErrorInvalidConfiguration;
   if (L.ctl.residual)
-    k_face_2d<N, GLL, true><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+    k_face_2d<N, GLL, true><<<grid, kBlock2D, 0, s>>>(L);
   else
-    k_face_2d<N, GLL, false><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+    k_face_2d<N, GLL, false><<<grid, kBlock2D, 0, s>>>(L);
   return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,40 @@
+"""The kernels replace the IEEE FP64 division 1/h and square root sqrt(g h)
+by their own routines (FP32 seed from the bit pattern, one third-order
+refinement).  Their error against the correctly rounded result must stay
+within one ulp over the range the path uses and far beyond it."""
+import numpy as np
+import pytest
+
+from gpu_common import load, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def crk():
+    return load()
+
+
+def ulps(got, want):
+    return np.abs(got - want) / np.spacing(np.abs(want))
+
+
+def samples():
+    rng = np.random.default_rng(5)
+    a = np.exp(rng.uniform(np.log(1e-30), np.log(1e30), 200000))
+    b = rng.uniform(0.05, 3.0, 200000)               # depths of the workloads
+    c = np.array([1.0, 2.0, 0.5, 0.1, 9.81, 1e-300, 1e300, 3.0e38, 1.1e-38])
+    return np.concatenate([a, b, c])
+
+
+def test_reciprocal_within_one_ulp(crk):
+    x = samples()
+    x = np.concatenate([x, -x])
+    got = to_host(crk.math_check(to_dev(x), "rcp"))
+    assert np.max(ulps(got, 1.0 / x)) <= 1.0
+
+
+def test_sqrt_within_one_ulp(crk):
+    x = samples()
+    got = to_host(crk.math_check(to_dev(x), "sqrt"))
+    assert np.max(ulps(got, np.sqrt(x))) <= 1.0
