@@ -192,6 +192,41 @@ crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches,
 crkfr_status crkfr_math_check(const double* x_dev, double* out_dev, int64_t n, int32_t op,
                               void* stream);
 
+/* crkfr_step_1d_noalloc: crkfr_step for a 1D system without any device
+ * memory allocation.  The paper has no counterpart to this entry point; it
+ * concerns memory handling only.
+ *
+ * Some callers cannot let a library call cudaMalloc: applications that hand
+ * out all device memory from their own pool and forbid allocations behind
+ * their back, and stepping loops that may not pay the device-wide
+ * synchronisation an allocation or a free can cause.  crkfr_step needs a
+ * context whose crkfr_set_mesh allocates buffers.  This entry point instead
+ * keeps everything it needs besides the caller's input and output (the
+ * static coefficient terms, the second state buffer, the stepping state) in
+ * one static device array of 2^21 doubles (16 MiB), which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc,
+ * no cudaFree and no allocating library routine, and launches the same
+ * kernels as crkfr_step.
+ *
+ * cfg: as for crkfr_create (CRKFR_SYS_VARADV_1D or CRKFR_SYS_SWE_1D);
+ * a uniform periodic mesh of n_elem elements on [lo, hi]; c_dev: the
+ * coefficient field [elem][p]; u_in_dev, u_out_dev: the state
+ * [var][elem][p], the same buffer or not overlapping at all; dt > 0: fixed
+ * step, dt <= 0: the step of Sec. 5, Eq. time.step.2d recomputed before
+ * every step; nsteps >= 0 (0 copies u_in to u_out).
+ * Limit: n_elem * (N+1) * (vars + 1) + 2 n_elem (plus alignment) must fit
+ * the array, e.g. about 123,000 elements for shallow water at N = 4;
+ * larger meshes return CRKFR_ERR_ARG without touching the GPU.
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and the array
+ * keeps the last call's contents (each call clears what must start at zero),
+ * so calls that overlap on the GPU (other streams, other host threads) race.
+ * Asynchronous on `stream`. */
+crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n_elem, double lo, double hi,
+                                   const double* c_dev, const double* u_in_dev, double* u_out_dev,
+                                   double dt, int64_t nsteps, void* stream);
+
 /* Static strings. */
 const char* crkfr_error_string(crkfr_status status);
 const char* crkfr_last_error(const crkfr_ctx* ctx);

@@ -65,6 +65,8 @@ SIGNATURES = {
     "crkfr_profile_enable": (_I32, [_P, _I32]),
     "crkfr_profile_read": (_I32, [_P, _I32, _PI64, _PD]),
     "crkfr_math_check": (_I32, [_P, _P, _I64, _I32, _P]),
+    "crkfr_step_1d_noalloc": (_I32, [ctypes.POINTER(Config), _I64, _D, _D, _P, _P, _P, _D, _I64,
+                                     _P]),
     "crkfr_error_string": (ctypes.c_char_p, [_I32]),
     "crkfr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -108,6 +110,19 @@ def math_check(x, op):
     if st != CRKFR_OK:
         raise CrkfrError(st, lib().crkfr_error_string(st).decode())
     return out
+
+
+def step_1d_noalloc(system, degree, n_elem, lo, hi, c, u_in, u_out, dt=0.0, nsteps=1,
+                    nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0):
+    """crkfr_step_1d_noalloc: 1D steps whose scratch lives in the library's
+    static device array, for callers that cannot allocate device memory."""
+    cfg = Config(SYSTEMS[system], degree, NODES[nodes], 0, gravity, cfl_safety, cfl_number)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = lib().crkfr_step_1d_noalloc(ctypes.byref(cfg), int(n_elem), float(lo), float(hi), ptr(c),
+                                     ptr(u_in), ptr(u_out), float(dt), int(nsteps), _stream())
+    if st != CRKFR_OK:
+        raise CrkfrError(st, lib().crkfr_error_string(st).decode())
+    return u_out
 
 
 class Solver:
