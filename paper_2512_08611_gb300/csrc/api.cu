@@ -356,26 +356,8 @@ crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, co
   }
   const double dx = (c->hi[0] - c->lo[0]) / (double)Ex;
   const double dy = (c->hi[1] - c->lo[1]) / (double)Ey;
-  Tables& T = c->tab;
-  std::memset(&T, 0, sizeof(T));
-  const HostBasis& b = c->basis;
-  for (int i = 0; i < n; ++i) {
-    for (int j = 0; j < n; ++j) {
-      T.Dx[i][j] = b.D[i][j] / dx;
-      T.Dy[i][j] = b.D[i][j] / dy;
-    }
-    T.l0[i] = b.l0[i];
-    T.l1[i] = b.l1[i];
-    T.gRx[i] = 0.5 * b.gR[i] / dx;
-    T.gLx[i] = 0.5 * b.gL[i] / dx;
-    T.gRy[i] = 0.5 * b.gR[i] / dy;
-    T.gLy[i] = 0.5 * b.gL[i] / dy;
-    T.w[i] = b.w[i];
-  }
-  T.inv_dx = 1.0 / dx;
-  T.inv_dy = dim == 2 ? 1.0 / dy : 0.0;
-  T.gravity = c->cfg.system == CRKFR_SYS_VARADV_1D ? 0.0 : c->cfg.gravity;
-  T.half_gravity = 0.5 * T.gravity;
+  fill_tables(c->basis, dx, dim == 2 ? dy : 0.0,
+              c->cfg.system == CRKFR_SYS_VARADV_1D ? 0.0 : c->cfg.gravity, &c->tab);
 
   size_t sn, sf;
   if (dim == 1) {

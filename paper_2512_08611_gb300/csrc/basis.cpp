@@ -191,6 +191,30 @@ bool build_basis(int N, bool gll, HostBasis* out) {
   return true;
 }
 
+void fill_tables(const HostBasis& b, double dx, double dy, double gravity, Tables* T) {
+  std::memset(T, 0, sizeof(*T));
+  const int n = b.n;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      T->Dx[i][j] = b.D[i][j] / dx;
+      T->Dy[i][j] = dy > 0.0 ? b.D[i][j] / dy : 0.0;
+    }
+    T->l0[i] = b.l0[i];
+    T->l1[i] = b.l1[i];
+    T->gRx[i] = 0.5 * b.gR[i] / dx;
+    T->gLx[i] = 0.5 * b.gL[i] / dx;
+    T->gRy[i] = dy > 0.0 ? 0.5 * b.gR[i] / dy : 0.0;
+    T->gLy[i] = dy > 0.0 ? 0.5 * b.gL[i] / dy : 0.0;
+    T->w[i] = b.w[i];
+  }
+  T->inv_dx = 1.0 / dx;
+  T->inv_dy = dy > 0.0 ? 1.0 / dy : 0.0;
+  T->gravity = gravity;
+  T->half_gravity = 0.5 * gravity;
+  T->b0 = tab_b(b.N, 0);
+  T->face_g = gravity / T->b0;
+}
+
 namespace {
 
 bool stable_at(const HostBasis& b, double nu, double tau) {

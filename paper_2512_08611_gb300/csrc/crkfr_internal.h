@@ -26,6 +26,11 @@ struct Tables {
   double w[kMaxNodes];              // quadrature weights
   double inv_dx, inv_dy;
   double gravity, half_gravity;
+  // The kernels accumulate time averages with the weights b_i / b_0 (so the
+  // first stage is a copy); b_0 multiplies dt instead, and the fluctuation
+  // term, which is not a time average, uses g / b_0.
+  double b0;
+  double face_g;   // g / b_0
 };
 
 // Device-resident stepping state of a context.
@@ -65,6 +70,8 @@ struct HostBasis {
 // basis.cpp
 bool build_basis(int N, bool gll, HostBasis* out);
 double von_neumann_cfl(const HostBasis& b);
+// Kernel tables for a uniform mesh (dy ignored in 1D, pass 0).
+void fill_tables(const HostBasis& b, double dx, double dy, double gravity, Tables* T);
 
 // Launchers (kernels_1d.cu / kernels_2d.cu).  Return cudaError_t as int.
 struct Launch1D {

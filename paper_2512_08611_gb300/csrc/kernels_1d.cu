@@ -95,10 +95,13 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
   const double c_l = L.sface[2 * e], c_r = L.sface[2 * e + 1];
 
   // ---- inner stages (element-local) ----------------------------------------
+  // Time averages are accumulated with the weights b_j / b_0 (the first
+  // stage is a copy); b_0 is applied to dt in the update, and the
+  // fluctuation, the one face term that is not a time average, uses g / b_0.
   double Ls[S][M][n];      // local operator at each stage
-  double V[M][n];          // sum_j b_j L_j   (= dloc F + Bloc)
-  double U[M][n];          // sum_j b_j u^(j) (time-averaged solution)
-  double F2[n];            // sum_j b_j f_2(u^(j)) (shallow water momentum flux)
+  double V[M][n];          // sum_j (b_j/b_0) L_j   (= (dloc F + Bloc) / b_0)
+  double U[M][n];          // sum_j (b_j/b_0) u^(j) (time-averaged solution / b_0)
+  double F2[n];            // sum_j (b_j/b_0) f_2(u^(j)) (shallow water momentum flux)
 #pragma unroll
   for (int i = 0; i < S; ++i) {
     double cur[M][n];
@@ -132,10 +135,10 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
         Ls[i][0][p] = a0;
         Ls[i][1][p] = a1;
       }
-      const double bi = tab_b(N, i);
-      if (bi != 0.0) {
+      const double wi = tab_b(N, i) / tab_b(N, 0);
+      if (wi != 0.0) {
 #pragma unroll
-        for (int p = 0; p < n; ++p) F2[p] = (i == 0) ? bi * f2[p] : fma(bi, f2[p], F2[p]);
+        for (int p = 0; p < n; ++p) F2[p] = (i == 0) ? f2[p] : fma(wi, f2[p], F2[p]);
       }
     } else {
 #pragma unroll
@@ -146,14 +149,14 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
         Ls[i][0][p] = sn[p] * a0;
       }
     }
-    const double bi = tab_b(N, i);
-    if (bi != 0.0) {
+    const double wi = tab_b(N, i) / tab_b(N, 0);
+    if (wi != 0.0) {
 #pragma unroll
       for (int v = 0; v < M; ++v)
 #pragma unroll
         for (int p = 0; p < n; ++p) {
-          V[v][p] = (i == 0) ? bi * Ls[i][v][p] : fma(bi, Ls[i][v][p], V[v][p]);
-          U[v][p] = (i == 0) ? bi * cur[v][p] : fma(bi, cur[v][p], U[v][p]);
+          V[v][p] = (i == 0) ? Ls[i][v][p] : fma(wi, Ls[i][v][p], V[v][p]);
+          U[v][p] = (i == 0) ? cur[v][p] : fma(wi, cur[v][p], U[v][p]);
         }
     }
   }
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
       // F_h = U_m (the h flux is the momentum)
       const double dFh = Mp - Mm, dUh = Hp - Hm;
       const double dFm = Fp - Fm, dUm = Mp - Mm;
-      const double gdb = T.gravity * (bp - bm);
+      const double gdb = T.face_g * (bp - bm);
       Tm[0] = fma(-lam, dUh, dFh);
       Tm[1] = fma(hm, gdb, fma(-lam, dUm, dFm));
       const double Tp0 = -fma(lam, dUh, dFh);
@@ -219,6 +222,8 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
     double Tp[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) Tp[v] = sm_T[v][t];
+    constexpr double b0 = tab_b(N, 0);
+    const double dtb0 = dt * b0;
     double out[M][n];
 #pragma unroll
     for (int v = 0; v < M; ++v)
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
         double R = V[v][p];
         if (!GLL || p == N) R = fma(Tm[v], T.gRx[p], R);
         if (!GLL || p == 0) R = fma(Tp[v], T.gLx[p], R);
-        out[v][p] = RES ? -R : fma(-dt, R, u0[v][p]);
+        out[v][p] = RES ? -b0 * R : fma(-dtb0, R, u0[v][p]);
         L.u_out[((int64_t)v * E + e) * n + p] = out[v][p];
       }
     if (!RES) {

@@ -38,6 +38,17 @@ namespace {
 
 constexpr int kBlock2D = 256;
 constexpr int kWarps2D = kBlock2D / 32;
+// Launch shape of the element-local kernel: FP64 issue needs enough warps
+// in flight, so the block is small and at least CRKFR_LOCAL2D_MINB blocks
+// must fit an SM (the compiler caps the registers accordingly).
+#ifndef CRKFR_LOCAL2D_BLOCK
+#define CRKFR_LOCAL2D_BLOCK 128
+#endif
+#ifndef CRKFR_LOCAL2D_MINB
+#define CRKFR_LOCAL2D_MINB 2
+#endif
+constexpr int kBlockLocal = CRKFR_LOCAL2D_BLOCK;
+constexpr int kWarpsLocal = kBlockLocal / 32;
 constexpr int kTrFields = 7;
 // x-face trace fields: U_h, U_hu, U_hv, F_hu, F_hv (time-averaged x fluxes of
 // hu and hv), h^n, hu^n.  y-face trace fields: U_h, U_hu, U_hv, G_hu, G_hv,
@@ -48,19 +59,19 @@ __device__ __forceinline__ double swe_speed(double h, double m, double g) {
 }
 
 template <int N, bool GLL, bool RES>
-__global__ void __launch_bounds__(kBlock2D) k_local_2d(const Launch2D L) {
+__global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(const Launch2D L) {
   constexpr int n = N + 1;
   constexpr int nn = n * n;
   constexpr int EPW = 32 / n;          // elements per warp
   constexpr int S = tab_stages(N);
   constexpr int NB = 4;                // fields per shared-memory exchange round
   const Tables& T = L.tab;
-  __shared__ double sm[kWarps2D][EPW][NB][n][n];
+  __shared__ double sm[kWarpsLocal][EPW][NB][n][n];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int le = lane / n, q = lane - le * n;
   const int64_t Ne = L.Ex * L.Ey;
-  const int64_t g = ((int64_t)blockIdx.x * kWarps2D + warp) * EPW + le;
+  const int64_t g = ((int64_t)blockIdx.x * kWarpsLocal + warp) * EPW + le;
   // lanes past EPW*n (n = 3, 5) and lanes past the last element compute on
   // element 0 and store nothing, neither to memory nor to shared memory
   const bool lane_ok = le < EPW;
@@ -143,30 +154,34 @@ __global__ void __launch_bounds__(kBlock2D) k_local_2d(const Launch2D L) {
       Ls[i][1][p] = a1;
       Ls[i][2][p] = a2;
     }
-    const double bi = tab_b(N, i);
-    if (bi != 0.0) {
+    // time averages with the weights b_i / b_0 (first stage: a copy)
+    const double wi = tab_b(N, i) / tab_b(N, 0);
+    if (wi != 0.0) {
 #pragma unroll
       for (int p = 0; p < n; ++p) {
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          V[v][p] = (i == 0) ? bi * Ls[i][v][p] : fma(bi, Ls[i][v][p], V[v][p]);
-          U[v][p] = (i == 0) ? bi * cur[v][p] : fma(bi, cur[v][p], U[v][p]);
+          V[v][p] = (i == 0) ? Ls[i][v][p] : fma(wi, Ls[i][v][p], V[v][p]);
+          U[v][p] = (i == 0) ? cur[v][p] : fma(wi, cur[v][p], U[v][p]);
         }
-        F2[p] = (i == 0) ? bi * f2[p] : fma(bi, f2[p], F2[p]);
-        F3[p] = (i == 0) ? bi * f3[p] : fma(bi, f3[p], F3[p]);
-        G3[p] = (i == 0) ? bi * g3[p] : fma(bi, g3[p], G3[p]);
+        F2[p] = (i == 0) ? f2[p] : fma(wi, f2[p], F2[p]);
+        F3[p] = (i == 0) ? f3[p] : fma(wi, f3[p], F3[p]);
+        G3[p] = (i == 0) ? g3[p] : fma(wi, g3[p], G3[p]);
       }
     }
   }
   static_assert(tab_b(N, 0) != 0.0, "accumulators are initialised by the first stage");
 
   // ---- W = u^n - dt (dloc F + Bloc)  (or -(dloc F + Bloc) for the residual) --
+  // (V holds the time averages divided by b_0)
+  constexpr double b0 = tab_b(N, 0);
+  const double dtb0 = dt * b0;
   if (active) {
 #pragma unroll
     for (int v = 0; v < 3; ++v)
 #pragma unroll
       for (int p = 0; p < n; ++p)
-        L.w[(v * Ne + ge) * nn + q * n + p] = RES ? -V[v][p] : fma(-dt, V[v][p], u0[v][p]);
+        L.w[(v * Ne + ge) * nn + q * n + p] = RES ? -b0 * V[v][p] : fma(-dtb0, V[v][p], u0[v][p]);
   }
 
   // ---- x-face traces of row q -------------------------------------------------
@@ -293,7 +308,8 @@ __global__ void __launch_bounds__(kBlock2D) k_face_2d(const Launch2D L) {
 
   const int64_t Ex = L.Ex, Ey = L.Ey, Ne = Ex * Ey, ts = Ne * n;
   const int64_t ex0 = (int64_t)blockIdx.x * TX, ey0 = (int64_t)blockIdx.y * TY;
-  const double dt = RES ? 1.0 : L.st->dt_cur;
+  // the traces hold time averages divided by b_0: so do the face terms
+  const double dt = (RES ? 1.0 : L.st->dt_cur) * tab_b(N, 0);
 
   // ---- phase 1: every face node of the tile once --------------------------
   for (int f = threadIdx.x; f < NX + NY; f += kBlock2D) {
@@ -444,7 +460,7 @@ __global__ void __launch_bounds__(kBlock2D) k_rate_2d(const Launch2D L, int slot
 }
 
 // Static terms from the bathymetry: g b_x, g b_y at the nodes and
-// g (b+ - b-) at the left x-face and bottom y-face of each element.
+// (g / b_0)(b+ - b-) at the left x-face and bottom y-face of each element.
 template <int N, bool GLL>
 __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c,
                           double* __restrict__ snode, double* __restrict__ sface, const Tables T) {
@@ -472,7 +488,7 @@ __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c,
         dy = fma(T.Dy[q][j], b[j][p], dy);
       }
       snode[e * nn + q * n + p] = T.gravity * dx;
-      snode[(Ne + e) * nn + q * n + p] = T.gravity * dy;
+      snode[(Ne + e) * nn + q * n + p] = T.gravity * dy;   // local term: g, not g / b_0
     }
   // own left/bottom traces and the neighbours' right/top traces
 #pragma unroll
@@ -485,23 +501,21 @@ __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c,
       nb_r = fma(T.l1[j], c[eL * nn + k * n + j], nb_r);
       nb_t = fma(T.l1[j], c[eB * nn + j * n + k], nb_t);
     }
-    sface[e * n + k] = T.gravity * (own_l - nb_r);
-    sface[(Ne + e) * n + k] = T.gravity * (own_b - nb_t);
+    // fluctuations meet time averages divided by b_0 in the face terms
+    sface[e * n + k] = T.face_g * (own_l - nb_r);
+    sface[(Ne + e) * n + k] = T.face_g * (own_b - nb_t);
   }
 }
 
 template <int N, bool GLL>
-unsigned blocks_2d(const Launch2D& L) {
-  constexpr int per_block = kWarps2D * (32 / (N + 1));
-  return (unsigned)((L.Ex * L.Ey + per_block - 1) / per_block);
-}
-
-template <int N, bool GLL>
 int launch_local_t(const Launch2D& L, cudaStream_t s) {
+  constexpr int per_block = kWarpsLocal * (32 / (N + 1));
+  const int64_t blocks = (L.Ex * L.Ey + per_block - 1) / per_block;
+  if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
   if (L.ctl.residual)
-    k_local_2d<N, GLL, true><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+    k_local_2d<N, GLL, true><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
   else
-    k_local_2d<N, GLL, false><<<blocks_2d<N, GLL>(L), kBlock2D, 0, s>>>(L);
+    k_local_2d<N, GLL, false><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
   return (int)cudaGetLastError();
 }
 

@@ -92,19 +92,8 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
   }
 
   Tables T;
-  std::memset(&T, 0, sizeof(T));
-  const double dx = (hi - lo) / (double)E;
-  for (int i = 0; i < n; ++i) {
-    for (int j = 0; j < n; ++j) T.Dx[i][j] = b.D[i][j] / dx;
-    T.l0[i] = b.l0[i];
-    T.l1[i] = b.l1[i];
-    T.gRx[i] = 0.5 * b.gR[i] / dx;
-    T.gLx[i] = 0.5 * b.gL[i] / dx;
-    T.w[i] = b.w[i];
-  }
-  T.inv_dx = 1.0 / dx;
-  T.gravity = cfg->system == CRKFR_SYS_VARADV_1D ? 0.0 : cfg->gravity;
-  T.half_gravity = 0.5 * T.gravity;
+  fill_tables(b, (hi - lo) / (double)E, 0.0,
+              cfg->system == CRKFR_SYS_VARADV_1D ? 0.0 : cfg->gravity, &T);
 
   // the array keeps the previous call's contents: reset the stepping state
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CRKFR_ERR_CUDA;

@@ -1,0 +1,65 @@
+"""Domain decomposition of the 2D step across ranks (torch.distributed).
+
+The mesh is split into horizontal slabs of element rows, one per rank, on a
+periodic ring: rank r's slab lies between rank r-1 (below) and rank r+1
+(above).  The only inter-element coupling of a cRK-FR step is one Riemann
+problem per face after the element-local stages (Sec. 3), so a step needs one
+exchange: after the local phase each rank sends the face traces of its bottom
+element row (their bottom side) to the rank below, which stores them as its
+top halo, and those of its top row (their top side) to the rank above, which
+stores them as its bottom halo.  The face phase then runs on every rank with
+no further communication.  This module holds only that exchange; the
+arithmetic stays in the library.
+"""
+import torch
+import torch.distributed as dist
+
+TAG_UP, TAG_DOWN = 7101, 7102
+
+
+def neighbours(rank, world):
+    """(below, above) ranks on the periodic ring."""
+    return (rank - 1) % world, (rank + 1) % world
+
+
+def halo_exchange(send_bottom, send_top, recv_bottom, recv_top, group=None):
+    """Exchange the slab-boundary traces with the two ring neighbours.
+
+    send_bottom: traces of this slab's bottom row (bottom side), goes to the
+                 rank below and becomes its ``recv_top``;
+    send_top:    traces of this slab's top row (top side), goes to the rank
+                 above and becomes its ``recv_bottom``.
+    With one rank the slab is its own neighbour (periodic)."""
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    if world == 1:
+        recv_top.copy_(send_bottom)
+        recv_bottom.copy_(send_top)
+        return
+    rank = dist.get_rank(group)
+    below, above = neighbours(rank, world)
+    ops = [dist.P2POp(dist.isend, send_top, above, group, TAG_UP),
+           dist.P2POp(dist.irecv, recv_bottom, below, group, TAG_UP),
+           dist.P2POp(dist.isend, send_bottom, below, group, TAG_DOWN),
+           dist.P2POp(dist.irecv, recv_top, above, group, TAG_DOWN)]
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()
+
+
+def slab_rows(global_rows, rank, world):
+    """(first row, row count) of a rank's slab: contiguous, sizes differ by at
+    most one."""
+    base, extra = divmod(global_rows, world)
+    count = base + (1 if rank < extra else 0)
+    first = rank * base + min(rank, extra)
+    return first, count
+
+
+def max_over_ranks(x):
+    """Max of a float over ranks (for the time step of Eq. time.step.2d the
+    ranks need the global maximum wave-speed rate)."""
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())

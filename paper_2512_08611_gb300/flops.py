@@ -8,14 +8,16 @@ nnz_i nonzero entries a_ij in row i):
                                     (hu)^2/h + p, (hv)^2/h + p: FMA)
   local operator   3 MUL + (6n - 1) FMA  (D_x and D_y chains of the three
                                           variables, g h b_x and g h b_y)
-  time averages    9 FMA if b_i != 0 (MUL at the first stage): V (3), U (3),
-                   two x-fluxes and one y-flux of the momenta
+  time averages    9 FMA if b_i != 0 (a copy at the first stage, the
+                   weights being b_i / b_0): V (3), U (3), two x-fluxes and
+                   one y-flux of the momenta
 and per node W = u - dt V: 3 FMA; per element row and face side, for each of
 7 trace fields: 1 MUL + (n - 1) FMA, in x and in y (GL nodes).
 
 Fused 1D kernel (shallow water, per node and stage): stage value 2 nnz_i FMA,
 flux 4 FMA + 2 MUL, local operator 2 MUL + (2n - 1) FMA, time averages
-5 FMA if b_i != 0 (V 2, U 2, F 1); per node the update 2 FMA + 1 FMA and the
+5 FMA if b_i != 0 (a copy at the first stage; V 2, U 2, F 1); per node the
+update 2 FMA + 1 FMA and the
 traces 5 fields x 2 sides x (1 MUL + (n - 1) FMA) per element.
 """
 import numpy as np
@@ -34,11 +36,8 @@ def local_flops_per_element(system, N):
         for i, (k, bz) in enumerate(zip(nnz, bnz)):
             fma += 3 * k + 5 + (6 * n - 1)
             mul += 5 + 3
-            if bz:
-                if i == 0:
-                    mul += 9
-                else:
-                    fma += 9
+            if bz and i > 0:
+                fma += 9
         fma += 3
         per_node = 2 * fma + mul
         traces = 2 * n * 7 * 2 * (1 + 2 * (n - 1))   # x and y, n rows, 7 fields, 2 sides
@@ -47,11 +46,8 @@ def local_flops_per_element(system, N):
         for i, (k, bz) in enumerate(zip(nnz, bnz)):
             fma += 2 * k + 4 + (2 * n - 1)
             mul += 2 + 2
-            if bz:
-                if i == 0:
-                    mul += 5
-                else:
-                    fma += 5
+            if bz and i > 0:
+                fma += 5
         fma += 3
         per_node = 2 * fma + mul
         traces = 5 * 2 * (1 + 2 * (n - 1))

@@ -1,0 +1,151 @@
+"""The domain-decomposed 2D step on CPU ranks (gloo, world sizes 2 and 3).
+
+1. halo_exchange sends each slab's bottom/top boundary traces to the right
+   ring neighbours.
+2. A step split over ranks — element-local phase per slab, one halo
+   exchange, face phase per slab — reproduces the single-domain step
+   bitwise.  The arithmetic here is the oracle's (CPU); the exchange is the
+   product's (paper_2512_08611_gb300.distributed)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _init(rank, world, port):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+
+
+def _worker_exchange(rank, world, port, out):
+    from paper_2512_08611_gb300.distributed import halo_exchange, neighbours
+    _init(rank, world, port)
+    sb = torch.full((5,), 10.0 * rank + 1, dtype=torch.float64)
+    st = torch.full((5,), 10.0 * rank + 2, dtype=torch.float64)
+    rb, rt = torch.zeros(5, dtype=torch.float64), torch.zeros(5, dtype=torch.float64)
+    halo_exchange(sb, st, rb, rt)
+    below, above = neighbours(rank, world)
+    ok = bool(torch.all(rt == 10.0 * above + 1)) and bool(torch.all(rb == 10.0 * below + 2))
+    out[rank] = ok
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_halo_exchange_ring(world):
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_exchange, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert all(out[r] for r in range(world))
+
+
+def _case(Ey, Ex, N, seed=3):
+    from oracle.basis import Basis
+    rng = np.random.default_rng(seed)
+    bs = Basis(N)
+    L = 10.0
+    dx, dy = L / Ex, L / Ey
+    x = (np.arange(Ex)[None, :, None, None] + bs.xi[None, None, None, :]) * dx
+    y = (np.arange(Ey)[:, None, None, None] + bs.xi[None, None, :, None]) * dy
+    x, y = np.broadcast_arrays(x, y)
+    b = 0.2 * np.exp(-((x - 4) ** 2 + (y - 6) ** 2) / 3.0)
+    u = np.stack([1.0 - b + 0.01 * rng.standard_normal(x.shape),
+                  0.1 * np.sin(2 * np.pi * y / L), 0.1 * np.cos(2 * np.pi * x / L)])
+    return u, b, dx, dy
+
+
+def _split_step(sch, u_slab, c_slab, dt):
+    """One step of a slab: local phase, halo exchange of the y-boundary face
+    traces, face phase (oracle arithmetic, product exchange)."""
+    from paper_2512_08611_gb300.distributed import halo_exchange
+    loc = sch.local(u_slab, c_slab, dt)
+    ax_y, ax_x = -3, -2
+    bot_keys = ("G_b", "U_b", "un_b", "c_b")
+    top_keys = ("G_t", "U_t", "un_t", "c_t")
+    pack = lambda keys, row: torch.from_numpy(np.concatenate(
+        [np.ascontiguousarray(np.take(loc[k], row, axis=ax_y)).ravel() for k in keys]))
+    Ey = u_slab.shape[1]
+    send_bottom, send_top = pack(bot_keys, 0), pack(top_keys, Ey - 1)
+    recv_bottom, recv_top = torch.empty_like(send_top), torch.empty_like(send_bottom)
+    halo_exchange(send_bottom, send_top, recv_bottom, recv_top)
+
+    def unpack(buf, keys):
+        out, off = {}, 0
+        for k in keys:
+            shape = np.take(loc[k], 0, axis=ax_y).shape
+            size = int(np.prod(shape))
+            out[k] = buf[off:off + size].numpy().reshape(shape)
+            off += size
+        return out
+    halo_below = unpack(recv_bottom, top_keys)   # top-side traces of the row below
+    halo_above = unpack(recv_top, bot_keys)      # bottom-side traces of the row above
+
+    xm = {k: np.roll(loc[k], 1, axis=ax_x) for k in ("F_r", "U_r", "un_r", "c_r")}
+    xp = {k: loc[k] for k in ("F_l", "U_l", "un_l", "c_l")}
+    Txm, Txp, _ = sch._xface(xm, xp)
+    # y faces: face k between row k-1 and row k, k = 0..Ey (0 and Ey use halos)
+    ym = {k: np.concatenate([np.expand_dims(halo_below[k], ax_y), loc[k]], axis=ax_y)
+          for k in top_keys}
+    yp = {k: np.concatenate([loc[k], np.expand_dims(halo_above[k], ax_y)], axis=ax_y)
+          for k in bot_keys}
+    Tym, Typ, _ = sch._yface(ym, yp)
+    Tr = np.roll(Txm, -1, axis=ax_x)
+    Tt = np.take(Tym, np.arange(1, Ey + 1), axis=ax_y)
+    Tb = np.take(Typ, np.arange(0, Ey), axis=ax_y)
+    return u_slab - dt * (loc["vol"] + sch._corrections(Tr, Txp, Tt, Tb))
+
+
+def _worker_step(rank, world, port, out):
+    from oracle.crkfr import Scheme2D
+    from oracle.systems import ShallowWater2D
+    from paper_2512_08611_gb300.distributed import slab_rows
+    _init(rank, world, port)
+    N, Ey, Ex = 2, 7, 5
+    u, b, dx, dy = _case(Ey, Ex, N)
+    sch = Scheme2D(ShallowWater2D(9.81), N, dx, dy)
+    first, count = slab_rows(Ey, rank, world)
+    rows = slice(first, first + count)
+    got = _split_step(sch, u[:, rows], b[rows], 0.004)
+    want = sch.step(u, b, 0.004)[:, rows]
+    out[rank] = (bool(np.array_equal(got, want)), float(np.max(np.abs(got - want))))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_step_equals_single_domain(world):
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_step, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert out[r][0], out[r]
+
+
+def test_slab_rows_cover_the_mesh():
+    from paper_2512_08611_gb300.distributed import slab_rows
+    for G in (1, 7, 1024):
+        for W in (1, 2, 3, 8):
+            parts = [slab_rows(G, r, W) for r in range(W)]
+            assert sum(c for _, c in parts) == G
+            assert all(parts[i][0] + parts[i][1] == parts[i + 1][0] for i in range(W - 1))
