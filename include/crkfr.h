@@ -154,6 +154,39 @@ crkfr_status crkfr_advance(crkfr_ctx* ctx, double* u_dev, double t_end, int64_t 
 crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_out_host,
                              double dt, int64_t nsteps, void* stream);
 
+/* Domain decomposition of the 2D step into horizontal slabs (one per rank
+ * or per GPU).  The only coupling of a cRK-FR step across the slab boundary
+ * is the face Riemann problem after the element-local stages (Sec. 3), so a
+ * step of a slab is: crkfr_step_local; exchange of one block of face traces
+ * with each neighbour; crkfr_step_faces.
+ *
+ * crkfr_set_subdomain(ctx, 1), after crkfr_set_mesh and before
+ * crkfr_set_coefficients, makes the context's mesh (Ex x Ey_local, periodic
+ * in x) one slab of a mesh that continues above and below.  In this mode
+ * crkfr_set_coefficients expects c with two extra rows,
+ * c[Ey_local + 2][Ex][n][n]: row 0 is the element row below the slab and row
+ * Ey_local + 1 the row above (periodic neighbours at the ends of the whole
+ * mesh).  crkfr_step, crkfr_advance, crkfr_step_host and crkfr_residual
+ * return CRKFR_ERR_STATE; crkfr_compute_dt gives the slab's own step (the
+ * step of the whole mesh is the minimum over slabs).
+ *
+ * crkfr_halo_buffers returns device pointers into the context's trace
+ * buffer, each to `count` contiguous doubles: send_bottom (traces of the
+ * bottom element row, bottom side: the rank below stores them as its
+ * recv_top), send_top (top row, top side: becomes the rank above's
+ * recv_bottom), recv_bottom and recv_top.  The pointers stay valid until the
+ * next crkfr_set_mesh.
+ *
+ * crkfr_step_local runs the element-local kernel with the step dt > 0 and
+ * writes the send blocks; crkfr_step_faces (after recv_bottom and recv_top
+ * have been filled) solves the face problems, applies the corrections and
+ * writes u_dev in place. */
+crkfr_status crkfr_set_subdomain(crkfr_ctx* ctx, int32_t enable);
+crkfr_status crkfr_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** send_top,
+                                double** recv_bottom, double** recv_top, int64_t* count);
+crkfr_status crkfr_step_local(crkfr_ctx* ctx, const double* u_dev, double dt, void* stream);
+crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
+
 /* Simulated time and the size of the last step taken (synchronises). */
 crkfr_status crkfr_get_time(crkfr_ctx* ctx, double* t_host, double* last_dt_host, void* stream);
 

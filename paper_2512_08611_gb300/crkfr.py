@@ -58,6 +58,11 @@ SIGNATURES = {
     "crkfr_step": (_I32, [_P, _P, _D, _I64, _P]),
     "crkfr_advance": (_I32, [_P, _P, _D, _I64, _PI64, _P]),
     "crkfr_step_host": (_I32, [_P, _P, _P, _D, _I64, _P]),
+    "crkfr_set_subdomain": (_I32, [_P, _I32]),
+    "crkfr_halo_buffers": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                  ctypes.POINTER(_P), _PI64]),
+    "crkfr_step_local": (_I32, [_P, _P, _D, _P]),
+    "crkfr_step_faces": (_I32, [_P, _P, _P]),
     "crkfr_get_time": (_I32, [_P, _PD, _PD, _P]),
     "crkfr_set_time": (_I32, [_P, _D, _P]),
     "crkfr_get_status": (_I32, [_P, _P]),
@@ -96,6 +101,14 @@ def _stream():
     if not torch.cuda.is_available():
         return ctypes.c_void_p(0)   # calls that reach CUDA report the error themselves
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class _DeviceBlock:
+    """A library-owned device array exposed to torch without a copy."""
+
+    def __init__(self, ptr, count):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3}
 
 
 def math_check(x, op):
@@ -179,6 +192,32 @@ class Solver:
             self.shape = (self.M, n_elem[1], n_elem[0], n, n)
             self.coef_shape = (n_elem[1], n_elem[0], n, n)
         return self
+
+    def set_subdomain(self, enable=True):
+        """Make the (2D) context one horizontal slab of a larger mesh; the
+        coefficient field then carries one halo row below and one above."""
+        self._check(lib().crkfr_set_subdomain(self.h, 1 if enable else 0))
+        self.subdomain = bool(enable)
+        if self.shape is not None and self.dim == 2:
+            n, (Ex, Ey) = self.n, self.n_elem
+            self.coef_shape = (Ey + 2 if enable else Ey, Ex, n, n)
+
+    def halo_buffers(self):
+        """(send_bottom, send_top, recv_bottom, recv_top) as float64 CUDA
+        tensors viewing the context's trace buffer (no copy)."""
+        import torch
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        cnt = ctypes.c_int64()
+        self._check(lib().crkfr_halo_buffers(self.h, *[ctypes.byref(p) for p in ptrs],
+                                             ctypes.byref(cnt)))
+        return tuple(torch.as_tensor(_DeviceBlock(p.value, cnt.value), device="cuda")
+                     for p in ptrs)
+
+    def step_local(self, u, dt):
+        self._check(lib().crkfr_step_local(self.h, self._dev(u, self.shape), float(dt), _stream()))
+
+    def step_faces(self, u):
+        self._check(lib().crkfr_step_faces(self.h, self._dev(u, self.shape), _stream()))
 
     def nodes(self):
         n = self.n

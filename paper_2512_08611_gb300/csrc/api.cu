@@ -33,6 +33,7 @@ struct crkfr_ctx {
   double* d_stage = nullptr;  // device copy of host state for crkfr_step_host
   DevState* d_state = nullptr;
   bool coef_set = false;
+  bool subdomain = false;   // 2D slab of a larger mesh: halo rows come from outside
   int64_t nstep = 0;
   int64_t launches = 0;
   int device = -1;
@@ -172,6 +173,7 @@ Launch2D make2d(crkfr_ctx* c) {
   L.sface = c->d_sface;
   L.st = c->d_state;
   L.tab = c->tab;
+  L.periodic_y = c->subdomain ? 0 : 1;
   return L;
 }
 
@@ -365,7 +367,7 @@ crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, co
     sf = (size_t)Ne * 2;
   } else {
     sn = (size_t)2 * Ne * n * n;
-    sf = (size_t)2 * Ne * n;
+    sf = (size_t)(2 * Ne + Ex) * n;
   }
   if (cudaMalloc(&c->d_snode, sizeof(double) * sn) != cudaSuccess ||
       cudaMalloc(&c->d_sface, sizeof(double) * sf) != cudaSuccess ||
@@ -376,9 +378,10 @@ crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, co
     return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
   }
   if (dim == 2) {
-    const size_t tr = (size_t)7 * 2 * Ne * n;
-    if (cudaMalloc(&c->d_trx, sizeof(double) * tr) != cudaSuccess ||
-        cudaMalloc(&c->d_try, sizeof(double) * tr) != cudaSuccess) {
+    const size_t trx = (size_t)7 * 2 * Ne * n;
+    const size_t try_ = (size_t)7 * 2 * (Ey + 2) * Ex * n;
+    if (cudaMalloc(&c->d_trx, sizeof(double) * trx) != cudaSuccess ||
+        cudaMalloc(&c->d_try, sizeof(double) * try_) != cudaSuccess) {
       free_buffers(c);
       cudaGetLastError();
       return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
@@ -425,7 +428,7 @@ crkfr_status crkfr_set_coefficients(crkfr_ctx* c, const double* coef, void* stre
       return launch_coef_1d(c->cfg.system, c->cfg.degree, c->Ex, coef, c->d_snode, c->d_sface,
                             c->tab, s);
     return launch_coef_2d(c->cfg.degree, c->cfg.nodes == CRKFR_NODES_GLL, c->Ex, c->Ey, coef,
-                          c->d_snode, c->d_sface, c->tab, s);
+                          c->subdomain, c->d_snode, c->d_sface, c->tab, s);
   });
   if (e) return cuda_fail(c, e, "coefficient kernel");
   c->launches += 1;
@@ -457,6 +460,7 @@ crkfr_status crkfr_compute_dt(crkfr_ctx* c, const double* u, double* dt_host, vo
 crkfr_status crkfr_residual(crkfr_ctx* c, const double* u, double dt, double* r, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
+  if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "subdomain: use crkfr_step_local / faces");
   if (!u || !r) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
   const size_t bytes = sizeof(double) * c->n_state;
@@ -490,6 +494,7 @@ crkfr_status crkfr_residual(crkfr_ctx* c, const double* u, double dt, double* r,
 crkfr_status crkfr_step(crkfr_ctx* c, double* u, double dt, int64_t nsteps, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
+  if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "subdomain: use crkfr_step_local / faces");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (nsteps < 0) return fail(c, CRKFR_ERR_ARG, "nsteps must be >= 0");
   if (!std::isfinite(dt) && dt > 0.0) return fail(c, CRKFR_ERR_ARG, "dt must be finite");
@@ -501,6 +506,7 @@ crkfr_status crkfr_advance(crkfr_ctx* c, double* u, double t_end, int64_t max_st
                            int64_t* steps_taken, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
+  if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "subdomain: use crkfr_step_local / faces");
   if (!u || !std::isfinite(t_end) || max_steps < 0) return fail(c, CRKFR_ERR_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   int64_t done = 0;
@@ -530,6 +536,7 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
                              int64_t nsteps, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
+  if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "subdomain: use crkfr_step_local / faces");
   if (!u_in || !u_out || nsteps < 0) return fail(c, CRKFR_ERR_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = sizeof(double) * c->n_state;
@@ -544,6 +551,76 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
   if (st != CRKFR_OK) return st;
   CK(c, cudaMemcpyAsync(u_out, c->d_stage, bytes, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_set_subdomain(crkfr_ctx* c, int32_t enable) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "subdomains are 2D slabs");
+  c->subdomain = enable != 0;
+  c->coef_set = false;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_halo_buffers(crkfr_ctx* c, double** send_bottom, double** send_top,
+                                double** recv_bottom, double** recv_top, int64_t* count) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim != 2) return fail(c, CRKFR_ERR_STATE, "no 2D mesh set");
+  const int64_t n = c->basis.n;
+  const int64_t block = 7 * c->Ex * n;           // one (row, side) block of the y traces
+  double* base = c->d_try;
+  auto at = [&](int64_t row, int side) { return base + (row * 2 + side) * block; };
+  if (send_bottom) *send_bottom = at(1, 0);       // bottom row, bottom side
+  if (send_top) *send_top = at(c->Ey, 1);         // top row, top side
+  if (recv_bottom) *recv_bottom = at(0, 1);       // halo below: top side of the row below
+  if (recv_top) *recv_top = at(c->Ey + 1, 0);     // halo above: bottom side of the row above
+  if (count) *count = block;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_step_local(crkfr_ctx* c, const double* u, double dt, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "phased steps are 2D");
+  if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  StepCtl ctl{};
+  ctl.dt_fixed = dt;
+  ctl.cs_cfl = c->cfg.cfl_safety * c->cfl;
+  ctl.t_end = std::numeric_limits<double>::infinity();
+  ctl.slot_read = (int)(c->nstep % 3);
+  ctl.slot_write = (int)((c->nstep + 1) % 3);
+  ctl.slot_reset = (int)((c->nstep + 2) % 3);
+  ctl.tslot = (int)(c->nstep % 2);
+  Launch2D L = make2d(c);
+  L.ctl = ctl;
+  L.u_in = u;
+  L.u_out = nullptr;
+  int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
+  if (e) return cuda_fail(c, e, "2D local kernel");
+  c->launches += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "phased steps are 2D");
+  if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  StepCtl ctl{};
+  ctl.dt_fixed = 1.0;   // the face kernel reads the step size the local phase stored
+  ctl.slot_write = (int)((c->nstep + 1) % 3);
+  ctl.want_rate = 0;
+  Launch2D L = make2d(c);
+  L.ctl = ctl;
+  L.u_in = u;
+  L.u_out = u;
+  int e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+  if (e) return cuda_fail(c, e, "2D face kernel");
+  c->launches += 1;
+  c->nstep += 1;
   return CRKFR_OK;
 }
 

@@ -100,9 +100,12 @@ struct Launch2D {
   double* u_out;         // step: may equal u_in
   double* w;             // [3][Ey][Ex][n][n] scratch
   double* trx;           // x-face traces [7][2][Ey][Ex][n]
-  double* try_;          // y-face traces [7][2][Ey][Ex][n]
+  double* try_;          // y-face traces [Ey+2][2][7][Ex][n]: element row r in buffer
+                         // row r+1, halo rows 0 (row below) and Ey+1 (row above)
   const double* snode;   // [2][Ey][Ex][n][n]: g dx b, g dy b
-  const double* sface;   // [2][Ey][Ex][n]: g (b+ - b-) at the left x-face / bottom y-face
+  const double* sface;   // (g/b_0)(b+ - b-): [Ey][Ex][n] at the left x-face of each
+                         // element, then [Ey+1][Ex][n] at the y-face below row k
+  int periodic_y;        // 1: the local kernel fills the halo rows from its own mesh
   DevState* st;
   Tables tab;
   StepCtl ctl;
@@ -110,7 +113,9 @@ struct Launch2D {
 int launch_local_2d(const Launch2D& L, void* stream);
 int launch_face_2d(const Launch2D& L, void* stream);
 int launch_rate_2d(const Launch2D& L, int slot, void* stream);
-int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, double* snode,
-                   double* sface, const Tables& tab, void* stream);
+// c: [Ey][Ex][n][n] (periodic in y) or, with halo_rows, [Ey+2][Ex][n][n]
+// holding the row below and the row above the mesh as rows 0 and Ey+1
+int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, bool halo_rows,
+                   double* snode, double* sface, const Tables& tab, void* stream);
 
 }  // namespace crkfr

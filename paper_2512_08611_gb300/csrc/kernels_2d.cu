@@ -259,8 +259,16 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
               tt = fma(T.l1[j], X[f - r0][j][q], tt);
             }
           }
-          L.try_[(2 * f + 0) * tstride + ge * n + q] = tb;
-          L.try_[(2 * f + 1) * tstride + ge * n + q] = tt;
+          // buffer row ey+1; in a periodic mesh the bottom row's bottom side
+          // is also the halo above the top row, and vice versa
+          const int64_t row = ge / L.Ex + 1, col = ge - (row - 1) * L.Ex;
+          const int64_t plane = L.Ex * n;
+          L.try_[((row * 2 + 0) * kTrFields + f) * plane + col * n + q] = tb;
+          L.try_[((row * 2 + 1) * kTrFields + f) * plane + col * n + q] = tt;
+          if (L.periodic_y && row == 1)
+            L.try_[(((L.Ey + 1) * 2 + 0) * kTrFields + f) * plane + col * n + q] = tb;
+          if (L.periodic_y && row == L.Ey)
+            L.try_[((0 * 2 + 1) * kTrFields + f) * plane + col * n + q] = tt;
         }
       }
     }
@@ -336,14 +344,16 @@ __global__ void __launch_bounds__(kBlock2D) k_face_2d(const Launch2D L) {
       const int p = g % n, c = (g / n) % TX, k = g / (n * TX);
       const int64_t ex = ex0 + c;
       if (ex >= Ex || (k > 0 && ey0 + k - 1 >= Ey)) continue;
-      const int64_t em = ((ey0 + k - 1 + Ey) % Ey) * Ex + ex;
-      const int64_t ep = ((ey0 + k) % Ey) * Ex + ex;
+      // face below element row ey0+k: minus side = buffer row ey0+k (top side),
+      // plus side = buffer row ey0+k+1 (bottom side); rows 0 and Ey+1 are halos
+      const int64_t plane = Ex * n;
+      const int64_t rm = ey0 + k, rp = ey0 + k + 1;
 #pragma unroll
       for (int fi = 0; fi < kTrFields; ++fi) {
-        a[fi] = L.try_[(2 * fi + 1) * ts + em * n + p];
-        b[fi] = L.try_[(2 * fi + 0) * ts + ep * n + p];
+        a[fi] = L.try_[((rm * 2 + 1) * kTrFields + fi) * plane + ex * n + p];
+        b[fi] = L.try_[((rp * 2 + 0) * kTrFields + fi) * plane + ex * n + p];
       }
-      face_terms(a, b, 2, L.sface[(Ne + ep) * n + p], T.gravity, Tm, Tp);
+      face_terms(a, b, 2, L.sface[Ne * n + (ey0 + k) * plane + ex * n + p], T.gravity, Tm, Tp);
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         sym[k][c][p][v] = Tm[v];
@@ -460,9 +470,10 @@ __global__ void __launch_bounds__(kBlock2D) k_rate_2d(const Launch2D L, int slot
 }
 
 // Static terms from the bathymetry: g b_x, g b_y at the nodes and
-// (g / b_0)(b+ - b-) at the left x-face and bottom y-face of each element.
+// (g / b_0)(b+ - b-) at the left x-face of each element and at the y-face
+// below each element row (plus the face above the top row).
 template <int N, bool GLL>
-__global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c,
+__global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c, int halo,
                           double* __restrict__ snode, double* __restrict__ sface, const Tables T) {
   constexpr int n = N + 1;
   constexpr int nn = n * n;
@@ -470,13 +481,20 @@ __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c,
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= Ne) return;
   const int64_t ey = e / Ex, ex = e - ey * Ex;
-  const int64_t eL = ey * Ex + (ex == 0 ? Ex - 1 : ex - 1);
-  const int64_t eB = (ey == 0 ? Ey - 1 : ey - 1) * Ex + ex;
+  const int64_t exl = ex == 0 ? Ex - 1 : ex - 1;
+  // rows of c: with halo rows, element row r is row r+1 of c
+  const int64_t cy = ey + halo;
+  const int64_t cyb = halo ? ey : (ey == 0 ? Ey - 1 : ey - 1);
+  const int64_t cyt = halo ? ey + 2 : (ey == Ey - 1 ? 0 : ey + 1);
+  const double* own = c + (cy * Ex + ex) * nn;
+  const double* lft = c + (cy * Ex + exl) * nn;
+  const double* blw = c + (cyb * Ex + ex) * nn;
+  const double* abv = c + (cyt * Ex + ex) * nn;
   double b[n][n];
 #pragma unroll
   for (int q = 0; q < n; ++q)
 #pragma unroll
-    for (int p = 0; p < n; ++p) b[q][p] = c[e * nn + q * n + p];
+    for (int p = 0; p < n; ++p) b[q][p] = own[q * n + p];
 #pragma unroll
   for (int q = 0; q < n; ++q)
 #pragma unroll
@@ -490,20 +508,22 @@ __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c,
       snode[e * nn + q * n + p] = T.gravity * dx;
       snode[(Ne + e) * nn + q * n + p] = T.gravity * dy;   // local term: g, not g / b_0
     }
-  // own left/bottom traces and the neighbours' right/top traces
+  // fluctuations meet time averages divided by b_0 in the face terms
 #pragma unroll
   for (int k = 0; k < n; ++k) {
-    double own_l = 0.0, own_b = 0.0, nb_r = 0.0, nb_t = 0.0;
+    double own_l = 0.0, own_b = 0.0, own_t = 0.0, nb_r = 0.0, nb_t = 0.0, nb_b = 0.0;
 #pragma unroll
     for (int j = 0; j < n; ++j) {
       own_l = fma(T.l0[j], b[k][j], own_l);
       own_b = fma(T.l0[j], b[j][k], own_b);
-      nb_r = fma(T.l1[j], c[eL * nn + k * n + j], nb_r);
-      nb_t = fma(T.l1[j], c[eB * nn + j * n + k], nb_t);
+      own_t = fma(T.l1[j], b[j][k], own_t);
+      nb_r = fma(T.l1[j], lft[k * n + j], nb_r);
+      nb_t = fma(T.l1[j], blw[j * n + k], nb_t);
+      nb_b = fma(T.l0[j], abv[j * n + k], nb_b);
     }
-    // fluctuations meet time averages divided by b_0 in the face terms
     sface[e * n + k] = T.face_g * (own_l - nb_r);
-    sface[(Ne + e) * n + k] = T.face_g * (own_b - nb_t);
+    sface[Ne * n + e * n + k] = T.face_g * (own_b - nb_t);
+    if (ey == Ey - 1) sface[Ne * n + (Ne + ex) * n + k] = T.face_g * (nb_b - own_t);
   }
 }
 
@@ -569,15 +589,16 @@ int launch_rate_2d(const Launch2D& L, int slot, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, double* snode,
-                   double* sface, const Tables& T, void* stream) {
+int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, bool halo_rows,
+                   double* snode, double* sface, const Tables& T, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const unsigned blocks = (unsigned)((Ex * Ey + 127) / 128);
+  const int h = halo_rows ? 1 : 0;
   switch (N) {
-    case 1: k_coef_2d<1, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
-    case 2: k_coef_2d<2, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
-    case 3: k_coef_2d<3, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
-    case 4: k_coef_2d<4, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, snode, sface, T); break;
+    case 1: k_coef_2d<1, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, h, snode, sface, T); break;
+    case 2: k_coef_2d<2, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, h, snode, sface, T); break;
+    case 3: k_coef_2d<3, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, h, snode, sface, T); break;
+    case 4: k_coef_2d<4, false><<<blocks, 128, 0, s>>>(Ex, Ey, c, h, snode, sface, T); break;
     default: return (int)cudaErrorInvalidValue;
   }
   (void)gll;

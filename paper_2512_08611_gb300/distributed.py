@@ -45,6 +45,25 @@ def halo_exchange(send_bottom, send_top, recv_bottom, recv_top, group=None):
         req.wait()
 
 
+class SlabStepper:
+    """Steps one rank's slab of a 2D mesh: local phase, halo exchange, face
+    phase.  ``solver`` is a crkfr.Solver in subdomain mode.  With a single
+    process (no process group) the slab is its own periodic neighbour."""
+
+    def __init__(self, solver, group=None):
+        self.s = solver
+        self.group = group
+        self.send_bottom, self.send_top, self.recv_bottom, self.recv_top = solver.halo_buffers()
+
+    def step(self, u, dt, nsteps=1):
+        for _ in range(nsteps):
+            self.s.step_local(u, dt)
+            halo_exchange(self.send_bottom, self.send_top, self.recv_bottom, self.recv_top,
+                          self.group)
+            self.s.step_faces(u)
+        return u
+
+
 def slab_rows(global_rows, rank, world):
     """(first row, row count) of a rank's slab: contiguous, sizes differ by at
     most one."""

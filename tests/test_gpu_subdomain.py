@@ -1,0 +1,88 @@
+"""The 2D step split into horizontal slabs (local phase, one exchange of face
+traces, face phase) equals the single-domain step bitwise on the GPU: two
+subdomain contexts exchanging their halo blocks in one process, and a single
+slab that is its own periodic neighbour."""
+import numpy as np
+import pytest
+
+from gpu_common import G, golden_cfl, load, rel_l2, to_dev, to_host
+from oracle.basis import Basis
+from paper_2512_08611_gb300.workloads import SWE2DInput, accept_seed
+
+pytestmark = pytest.mark.gpu
+
+
+def case(N, Ex, Ey, L):
+    bs = Basis(N)
+    dx, dy = L / Ex, L / Ey
+    x = (np.arange(Ex)[None, :, None, None] + bs.xi[None, None, None, :]) * dx
+    y = (np.arange(Ey)[:, None, None, None] + bs.xi[None, None, :, None]) * dy
+    x, y = np.broadcast_arrays(x, y)
+    inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=L, n_gauss=6), (x, y), 0)
+    u, b = inp.state(x, y)
+    u[1] = 0.05 * u[0] * np.sin(2 * np.pi * y / L)
+    u[2] = 0.05 * u[0] * np.cos(2 * np.pi * x / L)
+    return u, b
+
+
+def mono(crk, N, Ex, Ey, L, u, b, dt, steps):
+    s = crk.Solver("swe2d", N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+    s.set_mesh([Ex, Ey], [0.0, 0.0], [L, L])
+    s.set_coefficients(to_dev(b))
+    du = to_dev(u)
+    s.step(du, dt, steps)
+    return to_host(du)
+
+
+def slab(crk, N, Ex, Ey, L, b, first, count):
+    dy = L / Ey
+    s = crk.Solver("swe2d", N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+    s.set_mesh([Ex, count], [0.0, first * dy], [L, (first + count) * dy])
+    s.set_subdomain(True)
+    rows = [(first - 1) % Ey] + list(range(first, first + count)) + [(first + count) % Ey]
+    s.set_coefficients(to_dev(np.ascontiguousarray(b[rows])))
+    return s
+
+
+@pytest.mark.parametrize("N", [1, 3])
+def test_two_slabs_equal_single_domain(N):
+    crk = load()
+    Ex, Ey, L, dt, steps = 16, 16, 64.0, 0.02, 5      # dx = dy = 4: exact slab bounds
+    u, b = case(N, Ex, Ey, L)
+    want = mono(crk, N, Ex, Ey, L, u, b, dt, steps)
+    parts = [(0, 7), (7, 9)]
+    solvers = [slab(crk, N, Ex, Ey, L, b, f, c) for f, c in parts]
+    states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    bufs = [s.halo_buffers() for s in solvers]       # (send_bottom, send_top, recv_bottom, recv_top)
+    for _ in range(steps):
+        for s, x in zip(solvers, states):
+            s.step_local(x, dt)
+        for k in range(2):
+            below, above = (k - 1) % 2, (k + 1) % 2
+            bufs[k][2].copy_(bufs[below][1])           # recv_bottom <- send_top of the slab below
+            bufs[k][3].copy_(bufs[above][0])           # recv_top <- send_bottom of the slab above
+        for s, x in zip(solvers, states):
+            s.step_faces(x)
+    got = np.concatenate([to_host(x) for x in states], axis=1)
+    assert np.array_equal(got, want), rel_l2(got, want)
+
+
+def test_single_slab_is_its_own_neighbour():
+    from paper_2512_08611_gb300.distributed import SlabStepper
+    crk = load()
+    N, Ex, Ey, L, dt, steps = 3, 24, 8, 64.0, 0.02, 4
+    u, b = case(N, Ex, Ey, L)
+    want = mono(crk, N, Ex, Ey, L, u, b, dt, steps)
+    s = slab(crk, N, Ex, Ey, L, b, 0, Ey)
+    x = to_dev(u)
+    SlabStepper(s).step(x, dt, steps)
+    assert np.array_equal(to_host(x), want)
+
+
+def test_monolithic_step_refused_in_subdomain_mode():
+    crk = load()
+    u, b = case(2, 8, 8, 64.0)
+    s = slab(crk, 2, 8, 8, 64.0, b, 0, 8)
+    with pytest.raises(crk.CrkfrError) as e:
+        s.step(to_dev(u), 0.01, 1)
+    assert e.value.status == -6
