@@ -16,9 +16,12 @@ and per node W = u - dt V: 3 FMA; per element row and face side, for each of
 
 Fused 1D kernel (shallow water, per node and stage): stage value 2 nnz_i FMA,
 flux 4 FMA + 2 MUL, local operator 2 MUL + (2n - 1) FMA, time averages
-5 FMA if b_i != 0 (a copy at the first stage; V 2, U 2, F 1); per node the
-update 2 FMA + 1 FMA and the
-traces 5 fields x 2 sides x (1 MUL + (n - 1) FMA) per element.
+5 FMA if b_i != 0 (a copy at the first stage; V 2, U 2, F 1).  Per element:
+traces 5 fields x 2 sides x (1 MUL + (n - 1) FMA); one face (its right face):
+two wave speeds (1/h 3 FMA, |m/h| + sqrt(g h) with the 5-instruction square
+root: 6 FMA + 4 MUL + 1 ADD each), 5 ADD + 1 MUL of differences, 6 FMA of
+face terms; corrections and update 3 FMA per variable and node; the next
+time step's rate: element means 2 (n - 1) FMA + 2 MUL, one wave speed, 1 MUL.
 """
 import numpy as np
 
@@ -48,8 +51,11 @@ def local_flops_per_element(system, N):
             mul += 2 + 2
             if bz and i > 0:
                 fma += 5
-        fma += 3
         per_node = 2 * fma + mul
         traces = 5 * 2 * (1 + 2 * (n - 1))
-        return per_node * n + traces
+        speed = 2 * 6 + 4 + 1
+        face = 2 * speed + 5 + 1 + 2 * 6
+        update = 2 * 3 * 2 * n
+        rate = 2 * 2 * (n - 1) + 2 + speed + 1
+        return per_node * n + traces + face + update + rate
     raise ValueError(system)
