@@ -260,6 +260,41 @@ crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n_elem, doub
                                    const double* c_dev, const double* u_in_dev, double* u_out_dev,
                                    double dt, int64_t nsteps, void* stream);
 
+/* Ragged ensembles of independent 1D meshes (one system, node family and
+ * C_s for all; per instance its own degree, element count, interval,
+ * coefficient field and, with the CFL step, its own time step).  A step of
+ * the whole ensemble is one kernel launch per degree class over a work list
+ * of (instance, 126-element tile) pairs running the same fused step as
+ * crkfr_step, so instances of any size share the GPU.
+ *
+ * crkfr_batch_create: cfg->system CRKFR_SYS_VARADV_1D or CRKFR_SYS_SWE_1D
+ * (cfg->degree ignored); n instances with degrees[i], n_elem[i] elements on
+ * [lo[i], hi[i]] (host arrays).  Allocates the batch's device buffers.
+ * crkfr_batch_layout: offsets (n+1 values each, host) of every instance in
+ * the packed state (instance i's u[var][elem][p] starts at state_offsets[i])
+ * and in the packed coefficient field ([elem][p] at coef_offsets[i]).
+ * crkfr_batch_set_coefficients: packed c (device).
+ * crkfr_batch_step: nsteps steps of the packed state u in place; dt > 0: the
+ * same fixed step for all, dt <= 0: each instance's own step of Sec. 5,
+ * Eq. time.step.2d.  use_graph != 0 captures the whole call once into a
+ * CUDA graph (re-captured when u, nsteps or dt change) and replays it on
+ * `stream`.  crkfr_batch_get_times / get_status read the instances'
+ * simulated times (host array of n) and the status word (synchronise). */
+typedef struct crkfr_batch crkfr_batch;
+crkfr_status crkfr_batch_create(crkfr_batch** out, const crkfr_config* cfg, int32_t n,
+                                const int32_t* degrees, const int64_t* n_elem, const double* lo,
+                                const double* hi);
+void crkfr_batch_destroy(crkfr_batch* batch);
+crkfr_status crkfr_batch_layout(const crkfr_batch* batch, int64_t* state_offsets,
+                                int64_t* coef_offsets);
+crkfr_status crkfr_batch_set_coefficients(crkfr_batch* batch, const double* c_dev, void* stream);
+crkfr_status crkfr_batch_step(crkfr_batch* batch, double* u_dev, double dt, int64_t nsteps,
+                              int32_t use_graph, void* stream);
+crkfr_status crkfr_batch_get_times(crkfr_batch* batch, double* t_host, void* stream);
+crkfr_status crkfr_batch_get_status(crkfr_batch* batch, void* stream);
+int64_t crkfr_batch_launch_count(const crkfr_batch* batch);
+const char* crkfr_batch_last_error(const crkfr_batch* batch);
+
 /* Static strings. */
 const char* crkfr_error_string(crkfr_status status);
 const char* crkfr_last_error(const crkfr_ctx* ctx);

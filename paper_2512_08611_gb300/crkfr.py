@@ -72,6 +72,16 @@ SIGNATURES = {
     "crkfr_math_check": (_I32, [_P, _P, _I64, _I32, _P]),
     "crkfr_step_1d_noalloc": (_I32, [ctypes.POINTER(Config), _I64, _D, _D, _P, _P, _P, _D, _I64,
                                      _P]),
+    "crkfr_batch_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(Config), _I32,
+                                  ctypes.POINTER(ctypes.c_int32), _PI64, _PD, _PD]),
+    "crkfr_batch_destroy": (None, [_P]),
+    "crkfr_batch_layout": (_I32, [_P, _PI64, _PI64]),
+    "crkfr_batch_set_coefficients": (_I32, [_P, _P, _P]),
+    "crkfr_batch_step": (_I32, [_P, _P, _D, _I64, _I32, _P]),
+    "crkfr_batch_get_times": (_I32, [_P, _PD, _P]),
+    "crkfr_batch_get_status": (_I32, [_P, _P]),
+    "crkfr_batch_launch_count": (_I64, [_P]),
+    "crkfr_batch_last_error": (ctypes.c_char_p, [_P]),
     "crkfr_error_string": (ctypes.c_char_p, [_I32]),
     "crkfr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -325,3 +335,73 @@ class Solver:
             if n.value:
                 out[name] = (n.value, ms.value)
         return out
+
+
+class Batch:
+    """Ragged ensemble of independent 1D meshes advanced together
+    (crkfr_batch_*).  ``members``: list of (degree, n_elem, lo, hi)."""
+
+    def __init__(self, system, members, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0):
+        self.system = system
+        self.M = NVARS[system]
+        self.members = [(int(d), int(e), float(a), float(b)) for d, e, a, b in members]
+        n = len(self.members)
+        cfg = Config(SYSTEMS[system], 0, NODES[nodes], 0, gravity, cfl_safety, cfl_number)
+        deg = (ctypes.c_int32 * n)(*[m[0] for m in self.members])
+        ne = (ctypes.c_int64 * n)(*[m[1] for m in self.members])
+        lo = (ctypes.c_double * n)(*[m[2] for m in self.members])
+        hi = (ctypes.c_double * n)(*[m[3] for m in self.members])
+        h = ctypes.c_void_p()
+        st = lib().crkfr_batch_create(ctypes.byref(h), ctypes.byref(cfg), n, deg, ne, lo, hi)
+        if st != CRKFR_OK:
+            raise CrkfrError(st, lib().crkfr_error_string(st).decode())
+        self.h = h
+        so, co = (ctypes.c_int64 * (n + 1))(), (ctypes.c_int64 * (n + 1))()
+        self._check(lib().crkfr_batch_layout(self.h, so, co))
+        self.state_offsets, self.coef_offsets = list(so), list(co)
+
+    def _check(self, st):
+        if st != CRKFR_OK:
+            raise CrkfrError(st, lib().crkfr_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().crkfr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state_view(self, u, i):
+        """Instance i's state (var, elem, node) as a view of the packed u."""
+        d, E, _, _ = self.members[i]
+        a, b = self.state_offsets[i], self.state_offsets[i + 1]
+        return u[a:b].view(self.M, E, d + 1)
+
+    def coef_view(self, c, i):
+        d, E, _, _ = self.members[i]
+        a, b = self.coef_offsets[i], self.coef_offsets[i + 1]
+        return c[a:b].view(E, d + 1)
+
+    def set_coefficients(self, c):
+        self._check(lib().crkfr_batch_set_coefficients(self.h, ctypes.c_void_p(c.data_ptr()),
+                                                       _stream()))
+
+    def step(self, u, dt=0.0, nsteps=1, graph=True):
+        self._check(lib().crkfr_batch_step(self.h, ctypes.c_void_p(u.data_ptr()), float(dt),
+                                           int(nsteps), 1 if graph else 0, _stream()))
+        return u
+
+    def times(self):
+        t = (ctypes.c_double * len(self.members))()
+        self._check(lib().crkfr_batch_get_times(self.h, t, _stream()))
+        return np.array(t[:])
+
+    def status(self):
+        self._check(lib().crkfr_batch_get_status(self.h, _stream()))
+
+    def launch_count(self):
+        return lib().crkfr_batch_launch_count(self.h)

@@ -20,6 +20,7 @@ struct crkfr_ctx {
   HostBasis basis;
   Tables tab{};
   double cfl = 0.0;
+  double xs = 1.0;   // 1 / dx
   int M = 1;
   int dim = 0;
   int64_t Ex = 0, Ey = 1;
@@ -157,6 +158,7 @@ Launch1D make1d(crkfr_ctx* c) {
   L.sface = c->d_sface;
   L.st = c->d_state;
   L.tab = c->tab;
+  L.xs = c->xs;
   return L;
 }
 
@@ -358,8 +360,10 @@ crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, co
   }
   const double dx = (c->hi[0] - c->lo[0]) / (double)Ex;
   const double dy = (c->hi[1] - c->lo[1]) / (double)Ey;
-  fill_tables(c->basis, dx, dim == 2 ? dy : 0.0,
+  // 1D kernels take reference-element tables and 1/dx as a scalar
+  fill_tables(c->basis, dim == 2 ? dx : 1.0, dim == 2 ? dy : 0.0,
               c->cfg.system == CRKFR_SYS_VARADV_1D ? 0.0 : c->cfg.gravity, &c->tab);
+  c->xs = (double)Ex / (c->hi[0] - c->lo[0]);   // 1/dx, as the batch path computes it
 
   size_t sn, sf;
   if (dim == 1) {

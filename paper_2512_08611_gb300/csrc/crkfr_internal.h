@@ -84,13 +84,46 @@ struct Launch1D {
   const double* snode;   // [E][n]
   const double* sface;   // [E][2]
   DevState* st;
-  Tables tab;
+  Tables tab;            // reference element (dx = 1)
+  double xs;             // 1 / dx
   StepCtl ctl;
 };
 int launch_step_1d(const Launch1D& L, void* stream);
 int launch_rate_1d(const Launch1D& L, int slot, void* stream);
 int launch_coef_1d(int system, int N, int64_t E, const double* c, double* snode, double* sface,
                    const Tables& tab, void* stream);
+
+// Ragged ensemble of independent 1D meshes advanced together: every block
+// takes one (instance, tile) pair from a work list of one degree class.
+struct BatchInstance {
+  int64_t E;          // elements
+  int64_t u_off;      // offset of the instance's state in the packed state
+  int64_t sn_off;     // offset in the packed static node terms ([E][n])
+  int64_t sf_off;     // offset in the packed face traces of c ([E][2])
+  double xs;          // 1 / dx
+  DevState* st;       // the instance's stepping state
+};
+struct WorkItem {
+  int32_t inst;
+  int32_t tile;
+};
+struct LaunchBatch1D {
+  int system;
+  int N;
+  bool gll;
+  const BatchInstance* inst;
+  const WorkItem* work;
+  int64_t nwork;
+  const double* u_in;
+  double* u_out;
+  const double* snode;
+  const double* sface;
+  Tables tab;         // reference element of degree N
+  StepCtl ctl;
+};
+int launch_step_1d_batch(const LaunchBatch1D& B, void* stream);
+int launch_rate_1d_batch(const LaunchBatch1D& B, int slot, void* stream);
+constexpr int kTile1D = 126;   // elements a 1D block owns (128 threads, 2 halo)
 
 struct Launch2D {
   int N;

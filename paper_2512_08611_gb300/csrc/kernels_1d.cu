@@ -62,17 +62,26 @@ __device__ __forceinline__ double swe_speed(double h, double m, double g) {
   return fabs(m * drcp(h)) + dsqrt_pos(g * h);
 }
 
+// One tile (126 elements plus a halo element on each side) of the fused 1D
+// step of one mesh.  T holds reference-element tables (dx = 1: D, l(0), l(1),
+// 0.5 g'); xs = 1/dx scales the local operator and the corrections through
+// the scalar coefficients only (stage coefficients dt a_ij xs, update
+// coefficient dt b_0 xs), so one table serves meshes of any dx.
 template <int SYS, int N, bool GLL, bool RES>
-__global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
+__device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
+                                             const double* __restrict__ u_in,
+                                             double* __restrict__ u_out,
+                                             const double* __restrict__ snode,
+                                             const double* __restrict__ sface, int64_t E,
+                                             int64_t tile, DevState* st, const StepCtl& ctl,
+                                             bool first_tile) {
   constexpr int n = N + 1;
   constexpr int M = Sys1D<SYS>::M;
   constexpr int NL = Sys1D<SYS>::NLEFT;
   constexpr int S = tab_stages(N);
   constexpr bool SWE = (SYS == CRKFR_SYS_SWE_1D);
-  const Tables& T = L.tab;
-  const int64_t E = L.E;
   const int t = threadIdx.x;
-  const int64_t e_raw = (int64_t)blockIdx.x * (kBlock1D - 2) + t - 1;
+  const int64_t e_raw = tile * (kBlock1D - 2) + t - 1;
   int64_t e = e_raw % E;
   if (e < 0) e += E;
   const bool owner = (t >= 1) && (t <= kBlock1D - 2) && (e_raw < E);
@@ -80,19 +89,20 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
   __shared__ double sm_left[NL][kBlock1D];
   __shared__ double sm_T[M][kBlock1D];
 
-  const double dt = RES ? L.ctl.dt_fixed : step_dt(L.ctl, L.st);
-  if (!RES && blockIdx.x == 0 && t == 0) step_bookkeeping(L.ctl, L.st, dt);
+  const double dt = RES ? ctl.dt_fixed : step_dt(ctl, st);
+  if (!RES && first_tile && t == 0) step_bookkeeping(ctl, st, dt);
+  const double dtx = dt * xs;
 
   // ---- load u^n and the static coefficient terms of this element ----------
   double u0[M][n];
 #pragma unroll
   for (int v = 0; v < M; ++v)
 #pragma unroll
-    for (int p = 0; p < n; ++p) u0[v][p] = L.u_in[((int64_t)v * E + e) * n + p];
+    for (int p = 0; p < n; ++p) u0[v][p] = u_in[((int64_t)v * E + e) * n + p];
   double sn[n];
 #pragma unroll
-  for (int p = 0; p < n; ++p) sn[p] = L.snode[e * n + p];
-  const double c_l = L.sface[2 * e], c_r = L.sface[2 * e + 1];
+  for (int p = 0; p < n; ++p) sn[p] = snode[e * n + p];
+  const double c_l = sface[2 * e], c_r = sface[2 * e + 1];
 
   // ---- inner stages (element-local) ----------------------------------------
   // Time averages are accumulated with the weights b_j / b_0 (the first
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
         double acc = u0[v][p];
 #pragma unroll
         for (int j = 0; j < i; ++j)
-          if (tab_a(N, i, j) != 0.0) acc = fma(-(dt * tab_a(N, i, j)), Ls[j][v][p], acc);
+          if (tab_a(N, i, j) != 0.0) acc = fma(-(dtx * tab_a(N, i, j)), Ls[j][v][p], acc);
         cur[v][p] = acc;
       }
     if constexpr (SWE) {
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
 #pragma unroll
     for (int v = 0; v < M; ++v) Tp[v] = sm_T[v][t];
     constexpr double b0 = tab_b(N, 0);
-    const double dtb0 = dt * b0;
+    const double dtb0 = dtx * b0;
     double out[M][n];
 #pragma unroll
     for (int v = 0; v < M; ++v)
@@ -232,8 +242,8 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
         double R = V[v][p];
         if (!GLL || p == N) R = fma(Tm[v], T.gRx[p], R);
         if (!GLL || p == 0) R = fma(Tp[v], T.gLx[p], R);
-        out[v][p] = RES ? -b0 * R : fma(-dtb0, R, u0[v][p]);
-        L.u_out[((int64_t)v * E + e) * n + p] = out[v][p];
+        out[v][p] = RES ? -(b0 * xs) * R : fma(-dtb0, R, u0[v][p]);
+        u_out[((int64_t)v * E + e) * n + p] = out[v][p];
       }
     if (!RES) {
       if constexpr (SWE) {
@@ -243,7 +253,7 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
 #pragma unroll
         for (int p = 0; p < n; ++p) bad |= !finite(out[0][p]);
       }
-      if (L.ctl.want_rate) {
+      if (ctl.want_rate) {
         double hb = T.w[0] * out[0][0];
 #pragma unroll
         for (int p = 1; p < n; ++p) hb = fma(T.w[p], out[0][p], hb);
@@ -251,21 +261,27 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
           double mb = T.w[0] * out[1][0];
 #pragma unroll
           for (int p = 1; p < n; ++p) mb = fma(T.w[p], out[1][p], mb);
-          rate = swe_speed(hb, mb, T.gravity) * T.inv_dx;
+          rate = swe_speed(hb, mb, T.gravity) * xs;
         } else {
           // the speed of advection is |a| averaged over the element
           double ab = T.w[0] * sn[0];
 #pragma unroll
           for (int p = 1; p < n; ++p) ab = fma(T.w[p], sn[p], ab);
-          rate = fabs(ab) * T.inv_dx;
+          rate = fabs(ab) * xs;
         }
       }
     }
   }
   if (!RES) {
-    if (bad) atomicOr(&L.st->status, 1u);
-    if (L.ctl.want_rate) block_max_atomic<kBlock1D>(rate, &L.st->rate[L.ctl.slot_write]);
+    if (bad) atomicOr(&st->status, 1u);
+    if (ctl.want_rate) block_max_atomic<kBlock1D>(rate, &st->rate[ctl.slot_write]);
   }
+}
+
+template <int SYS, int N, bool GLL, bool RES>
+__global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
+  step_1d_tile<SYS, N, GLL, RES>(L.tab, L.xs, L.u_in, L.u_out, L.snode, L.sface, L.E,
+                                 blockIdx.x, L.st, L.ctl, blockIdx.x == 0);
 }
 
 // max_e sigma(ubar_e)/dx of a state into one rate slot (Sec. 5, Eq. time.step.2d)
@@ -284,20 +300,20 @@ __global__ void __launch_bounds__(kBlock1D) k_rate_1d(const Launch1D L, int slot
         hb = fma(T.w[p], L.u_in[e * n + p], hb);
         mb = fma(T.w[p], L.u_in[(L.E + e) * n + p], mb);
       }
-      rate = swe_speed(hb, mb, T.gravity) * T.inv_dx;
+      rate = swe_speed(hb, mb, T.gravity) * L.xs;
     } else {
       double ab = 0.0;
 #pragma unroll
       for (int p = 0; p < n; ++p) ab = fma(T.w[p], L.snode[e * n + p], ab);
-      rate = fabs(ab) * T.inv_dx;
+      rate = fabs(ab) * L.xs;
     }
   }
   block_max_atomic<kBlock1D>(rate, &L.st->rate[slot]);
 }
 
 // Static coefficient terms: per node the factor of the local non-conservative
-// product (a for advection, g (D b)/dx for shallow water) and per element the
-// face traces of c.
+// product (a for advection, g D b for shallow water, in reference units like
+// the rest of the 1D tables) and per element the face traces of c.
 template <int SYS, int N>
 __global__ void k_coef_1d(int64_t E, const double* __restrict__ c, double* __restrict__ snode,
                           double* __restrict__ sface, const Tables T) {
@@ -326,6 +342,84 @@ __global__ void k_coef_1d(int64_t E, const double* __restrict__ c, double* __res
   }
   sface[2 * e] = l;
   sface[2 * e + 1] = r;
+}
+
+// ---- ragged ensembles -----------------------------------------------------
+template <int SYS, int N, bool GLL>
+__global__ void __launch_bounds__(kBlock1D) k_step_1d_batch(const LaunchBatch1D B) {
+  const WorkItem w = B.work[blockIdx.x];
+  const BatchInstance I = B.inst[w.inst];
+  step_1d_tile<SYS, N, GLL, false>(B.tab, I.xs, B.u_in + I.u_off, B.u_out + I.u_off,
+                                   B.snode + I.sn_off, B.sface + I.sf_off, I.E, w.tile, I.st,
+                                   B.ctl, w.tile == 0);
+}
+
+// rate of each instance's state (the owned elements of each tile)
+template <int SYS, int N>
+__global__ void __launch_bounds__(kBlock1D) k_rate_1d_batch(const LaunchBatch1D B, int slot) {
+  constexpr int n = N + 1;
+  const WorkItem w = B.work[blockIdx.x];
+  const BatchInstance I = B.inst[w.inst];
+  const Tables& T = B.tab;
+  const int t = threadIdx.x;
+  const int64_t e = (int64_t)w.tile * (kBlock1D - 2) + t - 1;
+  double rate = 0.0;
+  if (t >= 1 && t <= kBlock1D - 2 && e < I.E) {
+    const double* u = B.u_in + I.u_off;
+    if constexpr (SYS == CRKFR_SYS_SWE_1D) {
+      double hb = 0.0, mb = 0.0;
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+        hb = fma(T.w[p], u[e * n + p], hb);
+        mb = fma(T.w[p], u[(I.E + e) * n + p], mb);
+      }
+      rate = swe_speed(hb, mb, T.gravity) * I.xs;
+    } else {
+      double ab = 0.0;
+#pragma unroll
+      for (int p = 0; p < n; ++p) ab = fma(T.w[p], B.snode[I.sn_off + e * n + p], ab);
+      rate = fabs(ab) * I.xs;
+    }
+  }
+  block_max_atomic<kBlock1D>(rate, &I.st->rate[slot]);
+}
+
+template <int SYS, int N, bool GLL>
+int launch_batch_t(const LaunchBatch1D& B, cudaStream_t s) {
+  if (B.nwork <= 0) return 0;
+  k_step_1d_batch<SYS, N, GLL><<<(unsigned)B.nwork, kBlock1D, 0, s>>>(B);
+  return (int)cudaGetLastError();
+}
+
+template <int SYS>
+int launch_batch_sys(const LaunchBatch1D& B, cudaStream_t s) {
+  switch (B.N * 2 + (B.gll ? 1 : 0)) {
+    case 0: return launch_batch_t<SYS, 0, false>(B, s);
+    case 2: return launch_batch_t<SYS, 1, false>(B, s);
+    case 3: return launch_batch_t<SYS, 1, true>(B, s);
+    case 4: return launch_batch_t<SYS, 2, false>(B, s);
+    case 5: return launch_batch_t<SYS, 2, true>(B, s);
+    case 6: return launch_batch_t<SYS, 3, false>(B, s);
+    case 7: return launch_batch_t<SYS, 3, true>(B, s);
+    case 8: return launch_batch_t<SYS, 4, false>(B, s);
+    case 9: return launch_batch_t<SYS, 4, true>(B, s);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <int SYS>
+int launch_batch_rate_sys(const LaunchBatch1D& B, int slot, cudaStream_t s) {
+  if (B.nwork <= 0) return 0;
+  const unsigned blocks = (unsigned)B.nwork;
+  switch (B.N) {
+    case 0: k_rate_1d_batch<SYS, 0><<<blocks, kBlock1D, 0, s>>>(B, slot); break;
+    case 1: k_rate_1d_batch<SYS, 1><<<blocks, kBlock1D, 0, s>>>(B, slot); break;
+    case 2: k_rate_1d_batch<SYS, 2><<<blocks, kBlock1D, 0, s>>>(B, slot); break;
+    case 3: k_rate_1d_batch<SYS, 3><<<blocks, kBlock1D, 0, s>>>(B, slot); break;
+    case 4: k_rate_1d_batch<SYS, 4><<<blocks, kBlock1D, 0, s>>>(B, slot); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
 }
 
 template <int SYS, int N, bool GLL>
@@ -389,6 +483,21 @@ int launch_step_1d(const Launch1D& L, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (L.system == CRKFR_SYS_SWE_1D) return launch_step_sys<CRKFR_SYS_SWE_1D>(L, s);
   if (L.system == CRKFR_SYS_VARADV_1D) return launch_step_sys<CRKFR_SYS_VARADV_1D>(L, s);
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_step_1d_batch(const LaunchBatch1D& B, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (B.system == CRKFR_SYS_SWE_1D) return launch_batch_sys<CRKFR_SYS_SWE_1D>(B, s);
+  if (B.system == CRKFR_SYS_VARADV_1D) return launch_batch_sys<CRKFR_SYS_VARADV_1D>(B, s);
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_rate_1d_batch(const LaunchBatch1D& B, int slot, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (B.system == CRKFR_SYS_SWE_1D) return launch_batch_rate_sys<CRKFR_SYS_SWE_1D>(B, slot, s);
+  if (B.system == CRKFR_SYS_VARADV_1D)
+    return launch_batch_rate_sys<CRKFR_SYS_VARADV_1D>(B, slot, s);
   return (int)cudaErrorInvalidValue;
 }
 

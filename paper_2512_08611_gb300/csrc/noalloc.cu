@@ -91,9 +91,9 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
     if (a != o && a < o + state_bytes && o < a + state_bytes) return CRKFR_ERR_ARG;
   }
 
-  Tables T;
-  fill_tables(b, (hi - lo) / (double)E, 0.0,
-              cfg->system == CRKFR_SYS_VARADV_1D ? 0.0 : cfg->gravity, &T);
+  Tables T;   // reference element; 1/dx goes with the launch
+  fill_tables(b, 1.0, 0.0, cfg->system == CRKFR_SYS_VARADV_1D ? 0.0 : cfg->gravity, &T);
+  const double xs = (double)E / (hi - lo);
 
   // the array keeps the previous call's contents: reset the stepping state
   if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess) return CRKFR_ERR_CUDA;
@@ -118,6 +118,7 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
   L.sface = sface;
   L.st = st;
   L.tab = T;
+  L.xs = xs;
   // ping-pong between the caller's output and the scratch state, ending in
   // the output; an input that is also the output is first moved to scratch
   // (an odd count in place starts from a copy in scratch: the first step may
