@@ -26,6 +26,7 @@ import numpy as np
 
 from .basis import Basis
 from .tableau import default_tableau
+from .xp import xp_of
 
 FROZEN, LITERAL, STAGEWISE = "frozen", "literal", "stagewise"
 
@@ -34,29 +35,29 @@ FROZEN, LITERAL, STAGEWISE = "frozen", "literal", "stagewise"
 # element-local derivatives (Eq. dlocx.defn with d/dx = (1/dx) d/dxi)
 # ----------------------------------------------------------------------------
 def dloc_1d(D, X):
-    return np.einsum("pj,...j->...p", D, X)
+    return xp_of(X).einsum("pj,...j->...p", D, X)
 
 
 def dlocx_2d(D, X):
-    return np.einsum("pj,...qj->...qp", D, X)
+    return xp_of(X).einsum("pj,...qj->...qp", D, X)
 
 
 def dlocy_2d(D, X):
-    return np.einsum("qj,...jp->...qp", D, X)
+    return xp_of(X).einsum("qj,...jp->...qp", D, X)
 
 
 def trace_1d(l, X):
-    return np.einsum("p,...p->...", l, X)
+    return xp_of(X).einsum("p,...p->...", l, X)
 
 
 def tracex_2d(l, X):
     """Extrapolation along x to a vertical face, one value per y-node."""
-    return np.einsum("p,...qp->...q", l, X)
+    return xp_of(X).einsum("p,...qp->...q", l, X)
 
 
 def tracey_2d(l, X):
     """Extrapolation along y to a horizontal face, one value per x-node."""
-    return np.einsum("q,...qp->...p", l, X)
+    return xp_of(X).einsum("q,...qp->...p", l, X)
 
 
 # ----------------------------------------------------------------------------
@@ -71,10 +72,11 @@ def face_terms(flux_m, flux_p, U_m, U_p, un_m, un_p, c_m, c_p,
     ``stage_m/stage_p`` (lists of stage traces) are needed only for the
     'literal' and 'stagewise' readings.  Returns (T_minus, T_plus, lam).
     """
+    xp = xp_of(U_m, un_m, flux_m)
     if lam_state == "n":
-        lam = np.maximum(speed(un_m, c_m), speed(un_p, c_p))
+        lam = xp.maximum(speed(un_m, c_m), speed(un_p, c_p))
     else:
-        lam = np.maximum(speed(U_m, c_m), speed(U_p, c_p))
+        lam = xp.maximum(speed(U_m, c_m), speed(U_p, c_p))
     Fnum = 0.5 * (flux_m + flux_p) - 0.5 * lam * (U_p - U_m)
     U_num = 0.5 * (U_m + U_p)
     c_num = 0.5 * (c_m + c_p)
@@ -168,12 +170,13 @@ class Scheme1D:
         wave: values wrapped across the periodic boundary are multiplied by
         exp(-+ i theta).  Used only by the von Neumann analysis."""
         bs = self.basis
+        xp = xp_of(u)
         loc = self.local(u, c, dt)
         ph = 1.0 if bloch is None else np.exp(-1j * bloch)
 
         def left_neighbour(X, scale=True):
             # element e-1 for each e (periodic); face k has minus side = elem k-1
-            Y = np.roll(X, 1, axis=-1)
+            Y = xp.roll(X, 1, axis=-1)
             if bloch is not None and scale:
                 Y = Y.astype(complex)
                 Y[..., 0] = Y[..., 0] * ph
@@ -190,11 +193,12 @@ class Scheme1D:
             lp["st_l"] = loc["st_l"]
         T_m, T_p, lam = self._faces(lm, lp)
         # element e: right face is face e+1 (minus side), left face is face e
-        T_right = np.roll(T_m, -1, axis=-1)
+        T_right = xp.roll(T_m, -1, axis=-1)
         if bloch is not None:
             T_right = T_right.astype(complex)
             T_right[..., -1] = T_right[..., -1] / ph
-        R = loc["vol"] + (T_right[..., None] * bs.gRp + T_p[..., None] * bs.gLp) / self.dx
+        gR, gL = xp.asarray(bs.gRp), xp.asarray(bs.gLp)
+        R = loc["vol"] + (T_right[..., None] * gR + T_p[..., None] * gL) / self.dx
         self._last_lam = lam
         return R
 
@@ -331,11 +335,14 @@ class Scheme2D:
         """Correction terms (Eq. crkfr.non.cons.final) from the face terms at
         the right (Tr), left (Tl), top (Tt) and bottom (Tb) faces."""
         bs = self.basis
-        cx = (Tr[..., :, None] * bs.gRp + Tl[..., :, None] * bs.gLp) / self.dx
-        cy = (Tt[..., None, :] * bs.gRp[:, None] + Tb[..., None, :] * bs.gLp[:, None]) / self.dy
+        xp = xp_of(Tr)
+        gR, gL = xp.asarray(bs.gRp), xp.asarray(bs.gLp)
+        cx = (Tr[..., :, None] * gR + Tl[..., :, None] * gL) / self.dx
+        cy = (Tt[..., None, :] * gR[:, None] + Tb[..., None, :] * gL[:, None]) / self.dy
         return cx + cy
 
     def residual(self, u, c, dt):
+        ns = xp_of(u)
         loc = self.local(u, c, dt)
         ax_y, ax_x = -3, -2   # element axes of the trace arrays (..., ey, ex, node)
 
@@ -346,9 +353,9 @@ class Scheme2D:
                 if v is None:
                     continue
                 if isinstance(v, list):
-                    out[k] = [np.roll(x, shift, axis=axis) for x in v]
+                    out[k] = [ns.roll(x, shift, axis=axis) for x in v]
                 else:
-                    out[k] = np.roll(v, shift, axis=axis)
+                    out[k] = ns.roll(v, shift, axis=axis)
             return out
 
         xm = sel(loc, ("F_r", "U_r", "un_r", "c_r", "st_r"), 1, ax_x)
@@ -357,8 +364,8 @@ class Scheme2D:
         ym = sel(loc, ("G_t", "U_t", "un_t", "c_t", "st_t"), 1, ax_y)
         yp = sel(loc, ("G_b", "U_b", "un_b", "c_b", "st_b"), 0, ax_y)
         Tym, Typ, _ = self._yface(ym, yp)           # face (ky, ex): elem ky-1 below | ky above
-        Tr = np.roll(Txm, -1, axis=ax_x)
-        Tt = np.roll(Tym, -1, axis=ax_y)
+        Tr = ns.roll(Txm, -1, axis=ax_x)
+        Tt = ns.roll(Tym, -1, axis=ax_y)
         return loc["vol"] + self._corrections(Tr, Txp, Tt, Typ)
 
     def step(self, u, c, dt):

@@ -11,7 +11,9 @@ matrix-vector product B(w) (du, dc); the row of c is zero because c is static.
 Array convention: the variable index is the leading axis of ``u``/``du``;
 ``c``/``dc`` have no variable axis.
 """
-import numpy as np
+import numpy as np  # noqa: F401  (constants)
+
+from .xp import xp_of
 
 
 class VarCoeffAdvection:
@@ -21,13 +23,14 @@ class VarCoeffAdvection:
     name = "varadv"
 
     def flux(self, u, c):
-        return np.zeros_like(u)
+        return xp_of(u).zeros_like(u)
 
     def ncprod(self, u, c, du, dc):
         return c[None] * du
 
     def speed(self, u, c):
-        return np.abs(c) * np.ones_like(u[0])
+        xp = xp_of(u, c)
+        return xp.abs(c) * xp.ones_like(u[0])
 
 
 class ShallowWater1D:
@@ -44,15 +47,17 @@ class ShallowWater1D:
 
     def flux(self, u, c):
         h, m = u[0], u[1]
-        return np.stack([m, m * m / h + 0.5 * self.g * h * h])
+        return xp_of(u).stack([m, m * m / h + 0.5 * self.g * h * h])
 
     def ncprod(self, u, c, du, dc):
+        xp = xp_of(u, dc)
         h = u[0]
-        return np.stack([np.zeros_like(h * dc), self.g * h * dc])
+        return xp.stack([xp.zeros_like(h * dc), self.g * h * dc])
 
     def speed(self, u, c):
+        xp = xp_of(u)
         h, m = u[0], u[1]
-        return np.abs(m / h) + np.sqrt(self.g * h)
+        return xp.abs(m / h) + xp.sqrt(self.g * h)
 
 
 class ShallowWater2D:
@@ -70,27 +75,31 @@ class ShallowWater2D:
     def flux_x(self, u, c):
         h, mx, my = u[0], u[1], u[2]
         p = 0.5 * self.g * h * h
-        return np.stack([mx, mx * mx / h + p, mx * my / h])
+        return xp_of(u).stack([mx, mx * mx / h + p, mx * my / h])
 
     def flux_y(self, u, c):
         h, mx, my = u[0], u[1], u[2]
         p = 0.5 * self.g * h * h
-        return np.stack([my, mx * my / h, my * my / h + p])
+        return xp_of(u).stack([my, mx * my / h, my * my / h + p])
 
     def ncprod_x(self, u, c, du, dc):
+        xp = xp_of(u, dc)
         h = u[0]
-        z = np.zeros_like(h * dc)
-        return np.stack([z, self.g * h * dc, z])
+        z = xp.zeros_like(h * dc)
+        return xp.stack([z, self.g * h * dc, z])
 
     def ncprod_y(self, u, c, du, dc):
+        xp = xp_of(u, dc)
         h = u[0]
-        z = np.zeros_like(h * dc)
-        return np.stack([z, z, self.g * h * dc])
+        z = xp.zeros_like(h * dc)
+        return xp.stack([z, z, self.g * h * dc])
 
     def speed_x(self, u, c):
+        xp = xp_of(u)
         h, mx = u[0], u[1]
-        return np.abs(mx / h) + np.sqrt(self.g * h)
+        return xp.abs(mx / h) + xp.sqrt(self.g * h)
 
     def speed_y(self, u, c):
+        xp = xp_of(u)
         h, my = u[0], u[2]
-        return np.abs(my / h) + np.sqrt(self.g * h)
+        return xp.abs(my / h) + xp.sqrt(self.g * h)
