@@ -527,13 +527,77 @@ def run_ensemble(args):
         "gpu_launches": launches, "clocks": clk}))
 
 
+def run_adjoint(args):
+    """Gradient of the final surface misfit w.r.t. the bathymetry on the 2D
+    256 x 256, N = 3 mesh: 200 fixed steps, checkpoints every 20; reports the
+    cost of the adjoint relative to the forward run."""
+    import torch
+    from paper_2512_08611_gb300.build import build_library
+    build_library()
+    from oracle.basis import Basis  # noqa: F401  (not used on the timed path)
+    from paper_2512_08611_gb300 import crkfr
+    from paper_2512_08611_gb300.adjoint import (BathymetryToState, quadrature_weights,
+                                                surface_misfit)
+    from paper_2512_08611_gb300.workloads import SWE2DInput, accept_seed
+    torch.cuda.set_device(0)
+    E, N, L, nsteps, every = 256, 3, 100.0, 200, 20
+    s = crkfr.Solver("swe2d", N, gravity=G, cfl_safety=0.5)
+    s.set_mesh([E, E], [0.0, 0.0], [L, L])
+    x, y = s.positions()
+    inp, _ = accept_seed(lambda k: SWE2DInput(seed=k, L=L), (x, y), 0)
+    _, b = inp.state(x, y)
+    inp2, _ = accept_seed(lambda k: SWE2DInput(seed=k, L=L), (x, y), 7)
+    _, b2 = inp2.state(x, y)
+    eta0 = torch.tensor(inp.eta(x, y), device="cuda")
+    bt, b2t = torch.tensor(b, device="cuda"), torch.tensor(b2, device="cuda")
+    s.set_coefficients(b2t)
+    dt = 0.5 * s.compute_dt(torch.stack([eta0 - b2t, 0 * b2t, 0 * b2t]).contiguous())
+    W = quadrature_weights(s)
+    with torch.no_grad():
+        target = BathymetryToState.apply(b2t, s, eta0, dt, nsteps, every)[0] + b2t
+    # warm-up of both directions
+    bb = bt.clone().requires_grad_(True)
+    surface_misfit(BathymetryToState.apply(bb, s, eta0, dt, nsteps, every), bb, target, W).backward()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    bb = bt.clone().requires_grad_(True)
+    s.profile(True)
+    ev[0].record()
+    J = surface_misfit(BathymetryToState.apply(bb, s, eta0, dt, nsteps, every), bb, target, W)
+    ev[1].record()
+    J.backward()
+    ev[2].record()
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    n_adj = prof.get("adjoint_2d", (0, 0.0))
+    n_loc = prof.get("local_2d", (0, 0.0))
+    n_face = prof.get("face_2d", (0, 0.0))
+    # per step: forward = local + face; adjoint step = local (traces) + adjoint kernels
+    fwd_step = (n_loc[1] / max(n_loc[0], 1)) + (n_face[1] / max(n_face[0], 1))
+    adj_step = (n_loc[1] / max(n_loc[0], 1)) + n_adj[1] / max(n_adj[0], 1)
+    dof = 3 * E * E * (N + 1) ** 2
+    print(json.dumps({
+        "metric": METRIC, "value": dof * nsteps / (bwd / 1e3), "unit": "DoF-updates/s (adjoint)",
+        "n_gpus": 1, "steps": nsteps, "warmup": 1, "ms_per_step": bwd / nsteps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "adjoint-swe2d-256x256-N3-200steps-ckpt20",
+                   "loss": "1/2 sum w (h + b - target)^2 at T", "dt": dt},
+        "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+        "adjoint_step_over_forward_step": adj_step / fwd_step,
+        "adjoint_step_ms": adj_step, "forward_step_ms": fwd_step,
+        "gradient_norm": float(bb.grad.norm())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="swe2d", choices=["swe2d", "swe1d", "ensemble"])
+    ap.add_argument("--workload", default="swe2d", choices=["swe2d", "swe1d", "ensemble", "adjoint"])
     ap.add_argument("--mesh", type=int, default=None,
                     help="elements per side (2D) or elements (1D); profiling of small cases")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
@@ -541,6 +605,13 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "adjoint":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the adjoint workload reports its own adjoint/forward ratio"}))
+            return
+        run_adjoint(args)
+        return
     if args.workload == "ensemble":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":

@@ -187,6 +187,20 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** s
 crkfr_status crkfr_step_local(crkfr_ctx* ctx, const double* u_dev, double dt, void* stream);
 crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
 
+/* Adjoint of one 2D shallow-water step with fixed dt > 0 (GL nodes, context
+ * not in subdomain mode).  With u^{n+1} = S(u^n; b) the step of crkfr_step
+ * and a scalar J: given ubar1 = dJ/du^{n+1} (device, state layout), writes
+ * ubar0 = (dS/du^n)^T ubar1 and adds (dS/db)^T ubar1 to bbar (device,
+ * coefficient layout [Ey][Ex][n][n]), b being the field passed to
+ * crkfr_set_coefficients.  The exact discrete adjoint of the kernels'
+ * arithmetic; at the non-smooth points |m/h| uses sign(0) = 0 and the
+ * maximum of two wave speeds follows the side the forward step selected.
+ * u_dev is u^n and is not modified; ubar1 and ubar0 must not overlap.  The
+ * simulated time is not changed.  Allocates the adjoint trace buffers on the
+ * first call. */
+crkfr_status crkfr_step_adjoint(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
+                                double* ubar0_dev, double* bbar_dev, double dt, void* stream);
+
 /* Simulated time and the size of the last step taken (synchronises). */
 crkfr_status crkfr_get_time(crkfr_ctx* ctx, double* t_host, double* last_dt_host, void* stream);
 
@@ -212,7 +226,8 @@ typedef enum {
   CRKFR_KERNEL_FACE_2D = 2,    /* 2D face Riemann problems, corrections, update */
   CRKFR_KERNEL_RATE = 3,       /* wave-speed rate of a state (time step)     */
   CRKFR_KERNEL_COEF = 4,       /* static coefficient terms                   */
-  CRKFR_KERNEL_KINDS = 5
+  CRKFR_KERNEL_ADJOINT_2D = 5, /* 2D adjoint step (face and local kernels)   */
+  CRKFR_KERNEL_KINDS = 6
 } crkfr_kernel_kind;
 crkfr_status crkfr_profile_enable(crkfr_ctx* ctx, int32_t enable);
 crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms);

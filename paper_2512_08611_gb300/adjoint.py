@@ -1,0 +1,81 @@
+"""Gradient of a final-time misfit with respect to the bathymetry, through the
+library's hand-written adjoint step (crkfr_step_adjoint), with step-level
+checkpointing.
+
+Forward: the initial state is u0 = (eta0 - b, 0, 0) (a given free surface at
+rest over the bathymetry b), the 2D shallow-water cRK-FR step S(.; b) with a
+fixed dt is applied nsteps times, and the state u_T is returned.  Backward:
+the states are recomputed segment by segment from checkpoints stored every
+``every`` steps, and the adjoint steps run in reverse, accumulating
+dJ/db through the static terms of the step (g b_x, g b_y, the face jumps of
+b) and, at the end, through the initial condition (h0 = eta0 - b).
+
+``BathymetryToState`` is a torch.autograd.Function, so any differentiable
+torch expression of u_T and b can serve as J; ``surface_misfit`` is the
+L2 misfit of the free surface h + b at the final time.
+"""
+import torch
+
+
+def quadrature_weights(solver):
+    """w_p w_q dx dy per node, shaped like one variable of the state."""
+    _, w = solver.nodes()
+    Ex, Ey = solver.n_elem
+    dx = (solver.hi[0] - solver.lo[0]) / Ex
+    dy = (solver.hi[1] - solver.lo[1]) / Ey
+    W = torch.tensor(w[:, None] * w[None, :] * dx * dy, dtype=torch.float64, device="cuda")
+    return W.expand(Ey, Ex, solver.n, solver.n)
+
+
+def initial_state(eta0, b):
+    z = torch.zeros_like(b)
+    return torch.stack([eta0 - b, z, z])
+
+
+class BathymetryToState(torch.autograd.Function):
+    """u_T(b) for a 2D swe Solver (GL nodes) with fixed dt."""
+
+    @staticmethod
+    def forward(ctx, b, solver, eta0, dt, nsteps, every):
+        solver.set_coefficients(b.detach().contiguous())
+        u = initial_state(eta0, b.detach()).contiguous()
+        checkpoints = [u.clone()]
+        done = 0
+        while done < nsteps:
+            k = min(every, nsteps - done)
+            solver.step(u, dt, k)
+            done += k
+            if done < nsteps:
+                checkpoints.append(u.clone())
+        ctx.solver, ctx.dt, ctx.nsteps, ctx.every = solver, dt, nsteps, every
+        ctx.checkpoints = checkpoints
+        ctx.b = b.detach().contiguous()
+        return u
+
+    @staticmethod
+    def backward(ctx, ubar):
+        s, dt, nsteps, every = ctx.solver, ctx.dt, ctx.nsteps, ctx.every
+        s.set_coefficients(ctx.b)
+        ubar = ubar.contiguous().clone()
+        bbar = torch.zeros_like(ctx.b)
+        other = torch.empty_like(ubar)
+        starts = list(range(0, nsteps, every))
+        for seg, start in reversed(list(enumerate(starts))):
+            k = min(every, nsteps - start)
+            states = [ctx.checkpoints[seg].clone()]
+            for _ in range(k - 1):
+                x = states[-1].clone()
+                s.step(x, dt, 1)
+                states.append(x)
+            for x in reversed(states):
+                s.step_adjoint(x, ubar, dt, ubar0=other, bbar=bbar)
+                ubar, other = other, ubar
+        # initial condition h0 = eta0 - b
+        bbar -= ubar[0]
+        return bbar, None, None, None, None, None
+
+
+def surface_misfit(u, b, target, weights):
+    """J = 1/2 sum_nodes w (h + b - target)^2."""
+    d = u[0] + b - target
+    return 0.5 * torch.sum(weights * d * d)

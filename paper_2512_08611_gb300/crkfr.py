@@ -63,6 +63,7 @@ SIGNATURES = {
                                   ctypes.POINTER(_P), _PI64]),
     "crkfr_step_local": (_I32, [_P, _P, _D, _P]),
     "crkfr_step_faces": (_I32, [_P, _P, _P]),
+    "crkfr_step_adjoint": (_I32, [_P, _P, _P, _P, _P, _D, _P]),
     "crkfr_get_time": (_I32, [_P, _PD, _PD, _P]),
     "crkfr_set_time": (_I32, [_P, _D, _P]),
     "crkfr_get_status": (_I32, [_P, _P]),
@@ -304,6 +305,21 @@ class Solver:
                                           int(nsteps), _stream()))
         return u_out
 
+    def step_adjoint(self, u, ubar1, dt, ubar0=None, bbar=None):
+        """ubar0 = (dS/du)^T ubar1; bbar += (dS/db)^T ubar1 for one 2D step of
+        size dt from state u (crkfr_step_adjoint).  Returns (ubar0, bbar)."""
+        import torch
+        if ubar0 is None:
+            ubar0 = torch.empty_like(ubar1)
+        if bbar is None:
+            bbar = torch.zeros(self.coef_shape, dtype=torch.float64, device=u.device)
+        self._check(lib().crkfr_step_adjoint(self.h, self._dev(u, self.shape),
+                                             self._dev(ubar1, self.shape),
+                                             self._dev(ubar0, self.shape),
+                                             self._dev(bbar, self.coef_shape), float(dt),
+                                             _stream()))
+        return ubar0, bbar
+
     def time(self):
         t, dt = ctypes.c_double(), ctypes.c_double()
         self._check(lib().crkfr_get_time(self.h, ctypes.byref(t), ctypes.byref(dt), _stream()))
@@ -320,7 +336,7 @@ class Solver:
     def launch_count(self):
         return lib().crkfr_launch_count(self.h)
 
-    KERNELS = {"step_1d": 0, "local_2d": 1, "face_2d": 2, "rate": 3, "coef": 4}
+    KERNELS = {"step_1d": 0, "local_2d": 1, "face_2d": 2, "rate": 3, "coef": 4, "adjoint_2d": 5}
 
     def profile(self, enable=True):
         """Start (clearing earlier values) or stop per-kernel event timing."""

@@ -32,6 +32,9 @@ struct crkfr_ctx {
   double* d_trx = nullptr;
   double* d_try = nullptr;
   double* d_stage = nullptr;  // device copy of host state for crkfr_step_host
+  double* d_atrx = nullptr;   // adjoint traces and face-jump adjoints (crkfr_step_adjoint)
+  double* d_atry = nullptr;
+  double* d_gbar = nullptr;
   DevState* d_state = nullptr;
   bool coef_set = false;
   bool subdomain = false;   // 2D slab of a larger mesh: halo rows come from outside
@@ -77,6 +80,10 @@ void free_buffers(crkfr_ctx* c) {
   cudaFree(c->d_try);
   cudaFree(c->d_stage);
   cudaFree(c->d_state);
+  cudaFree(c->d_atrx);
+  cudaFree(c->d_atry);
+  cudaFree(c->d_gbar);
+  c->d_atrx = c->d_atry = c->d_gbar = nullptr;
   c->d_snode = c->d_sface = c->d_work = c->d_trx = c->d_try = c->d_stage = nullptr;
   c->d_state = nullptr;
 }
@@ -625,6 +632,63 @@ crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
   if (e) return cuda_fail(c, e, "2D face kernel");
   c->launches += 1;
   c->nstep += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* ubar1, double* ubar0,
+                                double* bbar, double dt, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (c->dim != 2 || c->cfg.system != CRKFR_SYS_SWE_2D)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step is built for 2D shallow water");
+  if (c->cfg.nodes != CRKFR_NODES_GL) return fail(c, CRKFR_ERR_UNSUPPORTED, "GL nodes only");
+  if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "no adjoint in subdomain mode");
+  if (!u || !ubar1 || !ubar0 || !bbar) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
+  const size_t bytes = sizeof(double) * c->n_state;
+  const char *a = (const char*)ubar1, *o = (const char*)ubar0;
+  if (a < o + bytes && o < a + bytes) return fail(c, CRKFR_ERR_ARG, "ubar1 and ubar0 overlap");
+  const int64_t n = c->basis.n, Ne = c->Ex * c->Ey;
+  if (!c->d_atrx) {
+    const size_t tr = (size_t)7 * 2 * Ne * n;
+    if (cudaMalloc(&c->d_atrx, sizeof(double) * tr) != cudaSuccess ||
+        cudaMalloc(&c->d_atry, sizeof(double) * tr) != cudaSuccess ||
+        cudaMalloc(&c->d_gbar, sizeof(double) * 2 * Ne * n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // forward traces of u^n: the local kernel in its residual form (same traces,
+  // no time bookkeeping)
+  StepCtl ctl{};
+  ctl.dt_fixed = dt;
+  ctl.residual = 1;
+  Launch2D L = make2d(c);
+  L.ctl = ctl;
+  L.u_in = u;
+  int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
+  if (e) return cuda_fail(c, e, "2D local kernel");
+  Launch2DAdj A{};
+  A.N = c->cfg.degree;
+  A.Ex = c->Ex;
+  A.Ey = c->Ey;
+  A.dt = dt;
+  A.u = u;
+  A.ubar1 = ubar1;
+  A.ubar0 = ubar0;
+  A.bbar = bbar;
+  A.snode = c->d_snode;
+  A.sface = c->d_sface;
+  A.trx = c->d_trx;
+  A.try_ = c->d_try;
+  A.atrx = c->d_atrx;
+  A.atry = c->d_atry;
+  A.gbar = c->d_gbar;
+  A.tab = c->tab;
+  e = timed(c, CRKFR_KERNEL_ADJOINT_2D, s, [&] { return launch_adjoint_2d(A, s); });
+  if (e) return cuda_fail(c, e, "2D adjoint kernels");
+  c->launches += 3;
   return CRKFR_OK;
 }
 

@@ -143,6 +143,27 @@ struct Launch2D {
   Tables tab;
   StepCtl ctl;
 };
+// Adjoint of one 2D step (kernels_adj2d.cu); the forward local kernel must
+// have written the traces of u^n first.
+struct Launch2DAdj {
+  int N;
+  int64_t Ex, Ey;
+  double dt;
+  const double* u;       // u^n
+  const double* ubar1;   // adjoint of u^{n+1}
+  double* ubar0;         // adjoint of u^n (written)
+  double* bbar;          // adjoint of the nodal bathymetry [Ey][Ex][n][n] (accumulated)
+  const double* snode;
+  const double* sface;
+  const double* trx;     // forward traces of u^n
+  const double* try_;
+  double* atrx;          // adjoint traces [7][2][Ey][Ex][n]
+  double* atry;          // adjoint traces [Ey][2][7][Ex][n]
+  double* gbar;          // adjoint of the face jumps: [Ey][Ex][n] x faces, [Ey][Ex][n] y faces
+  Tables tab;
+};
+int launch_adjoint_2d(const Launch2DAdj& A, void* stream);
+
 int launch_local_2d(const Launch2D& L, void* stream);
 int launch_face_2d(const Launch2D& L, void* stream);
 int launch_rate_2d(const Launch2D& L, int slot, void* stream);
