@@ -13,7 +13,10 @@ Modules
 -------
 basis      reference element: nodes, weights, Lagrange basis, D, l(0), l(1),
            correction-function derivatives (Sec. 2; App. B, Eq. correction.identities)
-tableau    explicit Butcher tableaux (App. C and the readings below)
+tableau    Butcher tableaux: explicit ones, and the double (IMEX) tableaux
+           HT(1,1,2) and SSP3-IMEX(4,3,3) of App. C
+sources    source terms (linear damping, Chezy friction) and the
+           point-implicit stage solve (Sec. 2, Eqs. crkfr.inner, avg.source)
 systems    physical systems: variable-coefficient advection, shallow water
            with bathymetry as a non-conservative product (Sec. 3, Sec. 5.1.3)
 crkfr      the cRK-FR step, residual and time step in 1D and 2D
@@ -44,4 +47,17 @@ matters; the default is listed first):
    tau = 1e-12 for N <= 3 and 1e-4 for N = 4 (see ``fourier``).
 6. 2D is the tensor-product, line-by-line extension; face quantities are
    evaluated at every face node.
+7. The implicit tableau of SSP3-IMEX(4,3,3) as printed in App. C (Eq.
+   ssp33.butcher) disagrees with its own node column (rows 2 and 3 sum to
+   alpha and 2/3 + alpha, the printed c_2, c_3 are 0 and 1) and, so read, is
+   only first order and not L-stable, against the paper's statements.  The
+   oracle takes rows 2 and 3 as (-alpha, alpha, 0, 0) and
+   (0, 1 - alpha, alpha, 0): the rows that sum to the printed c_2 = 0 and
+   c_3 = 1 and that make the pair third order and L-stable (the cited source
+   of the scheme, Pareschi & Russo 2005, has these rows).  Row 4 is used as
+   printed (its sum is 1/2; the printed c_4 = 1 plays no role for an
+   autonomous source).
+8. With a source, the tableau is SSP3-IMEX(4,3,3) at every degree (the
+   paper's stiff tests use it at N = 3; HT(1,1,2) makes the N = 1 step grow
+   under a stiff source), and CFL(N) is that of its explicit part.
 """

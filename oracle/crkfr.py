@@ -15,6 +15,11 @@ Follows Sec. 3 in the paper's order:
                   + (F^num,- - F^tot,-)_{e+1/2} dx g_R + (F^num,+ - F^tot,+)_{e-1/2} dx g_L]
                 (Eq. crkfr.non.cons.final)
 
+With a source term s(u) (Sec. 2, Eqs. crkfr.inner, crkfr, avg.source) the
+inner stages add dt sum_{j<=i} a_ij s(u^(j)) with the implicit tableau of a
+double Butcher tableau, the stage equation being solved point by point
+(oracle.sources), and the final update adds dt S, S = sum_i b_i s(u^(i)).
+
 The readings of the oracle package docstring apply (``nc_face``, ``lam_state``,
 ``coef_dissipation``).  Meshes are uniform and periodic.
 
@@ -25,7 +30,8 @@ px the x-node index).
 import numpy as np
 
 from .basis import Basis
-from .tableau import default_tableau
+from .sources import point_implicit_solve
+from .tableau import ImexTableau, default_tableau, imex_tableau
 from .xp import xp_of
 
 FROZEN, LITERAL, STAGEWISE = "frozen", "literal", "stagewise"
@@ -103,6 +109,48 @@ def face_terms(flux_m, flux_p, U_m, U_p, un_m, un_p, c_m, c_p,
     return T_m, T_p, lam
 
 
+def _set_tableau(obj, N, tableau, source):
+    """Explicit (A, b) for the flux terms and, with a source, the implicit
+    (Ai, bi); the default is default_tableau(N), or imex_tableau(N) when a
+    source is given."""
+    if tableau is None:
+        tableau = imex_tableau(N) if source is not None else default_tableau(N)
+    if isinstance(tableau, ImexTableau):
+        obj.A, obj.b = tableau.Ae, tableau.be
+        obj.Ai, obj.bi = tableau.Ai, tableau.bi
+    else:
+        if source is not None:
+            raise ValueError("a source term needs a double (IMEX) tableau")
+        obj.A, obj.b = tableau
+        obj.Ai = obj.bi = None
+    obj.source = source
+
+
+def inner_stages(obj, u, c, dt, Lfun):
+    """Stages u^(i) of Eq. crkfr.non.cons.final (with a source: Eq.
+    crkfr.inner), the local operators L_i = Lfun(u^(i)) and, with a source,
+    the time-averaged source S = sum_i b_i s(u^(i)) (else None)."""
+    stages, L, Src = [], [], []
+    for i in range(len(obj.b)):
+        acc = 0.0
+        for j in range(i):
+            if obj.A[i, j] != 0.0:
+                acc = acc + obj.A[i, j] * L[j]
+        ui = u - dt * acc
+        if obj.source is not None:
+            for j in range(i):
+                if obj.Ai[i, j] != 0.0:
+                    ui = ui + (dt * obj.Ai[i, j]) * Src[j]
+            ui = point_implicit_solve(obj.source, ui, c, dt * obj.Ai[i, i])
+            Src.append(obj.source.source(ui, c))
+        stages.append(ui)
+        L.append(Lfun(ui))
+    S = None
+    if obj.source is not None:
+        S = sum(bj * sj for bj, sj in zip(obj.bi, Src))
+    return stages, L, S
+
+
 # ----------------------------------------------------------------------------
 # 1D
 # ----------------------------------------------------------------------------
@@ -110,10 +158,10 @@ class Scheme1D:
     """cRK-FR on a uniform periodic 1D mesh of E elements of width dx."""
 
     def __init__(self, system, N, dx, family="gl", tableau=None,
-                 nc_face=FROZEN, lam_state="n", coef_dissipation=False):
+                 nc_face=FROZEN, lam_state="n", coef_dissipation=False, source=None):
         self.sys = system
         self.basis = Basis(N, family)
-        self.A, self.b = tableau if tableau is not None else default_tableau(N)
+        _set_tableau(self, N, tableau, source)
         self.dx = dx
         self.nc_face = nc_face
         self.lam_state = lam_state
@@ -128,21 +176,14 @@ class Scheme1D:
         sy, bs = self.sys, self.basis
         D = bs.D / self.dx
         dc = dloc_1d(D, c)
-        s = len(self.b)
-        stages, L = [], []
-        for i in range(s):
-            acc = 0.0
-            for j in range(i):
-                if self.A[i, j] != 0.0:
-                    acc = acc + self.A[i, j] * L[j]
-            ui = u - dt * acc
-            stages.append(ui)
-            L.append(dloc_1d(D, sy.flux(ui, c)) + sy.ncprod(ui, c, dloc_1d(D, ui), dc))
+        stages, L, S = inner_stages(
+            self, u, c, dt,
+            lambda ui: dloc_1d(D, sy.flux(ui, c)) + sy.ncprod(ui, c, dloc_1d(D, ui), dc))
         F = sum(bj * sy.flux(uj, c) for bj, uj in zip(self.b, stages))
         U = sum(bj * uj for bj, uj in zip(self.b, stages))
         Bloc = sum(bj * sy.ncprod(uj, c, dloc_1d(D, uj), dc)
                    for bj, uj in zip(self.b, stages))
-        out = dict(vol=dloc_1d(D, F) + Bloc,
+        out = dict(vol=dloc_1d(D, F) + Bloc if S is None else dloc_1d(D, F) + Bloc - S,
                    F_r=trace_1d(bs.l1, F), F_l=trace_1d(bs.l0, F),
                    U_r=trace_1d(bs.l1, U), U_l=trace_1d(bs.l0, U),
                    un_r=trace_1d(bs.l1, u), un_l=trace_1d(bs.l0, u),
@@ -265,10 +306,10 @@ class Scheme2D:
     """cRK-FR on a uniform periodic Ey x Ex mesh of dx x dy quads."""
 
     def __init__(self, system, N, dx, dy, family="gl", tableau=None,
-                 nc_face=FROZEN, lam_state="n"):
+                 nc_face=FROZEN, lam_state="n", source=None):
         self.sys = system
         self.basis = Basis(N, family)
-        self.A, self.b = tableau if tableau is not None else default_tableau(N)
+        _set_tableau(self, N, tableau, source)
         self.dx, self.dy = dx, dy
         self.nc_face = nc_face
         self.lam_state = lam_state
@@ -285,15 +326,8 @@ class Scheme2D:
         sy, bs = self.sys, self.basis
         Dx, Dy = bs.D / self.dx, bs.D / self.dy
         dcx, dcy = dlocx_2d(Dx, c), dlocy_2d(Dy, c)
-        stages, L = [], []
-        for i in range(len(self.b)):
-            acc = 0.0
-            for j in range(i):
-                if self.A[i, j] != 0.0:
-                    acc = acc + self.A[i, j] * L[j]
-            ui = u - dt * acc
-            stages.append(ui)
-            L.append(self._L(ui, c, Dx, Dy, dcx, dcy))
+        stages, L, S = inner_stages(self, u, c, dt,
+                                    lambda ui: self._L(ui, c, Dx, Dy, dcx, dcy))
         F = sum(bj * sy.flux_x(uj, c) for bj, uj in zip(self.b, stages))
         G = sum(bj * sy.flux_y(uj, c) for bj, uj in zip(self.b, stages))
         U = sum(bj * uj for bj, uj in zip(self.b, stages))
@@ -301,7 +335,8 @@ class Scheme2D:
                          + sy.ncprod_y(uj, c, dlocy_2d(Dy, uj), dcy))
                    for bj, uj in zip(self.b, stages))
         l0, l1 = bs.l0, bs.l1
-        out = dict(vol=dlocx_2d(Dx, F) + dlocy_2d(Dy, G) + Bloc)
+        vol = dlocx_2d(Dx, F) + dlocy_2d(Dy, G) + Bloc
+        out = dict(vol=vol if S is None else vol - S)
         for name, X in (("F", F), ("U", U), ("un", u), ("c", c)):
             out[name + "_r"] = tracex_2d(l1, X)
             out[name + "_l"] = tracex_2d(l0, X)

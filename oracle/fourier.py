@@ -27,10 +27,12 @@ def tolerance(N):
     return 1e-4 if N >= 4 else 1e-12
 
 
-def amplification(N, nu, kappas, family="gl"):
-    """G(kappa, nu) for every kappa in ``kappas``; shape (K, N+1, N+1)."""
+def amplification(N, nu, kappas, family="gl", tableau=None, source=None):
+    """G(kappa, nu) for every kappa in ``kappas``; shape (K, N+1, N+1).
+    ``tableau``/``source`` as for Scheme1D (a linear source keeps the step
+    linear, so G is still its matrix)."""
     kappas = np.atleast_1d(np.asarray(kappas, dtype=float))
-    sch = Scheme1D(VarCoeffAdvection(), N, 1.0, family=family)
+    sch = Scheme1D(VarCoeffAdvection(), N, 1.0, family=family, tableau=tableau, source=source)
     n, K = N + 1, len(kappas)
     # batch axis enumerates (kappa, column j); one element per Bloch period
     e = np.zeros((1, K, n, 1, n), dtype=complex)
@@ -48,21 +50,24 @@ def kappa_grid(kgrid=KGRID):
     return np.pi * np.arange(kgrid + 1) / kgrid
 
 
-def spectral_radius(N, nu, family="gl", kgrid=KGRID):
-    G = amplification(N, nu, kappa_grid(kgrid), family)
+def spectral_radius(N, nu, family="gl", kgrid=KGRID, tableau=None, source=None):
+    G = amplification(N, nu, kappa_grid(kgrid), family, tableau, source)
     return np.max(np.abs(np.linalg.eigvals(G)))
 
 
-def stable(N, nu, family="gl", kgrid=KGRID, tol=None):
+def stable(N, nu, family="gl", kgrid=KGRID, tol=None, tableau=None):
     tol = tolerance(N) if tol is None else tol
-    return spectral_radius(N, nu, family, kgrid) <= 1.0 + tol
+    return spectral_radius(N, nu, family, kgrid, tableau) <= 1.0 + tol
 
 
-def cfl_number(N, family="gl", kgrid=KGRID, tol=None, halvings=60):
+def cfl_number(N, family="gl", kgrid=KGRID, tol=None, halvings=60, tableau=None):
+    """CFL(N) of the default tableau, or of an explicit tableau (A, b) given
+    as ``tableau`` (for a source term: the explicit part of the IMEX
+    tableau, the source being implicit)."""
     lo, hi = 0.0, 2.0
     for _ in range(halvings):
         mid = 0.5 * (lo + hi)
-        if stable(N, mid, family, kgrid, tol):
+        if stable(N, mid, family, kgrid, tol, tableau):
             lo = mid
         else:
             hi = mid
