@@ -1,7 +1,7 @@
 """Benchmark of the cRK-FR hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload swe2d|swe1d]
+                    [--workload swe2d|swe1d|swe2d-friction|ensemble|adjoint]
 
 A step is one cRK-FR time step (element-local inner stages, time averages,
 face Riemann problems with non-conservative fluctuations, FR corrections,
@@ -59,10 +59,13 @@ HBM_FALLBACK_GBS = 6800.0
 class Workload:
     def __init__(self, name, mesh=None):
         self.name = name
-        if name == "swe2d":
+        self.source, self.source_coef, self.current = None, 0.0, (0.0, 0.0)
+        if name in ("swe2d", "swe2d-friction"):
             side = mesh or 1024
             self.system, self.N, self.E, self.L = "swe2d", 3, (side, side), 100.0
             self.M, self.dim = 3, 2
+            if name == "swe2d-friction":
+                self.source, self.source_coef, self.current = "chezy", 0.0025, (0.3, 0.2)
         elif name == "swe1d":
             self.system, self.N, self.E, self.L = "swe1d", 4, (mesh or 100000,), 100.0
             self.M, self.dim = 2, 1
@@ -78,21 +81,30 @@ class Workload:
 
     def label(self):
         e = "x".join(str(v) for v in self.E)
-        return f"{self.system}-{e}-N{self.N}"
+        fr = f"-chezy{self.source_coef:g}" if self.source else ""
+        return f"{self.system}-{e}-N{self.N}{fr}"
+
+    def cfl_key(self):
+        return "cfl_imex" if self.source else "cfl"
+
+    def oracle_source(self):
+        from oracle.sources import ChezyFriction
+        return ChezyFriction(self.source_coef) if self.source == "chezy" else None
 
     def inputs(self, positions, seed=0):
         from paper_2512_08611_gb300.workloads import SWE1DInput, SWE2DInput, accept_seed
         if self.dim == 2:
-            inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=self.L), positions, seed)
+            inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=self.L, current=self.current),
+                                 positions, seed)
         else:
             inp, _ = accept_seed(lambda s: SWE1DInput(seed=s, L=self.L), positions, seed)
         return inp.state(*positions)
 
     def local_flops_per_element(self):
         """FP64 flops (FMA = 2) of the element-local kernel per element, from
-        the operation count of its formulation."""
+        the operation count of its formulation (paper_2512_08611_gb300.flops)."""
         from paper_2512_08611_gb300.flops import local_flops_per_element
-        return local_flops_per_element(self.system, self.N)
+        return local_flops_per_element(self.system, self.N, imex=self.source is not None)
 
 
 # ---------------------------------------------------------------------------
@@ -188,7 +200,7 @@ def oracle_patch(wl, side):
         y = (np.arange(side)[:, None, None, None] + bs.xi[None, None, :, None]) * dx
         x, y = np.broadcast_arrays(x, y)
         u, b = wl.inputs((x, y))
-        sch = Scheme2D(ShallowWater2D(G), wl.N, dx, dx)
+        sch = Scheme2D(ShallowWater2D(G), wl.N, dx, dx, source=wl.oracle_source())
         dof = side * side * wl.nodes_per_elem * wl.M
     else:
         dx = wl.L / wl.E[0]
@@ -228,7 +240,7 @@ def run_reference(args, wl):
     cpu_threads()
     budget = 90.0
     sch, u, b, dof, side = time_oracle(wl, budget, args.steps + args.warmup)
-    cfl = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")))["cfl"][f"{wl.N}_gl"]
+    cfl = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")))[wl.cfl_key()][f"{wl.N}_gl"]
     v = u
     for _ in range(args.warmup):
         v = sch.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
@@ -272,7 +284,8 @@ def run_ours(args, wl):
     split = world > 1
     if split and wl.dim != 2:
         raise SystemExit("multi-GPU runs use the 2D workload")
-    s = crkfr.Solver(wl.system, wl.N, gravity=G, cfl_safety=0.5)
+    s = crkfr.Solver(wl.system, wl.N, gravity=G, cfl_safety=0.5, source=wl.source,
+                     source_coef=wl.source_coef)
     if split:
         # weak scaling: this rank's slab is a full 1024 x 1024 workload, stacked
         # in y with the other ranks' slabs into one periodic mesh
@@ -382,10 +395,10 @@ def run_ours(args, wl):
     peaks = load_peaks()
     hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
     if wl.dim == 2:
-        kname, files, summary = "local_2d", ["kernels_2d.cu", "device_common.cuh", "tableau.h"], \
-            "k_local_2d__swe2d_N3.md"
+        kname, files = "local_2d", ["local_2d.cuh", "device_common.cuh", "tableau.h"]
+        summary = "k_local_2d__swe2d_friction_N3.md" if wl.source else "k_local_2d__swe2d_N3.md"
     else:
-        kname, files, summary = "step_1d", ["kernels_1d.cu", "device_common.cuh", "tableau.h"], \
+        kname, files, summary = "step_1d", ["step_1d.cuh", "device_common.cuh", "tableau.h"], \
             "k_step_1d__swe1d_N4.md"
     nk, ms_k = prof.get(kname, (0, float("nan")))
     avg_ms = ms_k / max(nk, 1)
@@ -597,7 +610,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="swe2d", choices=["swe2d", "swe1d", "ensemble", "adjoint"])
+    ap.add_argument("--workload", default="swe2d",
+                    choices=["swe2d", "swe1d", "swe2d-friction", "ensemble", "adjoint"])
     ap.add_argument("--mesh", type=int, default=None,
                     help="elements per side (2D) or elements (1D); profiling of small cases")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")

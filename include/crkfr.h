@@ -75,19 +75,36 @@ typedef enum {
   CRKFR_NODES_GLL = 1          /* Gauss-Lobatto-Legendre points, g_2 correction   */
 } crkfr_nodes;
 
+/* Source term s(u) of u_t + ... = s(u) (Sec. 2, Eq. con.law.source), treated
+ * implicitly in the inner stages (Eq. crkfr.inner) with the double tableau
+ * SSP3-IMEX(4,3,3) of App. C (Eq. ssp33.butcher; its implicit rows 2 and 3
+ * are read as the rows that sum to the printed nodes c_2 = 0, c_3 = 1, which
+ * make the pair third order and L-stable as the paper states).  The final
+ * update adds dt sum_i b_i s(u^(i)) (Eqs. crkfr, avg.source).  Each stage's
+ * implicit equation is solved point by point in closed form. */
+typedef enum {
+  CRKFR_SRC_NONE = 0,          /* no source: the explicit tableau of degree N      */
+  CRKFR_SRC_LINEAR_DAMPING = 1,/* s = -K v, advection only (model problem, App. A) */
+  CRKFR_SRC_CHEZY = 2          /* s = (0, -C_f |v| v) on the momentum, shallow water
+                                  only (the friction term of Sec. 5.5), v = hu/h   */
+} crkfr_source;
+
 typedef struct {
   int32_t system;      /* crkfr_system                                               */
   int32_t degree;      /* polynomial degree N                                        */
   int32_t nodes;       /* crkfr_nodes                                                */
-  int32_t reserved;    /* must be 0                                                  */
+  int32_t source;      /* crkfr_source; a source that does not belong to the system
+                          gives CRKFR_ERR_UNSUPPORTED                                */
   double gravity;      /* g for shallow water; ignored for advection                */
   double cfl_safety;   /* C_s of Sec. 5, Eq. time.step.2d; 0 < C_s <= 1             */
   double cfl_number;   /* CFL(N) of Eq. time.step.2d; <= 0 selects the library's own
-                          von Neumann value (crkfr_get_cfl)                          */
+                          von Neumann value (crkfr_get_cfl), which with a source is
+                          that of the explicit part of SSP3-IMEX(4,3,3)              */
+  double source_coef;  /* K or C_f, finite and >= 0; ignored without a source       */
 } crkfr_config;
 
-/* Create a context for one system / degree / node family.  Runs the
- * library's von Neumann analysis of the scheme for linear advection when
+/* Create a context for one system / degree / node family / source.  Runs
+ * the library's von Neumann analysis of the scheme for linear advection when
  * cfg->cfl_number <= 0 (Sec. 5, under Eq. time.step.2d).  *out is set to NULL
  * on failure. */
 crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg);
@@ -187,8 +204,9 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** s
 crkfr_status crkfr_step_local(crkfr_ctx* ctx, const double* u_dev, double dt, void* stream);
 crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
 
-/* Adjoint of one 2D shallow-water step with fixed dt > 0 (GL nodes, context
- * not in subdomain mode).  With u^{n+1} = S(u^n; b) the step of crkfr_step
+/* Adjoint of one 2D shallow-water step with fixed dt > 0 (GL nodes, no
+ * source term, context not in subdomain mode; otherwise
+ * CRKFR_ERR_UNSUPPORTED or CRKFR_ERR_STATE).  With u^{n+1} = S(u^n; b) the step of crkfr_step
  * and a scalar J: given ubar1 = dJ/du^{n+1} (device, state layout), writes
  * ubar0 = (dS/du^n)^T ubar1 and adds (dS/db)^T ubar1 to bbar (device,
  * coefficient layout [Ey][Ex][n][n]), b being the field passed to

@@ -20,6 +20,9 @@ STATUS = {0: "CRKFR_OK", -1: "CRKFR_ERR_ARG", -2: "CRKFR_ERR_UNSUPPORTED", -3: "
           -4: "CRKFR_ERR_NONPHYSICAL", -6: "CRKFR_ERR_STATE", -7: "CRKFR_ERR_ALLOC"}
 SYSTEMS = {"varadv1d": 0, "swe1d": 1, "swe2d": 2}
 NODES = {"gl": 0, "gll": 1}
+# source terms (crkfr_source): None, linear damping -K v (advection), Chezy
+# friction -C_f |v| v on the momentum (shallow water)
+SOURCES = {None: 0, "linear": 1, "chezy": 2}
 NVARS = {"varadv1d": 1, "swe1d": 2, "swe2d": 3}
 DIM = {"varadv1d": 1, "swe1d": 1, "swe2d": 2}
 
@@ -32,9 +35,14 @@ class CrkfrError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int32), ("degree", ctypes.c_int32),
-                ("nodes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("nodes", ctypes.c_int32), ("source", ctypes.c_int32),
                 ("gravity", ctypes.c_double), ("cfl_safety", ctypes.c_double),
-                ("cfl_number", ctypes.c_double)]
+                ("cfl_number", ctypes.c_double), ("source_coef", ctypes.c_double)]
+
+
+def make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source, source_coef):
+    return Config(SYSTEMS[system], degree, NODES[nodes], SOURCES[source], gravity, cfl_safety,
+                  cfl_number, float(source_coef))
 
 
 _P = ctypes.c_void_p
@@ -137,10 +145,11 @@ def math_check(x, op):
 
 
 def step_1d_noalloc(system, degree, n_elem, lo, hi, c, u_in, u_out, dt=0.0, nsteps=1,
-                    nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0):
+                    nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0, source=None,
+                    source_coef=0.0):
     """crkfr_step_1d_noalloc: 1D steps whose scratch lives in the library's
     static device array, for callers that cannot allocate device memory."""
-    cfg = Config(SYSTEMS[system], degree, NODES[nodes], 0, gravity, cfl_safety, cfl_number)
+    cfg = make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source, source_coef)
     ptr = lambda t: ctypes.c_void_p(t.data_ptr())
     st = lib().crkfr_step_1d_noalloc(ctypes.byref(cfg), int(n_elem), float(lo), float(hi), ptr(c),
                                      ptr(u_in), ptr(u_out), float(dt), int(nsteps), _stream())
@@ -154,14 +163,20 @@ class Solver:
 
     ``system``: 'varadv1d', 'swe1d' or 'swe2d'; ``nodes``: 'gl' (Radau
     correction) or 'gll' (g_2 correction).  ``cfl_number`` <= 0 takes the
-    library's own von Neumann CFL(N)."""
+    library's own von Neumann CFL(N).  ``source``: None, 'linear' (s = -K v,
+    advection) or 'chezy' (s = -C_f |v| v on the momentum, shallow water),
+    with ``source_coef`` K or C_f; a source switches the stages to
+    SSP3-IMEX(4,3,3)."""
 
-    def __init__(self, system, degree, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0):
+    def __init__(self, system, degree, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0,
+                 source=None, source_coef=0.0):
         self.system, self.degree, self.family = system, degree, nodes
+        self.source, self.source_coef = source, source_coef
         self.M = NVARS[system]
         self.dim = DIM[system]
         self.n = degree + 1
-        cfg = Config(SYSTEMS[system], degree, NODES[nodes], 0, gravity, cfl_safety, cfl_number)
+        cfg = make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source,
+                          source_coef)
         h = ctypes.c_void_p()
         self._check(lib().crkfr_create(ctypes.byref(h), ctypes.byref(cfg)), None)
         self.h = h
@@ -357,12 +372,13 @@ class Batch:
     """Ragged ensemble of independent 1D meshes advanced together
     (crkfr_batch_*).  ``members``: list of (degree, n_elem, lo, hi)."""
 
-    def __init__(self, system, members, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0):
+    def __init__(self, system, members, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0,
+                 source=None, source_coef=0.0):
         self.system = system
         self.M = NVARS[system]
         self.members = [(int(d), int(e), float(a), float(b)) for d, e, a, b in members]
         n = len(self.members)
-        cfg = Config(SYSTEMS[system], 0, NODES[nodes], 0, gravity, cfl_safety, cfl_number)
+        cfg = make_config(system, 0, nodes, gravity, cfl_safety, cfl_number, source, source_coef)
         deg = (ctypes.c_int32 * n)(*[m[0] for m in self.members])
         ne = (ctypes.c_int64 * n)(*[m[1] for m in self.members])
         lo = (ctypes.c_double * n)(*[m[2] for m in self.members])

@@ -160,6 +160,7 @@ Launch1D make1d(crkfr_ctx* c) {
   L.system = c->cfg.system;
   L.N = c->cfg.degree;
   L.gll = c->cfg.nodes == CRKFR_NODES_GLL;
+  L.imex = c->cfg.source != CRKFR_SRC_NONE;
   L.E = c->Ex;
   L.snode = c->d_snode;
   L.sface = c->d_sface;
@@ -173,6 +174,7 @@ Launch2D make2d(crkfr_ctx* c) {
   Launch2D L{};
   L.N = c->cfg.degree;
   L.gll = c->cfg.nodes == CRKFR_NODES_GLL;
+  L.imex = c->cfg.source != CRKFR_SRC_NONE;
   L.Ex = c->Ex;
   L.Ey = c->Ey;
   L.w = c->d_work;
@@ -272,6 +274,26 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
 
 }  // namespace
 
+namespace crkfr {
+
+crkfr_status check_source(const crkfr_config* cfg) {
+  if (cfg->source == CRKFR_SRC_NONE) return CRKFR_OK;
+  if (cfg->source != CRKFR_SRC_LINEAR_DAMPING && cfg->source != CRKFR_SRC_CHEZY)
+    return CRKFR_ERR_ARG;
+  if (!(cfg->source_coef >= 0.0) || !std::isfinite(cfg->source_coef)) return CRKFR_ERR_ARG;
+  const bool swe = cfg->system == CRKFR_SYS_SWE_1D || cfg->system == CRKFR_SYS_SWE_2D;
+  if (cfg->source == CRKFR_SRC_LINEAR_DAMPING && cfg->system != CRKFR_SYS_VARADV_1D)
+    return CRKFR_ERR_UNSUPPORTED;
+  if (cfg->source == CRKFR_SRC_CHEZY && !swe) return CRKFR_ERR_UNSUPPORTED;
+  return CRKFR_OK;
+}
+
+double source_coef(const crkfr_config& cfg) {
+  return cfg.source == CRKFR_SRC_NONE ? 0.0 : cfg.source_coef;
+}
+
+}  // namespace crkfr
+
 extern "C" {
 
 const char* crkfr_error_string(crkfr_status s) {
@@ -291,13 +313,14 @@ const char* crkfr_last_error(const crkfr_ctx* c) { return c ? c->err.c_str() : "
 
 int64_t crkfr_launch_count(const crkfr_ctx* c) { return c ? c->launches : 0; }
 
+
 crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg) {
   if (!out) return CRKFR_ERR_ARG;
   *out = nullptr;
   if (!cfg) return CRKFR_ERR_ARG;
-  if (cfg->reserved != 0) return CRKFR_ERR_ARG;
   if (cfg->system < CRKFR_SYS_VARADV_1D || cfg->system > CRKFR_SYS_SWE_2D)
     return CRKFR_ERR_UNSUPPORTED;
+  if (crkfr_status st = check_source(cfg); st != CRKFR_OK) return st;
   if (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL) return CRKFR_ERR_UNSUPPORTED;
   const int minN = (cfg->system == CRKFR_SYS_SWE_2D || cfg->nodes == CRKFR_NODES_GLL) ? 1 : 0;
   if (cfg->degree < minN || cfg->degree > kMaxN) return CRKFR_ERR_UNSUPPORTED;
@@ -311,7 +334,8 @@ crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg) {
     delete c;
     return CRKFR_ERR_UNSUPPORTED;
   }
-  c->cfl = cfg->cfl_number > 0.0 ? cfg->cfl_number : von_neumann_cfl(c->basis);
+  c->cfl = cfg->cfl_number > 0.0 ? cfg->cfl_number
+                                 : von_neumann_cfl(c->basis, cfg->source != CRKFR_SRC_NONE);
   *out = c;
   return CRKFR_OK;
 }
@@ -369,7 +393,8 @@ crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, co
   const double dy = (c->hi[1] - c->lo[1]) / (double)Ey;
   // 1D kernels take reference-element tables and 1/dx as a scalar
   fill_tables(c->basis, dim == 2 ? dx : 1.0, dim == 2 ? dy : 0.0,
-              c->cfg.system == CRKFR_SYS_VARADV_1D ? 0.0 : c->cfg.gravity, &c->tab);
+              c->cfg.system == CRKFR_SYS_VARADV_1D ? 0.0 : c->cfg.gravity,
+              c->cfg.source != CRKFR_SRC_NONE, source_coef(c->cfg), &c->tab);
   c->xs = (double)Ex / (c->hi[0] - c->lo[0]);   // 1/dx, as the batch path computes it
 
   size_t sn, sf;
@@ -642,6 +667,8 @@ crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* uba
   if (c->dim != 2 || c->cfg.system != CRKFR_SYS_SWE_2D)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step is built for 2D shallow water");
   if (c->cfg.nodes != CRKFR_NODES_GL) return fail(c, CRKFR_ERR_UNSUPPORTED, "GL nodes only");
+  if (c->cfg.source != CRKFR_SRC_NONE)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step has no source term");
   if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "no adjoint in subdomain mode");
   if (!u || !ubar1 || !ubar0 || !bbar) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");

@@ -191,7 +191,8 @@ bool build_basis(int N, bool gll, HostBasis* out) {
   return true;
 }
 
-void fill_tables(const HostBasis& b, double dx, double dy, double gravity, Tables* T) {
+void fill_tables(const HostBasis& b, double dx, double dy, double gravity, bool imex,
+                 double src_coef, Tables* T) {
   std::memset(T, 0, sizeof(*T));
   const int n = b.n;
   for (int i = 0; i < n; ++i) {
@@ -211,14 +212,15 @@ void fill_tables(const HostBasis& b, double dx, double dy, double gravity, Table
   T->inv_dy = dy > 0.0 ? 1.0 / dy : 0.0;
   T->gravity = gravity;
   T->half_gravity = 0.5 * gravity;
-  T->b0 = tab_b(b.N, 0);
+  T->b0 = host_bref(b.N, imex);
   T->face_g = gravity / T->b0;
+  T->src_coef = src_coef;
 }
 
 namespace {
 
-bool stable_at(const HostBasis& b, double nu, double tau) {
-  const int n = b.n, N = b.N, s = tab_stages(N);
+bool stable_at(const HostBasis& b, bool imex, double nu, double tau) {
+  const int n = b.n, N = b.N, s = host_stages(N, imex);
   // Z = -nu D; stage polynomials P_i(Z) and T = sum_i b_i P_i
   double Z[kMaxNodes][kMaxNodes], P[6][kMaxNodes][kMaxNodes], T[kMaxNodes][kMaxNodes];
   for (int i = 0; i < n; ++i)
@@ -231,7 +233,7 @@ bool stable_at(const HostBasis& b, double nu, double tau) {
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) S[i][j] = 0.0;
     for (int k = 0; k < st; ++k) {
-      double a = tab_a(N, st, k);
+      double a = host_a(N, imex, st, k);
       if (a == 0.0) continue;
       for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) S[i][j] += a * P[k][i][j];
@@ -242,7 +244,7 @@ bool stable_at(const HostBasis& b, double nu, double tau) {
         for (int l = 0; l < n; ++l) v += Z[i][l] * S[l][j];
         P[st][i][j] = v;
       }
-    double bs = tab_b(N, st);
+    double bs = host_b(N, imex, st);
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) T[i][j] += bs * P[st][i][j];
   }
@@ -267,23 +269,23 @@ bool stable_at(const HostBasis& b, double nu, double tau) {
 
 }  // namespace
 
-double von_neumann_cfl(const HostBasis& b) {
+double von_neumann_cfl(const HostBasis& b, bool imex) {
   static std::mutex mu;
-  static double cache[kMaxNodes][2];
-  static bool have[kMaxNodes][2];
+  static double cache[kMaxNodes][2][2];
+  static bool have[kMaxNodes][2][2];
   std::lock_guard<std::mutex> lock(mu);
-  if (have[b.N][b.gll]) return cache[b.N][b.gll];
+  if (have[b.N][b.gll][imex]) return cache[b.N][b.gll][imex];
   const double tau = (b.N >= 4) ? 1e-4 : 1e-12;
   double lo = 0.0, hi = 2.0;
   for (int it = 0; it < 60; ++it) {
     double mid = 0.5 * (lo + hi);
-    if (stable_at(b, mid, tau))
+    if (stable_at(b, imex, mid, tau))
       lo = mid;
     else
       hi = mid;
   }
-  cache[b.N][b.gll] = lo;
-  have[b.N][b.gll] = true;
+  cache[b.N][b.gll][imex] = lo;
+  have[b.N][b.gll][imex] = true;
   return lo;
 }
 

@@ -99,6 +99,7 @@ LaunchBatch1D make(crkfr_batch* b, int N) {
   B.system = b->cfg.system;
   B.N = N;
   B.gll = b->cfg.nodes == CRKFR_NODES_GLL;
+  B.imex = b->cfg.source != CRKFR_SRC_NONE;
   B.inst = b->d_inst;
   B.work = b->d_work[N];
   B.nwork = b->nwork[N];
@@ -180,8 +181,9 @@ crkfr_status crkfr_batch_create(crkfr_batch** out, const crkfr_config* cfg, int3
   if (!cfg || !degrees || !n_elem || !lo || !hi || n <= 0) return CRKFR_ERR_ARG;
   if (cfg->system != CRKFR_SYS_VARADV_1D && cfg->system != CRKFR_SYS_SWE_1D)
     return CRKFR_ERR_UNSUPPORTED;
-  if (cfg->reserved != 0 || (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL))
-    return CRKFR_ERR_ARG;
+  if (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL) return CRKFR_ERR_ARG;
+  if (crkfr_status sst = check_source(cfg); sst != CRKFR_OK) return sst;
+  const bool imex = cfg->source != CRKFR_SRC_NONE;
   if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
   if (cfg->system == CRKFR_SYS_SWE_1D && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
   const bool gll = cfg->nodes == CRKFR_NODES_GLL;
@@ -204,8 +206,8 @@ crkfr_status crkfr_batch_create(crkfr_batch** out, const crkfr_config* cfg, int3
     }
     if (!b->have[N]) {
       build_basis(N, gll, &b->basis[N]);
-      fill_tables(b->basis[N], 1.0, 0.0, g, &b->tab[N]);
-      b->cfl[N] = cfg->cfl_number > 0.0 ? cfg->cfl_number : von_neumann_cfl(b->basis[N]);
+      fill_tables(b->basis[N], 1.0, 0.0, g, imex, source_coef(*cfg), &b->tab[N]);
+      b->cfl[N] = cfg->cfl_number > 0.0 ? cfg->cfl_number : von_neumann_cfl(b->basis[N], imex);
       b->have[N] = true;
     }
     const int64_t nn = N + 1;

@@ -26,11 +26,13 @@ struct Tables {
   double w[kMaxNodes];              // quadrature weights
   double inv_dx, inv_dy;
   double gravity, half_gravity;
-  // The kernels accumulate time averages with the weights b_i / b_0 (so the
-  // first stage is a copy); b_0 multiplies dt instead, and the fluctuation
-  // term, which is not a time average, uses g / b_0.
-  double b0;
-  double face_g;   // g / b_0
+  // The kernels accumulate time averages with the weights b_i / b_ref, b_ref
+  // the first non-zero weight of the tableau (so that stage is a copy);
+  // b_ref multiplies dt instead, and the fluctuation term, which is not a
+  // time average, uses g / b_ref.
+  double b0;       // b_ref
+  double face_g;   // g / b_ref
+  double src_coef; // source coefficient: K (linear damping) or C_f (Chezy)
 };
 
 // Device-resident stepping state of a context.
@@ -67,17 +69,27 @@ struct HostBasis {
   double gL[kMaxNodes] = {}, gR[kMaxNodes] = {};
 };
 
+// api.cu: validity of cfg->source / cfg->source_coef for cfg->system
+// (CRKFR_OK, CRKFR_ERR_ARG or CRKFR_ERR_UNSUPPORTED), and the coefficient the
+// kernels take (0 without a source)
+crkfr_status check_source(const crkfr_config* cfg);
+double source_coef(const crkfr_config& cfg);
+
 // basis.cpp
 bool build_basis(int N, bool gll, HostBasis* out);
-double von_neumann_cfl(const HostBasis& b);
-// Kernel tables for a uniform mesh (dy ignored in 1D, pass 0).
-void fill_tables(const HostBasis& b, double dx, double dy, double gravity, Tables* T);
+// CFL(N) of the explicit tableau the step uses (imex: SSP3-IMEX(4,3,3)).
+double von_neumann_cfl(const HostBasis& b, bool imex);
+// Kernel tables for a uniform mesh (dy ignored in 1D, pass 0); imex selects
+// the weights of SSP3-IMEX(4,3,3), src_coef the source coefficient.
+void fill_tables(const HostBasis& b, double dx, double dy, double gravity, bool imex,
+                 double src_coef, Tables* T);
 
 // Launchers (kernels_1d.cu / kernels_2d.cu).  Return cudaError_t as int.
 struct Launch1D {
   int system;  // crkfr_system
   int N;
   bool gll;
+  bool imex;   // source term with SSP3-IMEX(4,3,3)
   int64_t E;
   const double* u_in;
   double* u_out;
@@ -89,6 +101,7 @@ struct Launch1D {
   StepCtl ctl;
 };
 int launch_step_1d(const Launch1D& L, void* stream);
+int launch_step_1d_imex(const Launch1D& L, void* stream);   // kernels_imex.cu
 int launch_rate_1d(const Launch1D& L, int slot, void* stream);
 int launch_coef_1d(int system, int N, int64_t E, const double* c, double* snode, double* sface,
                    const Tables& tab, void* stream);
@@ -111,6 +124,7 @@ struct LaunchBatch1D {
   int system;
   int N;
   bool gll;
+  bool imex;
   const BatchInstance* inst;
   const WorkItem* work;
   int64_t nwork;
@@ -122,12 +136,14 @@ struct LaunchBatch1D {
   StepCtl ctl;
 };
 int launch_step_1d_batch(const LaunchBatch1D& B, void* stream);
+int launch_step_1d_batch_imex(const LaunchBatch1D& B, void* stream);   // kernels_imex.cu
 int launch_rate_1d_batch(const LaunchBatch1D& B, int slot, void* stream);
 constexpr int kTile1D = 126;   // elements a 1D block owns (128 threads, 2 halo)
 
 struct Launch2D {
   int N;
   bool gll;
+  bool imex;             // Chezy friction with SSP3-IMEX(4,3,3)
   int64_t Ex, Ey;
   const double* u_in;
   double* u_out;         // step: may equal u_in
@@ -165,6 +181,7 @@ struct Launch2DAdj {
 int launch_adjoint_2d(const Launch2DAdj& A, void* stream);
 
 int launch_local_2d(const Launch2D& L, void* stream);
+int launch_local_2d_imex(const Launch2D& L, void* stream);   // kernels_imex.cu
 int launch_face_2d(const Launch2D& L, void* stream);
 int launch_rate_2d(const Launch2D& L, int slot, void* stream);
 // c: [Ey][Ex][n][n] (periodic in y) or, with halo_rows, [Ey+2][Ex][n][n]

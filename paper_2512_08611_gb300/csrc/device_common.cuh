@@ -63,6 +63,11 @@ __device__ __forceinline__ double dsqrt_pos(double x) {
   return fma(q, p, t);
 }
 
+// sigma(f' + B) of shallow water in one direction: |m/h| + sqrt(g h)
+__device__ __forceinline__ double swe_speed(double h, double m, double g) {
+  return fabs(m * drcp(h)) + dsqrt_pos(g * h);
+}
+
 // max of two non-negative doubles through their bit patterns (integer pipe)
 __device__ __forceinline__ double max_nonneg(double a, double b) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);

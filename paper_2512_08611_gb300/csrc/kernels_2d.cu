@@ -31,249 +31,13 @@
 // equation with g h b_x, B_2 on the hv equation with g h b_y.
 #include <cuda_runtime.h>
 
-#include "device_common.cuh"
+#include "local_2d.cuh"
 
 namespace crkfr {
 namespace {
 
 constexpr int kBlock2D = 256;
 constexpr int kWarps2D = kBlock2D / 32;
-// Launch shape of the element-local kernel: FP64 issue needs enough warps
-// in flight, so the block is small and at least CRKFR_LOCAL2D_MINB blocks
-// must fit an SM (the compiler caps the registers accordingly).
-#ifndef CRKFR_LOCAL2D_BLOCK
-#define CRKFR_LOCAL2D_BLOCK 128
-#endif
-#ifndef CRKFR_LOCAL2D_MINB
-#define CRKFR_LOCAL2D_MINB 2
-#endif
-constexpr int kBlockLocal = CRKFR_LOCAL2D_BLOCK;
-constexpr int kWarpsLocal = kBlockLocal / 32;
-constexpr int kTrFields = 7;
-// x-face trace fields: U_h, U_hu, U_hv, F_hu, F_hv (time-averaged x fluxes of
-// hu and hv), h^n, hu^n.  y-face trace fields: U_h, U_hu, U_hv, G_hu, G_hv,
-// h^n, hv^n.  (The time-averaged h fluxes are U_hu and U_hv.)
-
-__device__ __forceinline__ double swe_speed(double h, double m, double g) {
-  return fabs(m * drcp(h)) + dsqrt_pos(g * h);
-}
-
-template <int N, bool GLL, bool RES>
-__global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(const Launch2D L) {
-  constexpr int n = N + 1;
-  constexpr int nn = n * n;
-  constexpr int EPW = 32 / n;          // elements per warp
-  constexpr int S = tab_stages(N);
-  constexpr int NB = 4;                // fields per shared-memory exchange round
-  const Tables& T = L.tab;
-  __shared__ double sm[kWarpsLocal][EPW][NB][n][n];
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int le = lane / n, q = lane - le * n;
-  const int64_t Ne = L.Ex * L.Ey;
-  const int64_t g = ((int64_t)blockIdx.x * kWarpsLocal + warp) * EPW + le;
-  // lanes past EPW*n (n = 3, 5) and lanes past the last element compute on
-  // element 0 and store nothing, neither to memory nor to shared memory
-  const bool lane_ok = le < EPW;
-  const bool active = lane_ok && (g < Ne);
-  const int64_t ge = active ? g : 0;
-  const int lec = lane_ok ? le : 0;
-  double (*X)[n][n] = sm[warp][lec];
-
-  const double dt = RES ? L.ctl.dt_fixed : step_dt(L.ctl, L.st);
-  if (!RES && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(L.ctl, L.st, dt);
-
-  // ---- load row q of u^n and of the static terms g b_x, g b_y ---------------
-  double u0[3][n], gbx[n], gby[n];
-#pragma unroll
-  for (int v = 0; v < 3; ++v)
-#pragma unroll
-    for (int p = 0; p < n; ++p) u0[v][p] = L.u_in[(v * Ne + ge) * nn + q * n + p];
-#pragma unroll
-  for (int p = 0; p < n; ++p) {
-    gbx[p] = L.snode[ge * nn + q * n + p];
-    gby[p] = L.snode[(Ne + ge) * nn + q * n + p];
-  }
-
-  double Ls[S][3][n];
-  double V[3][n], U[3][n], F2[n], F3[n], G3[n];
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    double cur[3][n];
-#pragma unroll
-    for (int v = 0; v < 3; ++v)
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-        double acc = u0[v][p];
-#pragma unroll
-        for (int j = 0; j < i; ++j)
-          if (tab_a(N, i, j) != 0.0) acc = fma(-(dt * tab_a(N, i, j)), Ls[j][v][p], acc);
-        cur[v][p] = acc;
-      }
-    // fluxes at this row's nodes
-    double f2[n], f3[n], g3[n];
-#pragma unroll
-    for (int p = 0; p < n; ++p) {
-      const double h = cur[0][p], mx = cur[1][p], my = cur[2][p];
-      const double r = drcp(h);
-      const double vx = mx * r, vy = my * r;
-      const double ph = (h * h) * T.half_gravity;
-      f2[p] = fma(mx, vx, ph);
-      f3[p] = mx * vy;
-      g3[p] = fma(my, vy, ph);
-    }
-    // y-fluxes (hv, hu hv / h, hv^2/h + g h^2/2) go through shared memory
-    __syncwarp();
-    if (lane_ok) {
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-        X[0][q][p] = cur[2][p];
-        X[1][q][p] = f3[p];
-        X[2][q][p] = g3[p];
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int p = 0; p < n; ++p) {
-      double a0 = T.Dy[q][0] * X[0][0][p];
-      double a1 = fma(cur[0][p], gbx[p], T.Dy[q][0] * X[1][0][p]);
-      double a2 = fma(cur[0][p], gby[p], T.Dy[q][0] * X[2][0][p]);
-#pragma unroll
-      for (int j = 1; j < n; ++j) {
-        a0 = fma(T.Dy[q][j], X[0][j][p], a0);
-        a1 = fma(T.Dy[q][j], X[1][j][p], a1);
-        a2 = fma(T.Dy[q][j], X[2][j][p], a2);
-      }
-#pragma unroll
-      for (int j = 0; j < n; ++j) {
-        a0 = fma(T.Dx[p][j], cur[1][j], a0);
-        a1 = fma(T.Dx[p][j], f2[j], a1);
-        a2 = fma(T.Dx[p][j], f3[j], a2);
-      }
-      Ls[i][0][p] = a0;
-      Ls[i][1][p] = a1;
-      Ls[i][2][p] = a2;
-    }
-    // time averages with the weights b_i / b_0 (first stage: a copy)
-    const double wi = tab_b(N, i) / tab_b(N, 0);
-    if (wi != 0.0) {
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          V[v][p] = (i == 0) ? Ls[i][v][p] : fma(wi, Ls[i][v][p], V[v][p]);
-          U[v][p] = (i == 0) ? cur[v][p] : fma(wi, cur[v][p], U[v][p]);
-        }
-        F2[p] = (i == 0) ? f2[p] : fma(wi, f2[p], F2[p]);
-        F3[p] = (i == 0) ? f3[p] : fma(wi, f3[p], F3[p]);
-        G3[p] = (i == 0) ? g3[p] : fma(wi, g3[p], G3[p]);
-      }
-    }
-  }
-  static_assert(tab_b(N, 0) != 0.0, "accumulators are initialised by the first stage");
-
-  // ---- W = u^n - dt (dloc F + Bloc)  (or -(dloc F + Bloc) for the residual) --
-  // (V holds the time averages divided by b_0)
-  constexpr double b0 = tab_b(N, 0);
-  const double dtb0 = dt * b0;
-  if (active) {
-#pragma unroll
-    for (int v = 0; v < 3; ++v)
-#pragma unroll
-      for (int p = 0; p < n; ++p)
-        L.w[(v * Ne + ge) * nn + q * n + p] = RES ? -b0 * V[v][p] : fma(-dtb0, V[v][p], u0[v][p]);
-  }
-
-  // ---- x-face traces of row q -------------------------------------------------
-  const int64_t tstride = Ne * n;  // one (field, side) plane of a trace array
-  // field f of the x-face traces at node p of this row (f, p constant after unrolling)
-  auto fx = [&](int f, int p) -> double {
-    switch (f) {
-      case 0: return U[0][p];
-      case 1: return U[1][p];
-      case 2: return U[2][p];
-      case 3: return F2[p];
-      case 4: return F3[p];
-      case 5: return u0[0][p];
-      default: return u0[1][p];
-    }
-  };
-  auto fy = [&](int f, int p) -> double {
-    switch (f) {
-      case 0: return U[0][p];
-      case 1: return U[1][p];
-      case 2: return U[2][p];
-      case 3: return F3[p];
-      case 4: return G3[p];
-      case 5: return u0[0][p];
-      default: return u0[2][p];
-    }
-  };
-  {
-    if (active) {
-#pragma unroll
-      for (int f = 0; f < kTrFields; ++f) {
-        double tl, tr;
-        if (GLL) {
-          tl = fx(f, 0);
-          tr = fx(f, N);
-        } else {
-          tl = T.l0[0] * fx(f, 0);
-          tr = T.l1[0] * fx(f, 0);
-#pragma unroll
-          for (int p = 1; p < n; ++p) {
-            tl = fma(T.l0[p], fx(f, p), tl);
-            tr = fma(T.l1[p], fx(f, p), tr);
-          }
-        }
-        L.trx[(2 * f + 0) * tstride + ge * n + q] = tl;
-        L.trx[(2 * f + 1) * tstride + ge * n + q] = tr;
-      }
-    }
-  }
-  // ---- y-face traces of column p = q (two shared-memory rounds) -------------
-  {
-#pragma unroll
-    for (int r0 = 0; r0 < kTrFields; r0 += NB) {
-      __syncwarp();
-      if (lane_ok) {
-#pragma unroll
-        for (int f = r0; f < r0 + NB && f < kTrFields; ++f)
-#pragma unroll
-          for (int p = 0; p < n; ++p) X[f - r0][q][p] = fy(f, p);
-      }
-      __syncwarp();
-      if (active) {
-#pragma unroll
-        for (int f = r0; f < r0 + NB && f < kTrFields; ++f) {
-          double tb, tt;
-          if (GLL) {
-            tb = X[f - r0][0][q];
-            tt = X[f - r0][N][q];
-          } else {
-            tb = T.l0[0] * X[f - r0][0][q];
-            tt = T.l1[0] * X[f - r0][0][q];
-#pragma unroll
-            for (int j = 1; j < n; ++j) {
-              tb = fma(T.l0[j], X[f - r0][j][q], tb);
-              tt = fma(T.l1[j], X[f - r0][j][q], tt);
-            }
-          }
-          // buffer row ey+1; in a periodic mesh the bottom row's bottom side
-          // is also the halo above the top row, and vice versa
-          const int64_t row = ge / L.Ex + 1, col = ge - (row - 1) * L.Ex;
-          const int64_t plane = L.Ex * n;
-          L.try_[((row * 2 + 0) * kTrFields + f) * plane + col * n + q] = tb;
-          L.try_[((row * 2 + 1) * kTrFields + f) * plane + col * n + q] = tt;
-          if (L.periodic_y && row == 1)
-            L.try_[(((L.Ey + 1) * 2 + 0) * kTrFields + f) * plane + col * n + q] = tb;
-          if (L.periodic_y && row == L.Ey)
-            L.try_[((0 * 2 + 1) * kTrFields + f) * plane + col * n + q] = tt;
-        }
-      }
-    }
-  }
-}
 
 // Doubled face terms of both sides of one face node, T'^- = 2 (F^num,- - F^tot,-)
 // and T'^+ = 2 (F^num,+ - F^tot,+), from the two sides' traces.
@@ -317,7 +81,7 @@ __global__ void __launch_bounds__(kBlock2D) k_face_2d(const Launch2D L) {
   const int64_t Ex = L.Ex, Ey = L.Ey, Ne = Ex * Ey, ts = Ne * n;
   const int64_t ex0 = (int64_t)blockIdx.x * TX, ey0 = (int64_t)blockIdx.y * TY;
   // the traces hold time averages divided by b_0: so do the face terms
-  const double dt = (RES ? 1.0 : L.st->dt_cur) * tab_b(N, 0);
+  const double dt = (RES ? 1.0 : L.st->dt_cur) * T.b0;
 
   // ---- phase 1: every face node of the tile once --------------------------
   for (int f = threadIdx.x; f < NX + NY; f += kBlock2D) {
@@ -528,18 +292,6 @@ __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c, 
 }
 
 template <int N, bool GLL>
-int launch_local_t(const Launch2D& L, cudaStream_t s) {
-  constexpr int per_block = kWarpsLocal * (32 / (N + 1));
-  const int64_t blocks = (L.Ex * L.Ey + per_block - 1) / per_block;
-  if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
-  if (L.ctl.residual)
-    k_local_2d<N, GLL, true><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
-  else
-    k_local_2d<N, GLL, false><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
-  return (int)cudaGetLastError();
-}
-
-template <int N, bool GLL>
 int launch_face_t(const Launch2D& L, cudaStream_t s) {
   constexpr int TX = 32 / (N + 1);
   const dim3 grid((unsigned)((L.Ex + TX - 1) / TX), (unsigned)((L.Ey + kWarps2D - 1) / kWarps2D));
@@ -567,8 +319,8 @@ int launch_face_t(const Launch2D& L, cudaStream_t s) {
   return (int)cudaErrorInvalidValue;
 
 int launch_local_2d(const Launch2D& L, void* stream) {
-  cudaStream_t s = (cudaStream_t)stream;
-  CRKFR_DISPATCH_2D(launch_local_t)
+  if (L.imex) return launch_local_2d_imex(L, stream);
+  return launch_local_dispatch<false>(L, (cudaStream_t)stream);
 }
 
 int launch_face_2d(const Launch2D& L, void* stream) {

@@ -56,8 +56,9 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
   if (!cfg || !c_dev || !u_in_dev || !u_out_dev) return CRKFR_ERR_ARG;
   if (cfg->system != CRKFR_SYS_VARADV_1D && cfg->system != CRKFR_SYS_SWE_1D)
     return CRKFR_ERR_UNSUPPORTED;
-  if (cfg->reserved != 0 || cfg->nodes < CRKFR_NODES_GL || cfg->nodes > CRKFR_NODES_GLL)
-    return CRKFR_ERR_ARG;
+  if (cfg->nodes < CRKFR_NODES_GL || cfg->nodes > CRKFR_NODES_GLL) return CRKFR_ERR_ARG;
+  if (crkfr_status sst = check_source(cfg); sst != CRKFR_OK) return sst;
+  const bool imex = cfg->source != CRKFR_SRC_NONE;
   const bool gll = cfg->nodes == CRKFR_NODES_GLL;
   if (cfg->degree < (gll ? 1 : 0) || cfg->degree > kMaxN) return CRKFR_ERR_UNSUPPORTED;
   if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
@@ -92,7 +93,8 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
   }
 
   Tables T;   // reference element; 1/dx goes with the launch
-  fill_tables(b, 1.0, 0.0, cfg->system == CRKFR_SYS_VARADV_1D ? 0.0 : cfg->gravity, &T);
+  fill_tables(b, 1.0, 0.0, cfg->system == CRKFR_SYS_VARADV_1D ? 0.0 : cfg->gravity, imex,
+              source_coef(*cfg), &T);
   const double xs = (double)E / (hi - lo);
 
   // the array keeps the previous call's contents: reset the stepping state
@@ -107,12 +109,13 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
 
   const bool cfl_mode = !(dt > 0.0);
   double cfl = cfg->cfl_number;
-  if (cfl_mode && !(cfl > 0.0)) cfl = von_neumann_cfl(b);
+  if (cfl_mode && !(cfl > 0.0)) cfl = von_neumann_cfl(b, imex);
 
   Launch1D L{};
   L.system = cfg->system;
   L.N = cfg->degree;
   L.gll = gll;
+  L.imex = imex;
   L.E = E;
   L.snode = snode;
   L.sface = sface;

@@ -1,0 +1,402 @@
+// The fused 1D cRK-FR step (sm_103a, FP64): the tile body shared by the
+// single-mesh kernel, the ragged-ensemble kernel and their source-term (IMEX)
+// instantiations, which live in different translation units.
+//
+// Mapping: one thread owns one element and keeps its N+1 nodes of every
+// variable, all inner stages and all time averages in registers (Sec. 3,
+// Eq. crkfr.non.cons.final, inner stages; Eqs. disc.avg.flux,
+// time.avg.soln, local.time.avg.non.cons).  A block of 128 threads updates
+// 126 consecutive elements; its first and last threads recompute the stages
+// of the two neighbouring elements (2 of 128 threads, 1.6% extra FP64) so
+// that the only inter-element coupling, one Riemann problem per face
+// (Eqs. numflux.cons, combined.wave.speed, good.numflux.non.cons,
+// total.F.non.cons), is solved from face traces exchanged through shared
+// memory, and u is read and written once per step.  The step therefore
+// reads u^n from one buffer and writes u^{n+1} to another.
+//
+// Face terms are carried doubled, T' = 2 (F^num,+- - F^tot,+-), and the
+// correction tables hold 0.5 g'(xi_p)/dx, which saves two FP64 multiplies
+// per face.  For GLL nodes the traces are the end values and g_L', g_R'
+// vanish away from the end nodes (App. B, under Eq. fr.gll), which the
+// GLL instantiation uses at compile time.
+//
+// With a source term (IMEX = true; Sec. 2, Eqs. crkfr.inner, crkfr,
+// avg.source) the stages follow SSP3-IMEX(4,3,3): the implicit source terms
+// of earlier stages join the stage sum, each stage's own source term is
+// solved point by point in closed form, and the final update adds
+// dt sum_i b_i s(u^(i)).  Sources: linear damping s = -K v for advection
+// (the model problem of App. A), Chezy friction s = (0, -C_f |v| v) for
+// shallow water (the friction term of Sec. 5.5).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace crkfr {
+namespace {
+
+constexpr int kBlock1D = 128;
+
+template <int SYS>
+struct Sys1D;
+template <>
+struct Sys1D<CRKFR_SYS_VARADV_1D> {
+  static constexpr int M = 1;
+  static constexpr int NLEFT = 2;   // left-trace fields exchanged: V, a
+  static constexpr int SV = 0;      // variable carrying the source (v)
+};
+template <>
+struct Sys1D<CRKFR_SYS_SWE_1D> {
+  static constexpr int M = 2;
+  static constexpr int NLEFT = 6;   // H, M (time averages), F_m, h^n, m^n, b
+  static constexpr int SV = 1;      // variable carrying the source (hu)
+};
+
+template <int N, bool GLL>
+__device__ __forceinline__ double trace_r(const Tables& T, const double* X) {
+  if (GLL) return X[N];
+  double s = T.l1[0] * X[0];
+#pragma unroll
+  for (int p = 1; p <= N; ++p) s = fma(T.l1[p], X[p], s);
+  return s;
+}
+
+template <int N, bool GLL>
+__device__ __forceinline__ double trace_l(const Tables& T, const double* X) {
+  if (GLL) return X[0];
+  double s = T.l0[0] * X[0];
+#pragma unroll
+  for (int p = 1; p <= N; ++p) s = fma(T.l0[p], X[p], s);
+  return s;
+}
+
+// One tile (126 elements plus a halo element on each side) of the fused 1D
+// step of one mesh.  T holds reference-element tables (dx = 1: D, l(0), l(1),
+// 0.5 g'); xs = 1/dx scales the local operator and the corrections through
+// the scalar coefficients only (stage coefficients dt a_ij xs, update
+// coefficient dt b_ref xs), so one table serves meshes of any dx.
+template <int SYS, int N, bool GLL, bool RES, bool IMEX>
+__device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
+                                             const double* __restrict__ u_in,
+                                             double* __restrict__ u_out,
+                                             const double* __restrict__ snode,
+                                             const double* __restrict__ sface, int64_t E,
+                                             int64_t tile, DevState* st, const StepCtl& ctl,
+                                             bool first_tile) {
+  using TB = Tab<N, IMEX>;
+  constexpr int n = N + 1;
+  constexpr int M = Sys1D<SYS>::M;
+  constexpr int NL = Sys1D<SYS>::NLEFT;
+  constexpr int SV = Sys1D<SYS>::SV;
+  constexpr int S = TB::S;
+  constexpr int F0 = TB::first();
+  constexpr bool SWE = (SYS == CRKFR_SYS_SWE_1D);
+  const int t = threadIdx.x;
+  const int64_t e_raw = tile * (kBlock1D - 2) + t - 1;
+  int64_t e = e_raw % E;
+  if (e < 0) e += E;
+  const bool owner = (t >= 1) && (t <= kBlock1D - 2) && (e_raw < E);
+
+  __shared__ double sm_left[NL][kBlock1D];
+  __shared__ double sm_T[M][kBlock1D];
+
+  const double dt = RES ? ctl.dt_fixed : step_dt(ctl, st);
+  if (!RES && first_tile && t == 0) step_bookkeeping(ctl, st, dt);
+  const double dtx = dt * xs;
+
+  // ---- load u^n and the static coefficient terms of this element ----------
+  double u0[M][n];
+#pragma unroll
+  for (int v = 0; v < M; ++v)
+#pragma unroll
+    for (int p = 0; p < n; ++p) u0[v][p] = u_in[((int64_t)v * E + e) * n + p];
+  double sn[n];
+#pragma unroll
+  for (int p = 0; p < n; ++p) sn[p] = snode[e * n + p];
+  const double c_l = sface[2 * e], c_r = sface[2 * e + 1];
+
+  // ---- inner stages (element-local) ----------------------------------------
+  // Time averages are accumulated with the weights b_j / b_ref (the first
+  // weighted stage is a copy); b_ref is applied to dt in the update, and the
+  // fluctuation, the one face term that is not a time average, uses
+  // g / b_ref.
+  double Ls[S][M][n];            // local operator at each stage
+  double Ss[S][n];               // source of variable SV at each stage (IMEX)
+  double V[M][n];                // sum_j (b_j/b_ref) L_j
+  double U[M][n];                // sum_j (b_j/b_ref) u^(j)
+  double F2[n];                  // sum_j (b_j/b_ref) f_2(u^(j)) (shallow water momentum flux)
+  double Sb[n];                  // sum_j (b_j/b_ref) s(u^(j)) (IMEX)
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double cur[M][n];
+#pragma unroll
+    for (int v = 0; v < M; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+        double acc = u0[v][p];
+#pragma unroll
+        for (int j = 0; j < i; ++j)
+          if (TB::a(i, j) != 0.0) acc = fma(-(dtx * TB::a(i, j)), Ls[j][v][p], acc);
+        if (IMEX && v == SV) {
+#pragma unroll
+          for (int j = 0; j < i; ++j)
+            if (TB::ai(i, j) != 0.0) acc = fma(dt * TB::ai(i, j), Ss[j][p], acc);
+        }
+        cur[v][p] = acc;
+      }
+    if constexpr (IMEX) {
+      // point-implicit source of this stage: cur - dt a_ii s(cur) = r
+      const double gam = dt * TB::ai(i, i);
+      if constexpr (SWE) {
+        // s = -C_f |m| m / h^2 with h fixed: |m| + gam C_f |m|^2 / h^2 = |r|
+        const double gcf = gam * T.src_coef;
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+          const double ih = drcp(cur[0][p]);
+          const double ih2 = ih * ih;
+          if (TB::ai(i, i) != 0.0) {
+            const double r = cur[1][p];
+            const double q = dsqrt_pos(fma(4.0 * gcf * ih2, fabs(r), 1.0));
+            cur[1][p] = r * (2.0 * drcp(1.0 + q));
+          }
+          if (TB::need_S(i)) Ss[i][p] = -(T.src_coef * ih2) * fabs(cur[1][p]) * cur[1][p];
+        }
+      } else {
+        // s = -K v
+        const double inv = (TB::ai(i, i) != 0.0) ? drcp(fma(gam, T.src_coef, 1.0)) : 1.0;
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+          if (TB::ai(i, i) != 0.0) cur[0][p] *= inv;
+          if (TB::need_S(i)) Ss[i][p] = -T.src_coef * cur[0][p];
+        }
+      }
+    }
+    const double wi = TB::b(i) / TB::bref();
+    if (TB::need_L(i)) {
+      if constexpr (SWE) {
+        double f2[n];
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+          const double h = cur[0][p], m = cur[1][p];
+          const double vel = m * drcp(h);
+          f2[p] = fma(h * h, T.half_gravity, m * vel);
+        }
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+          double a0 = T.Dx[p][0] * cur[1][0];
+          double a1 = fma(cur[0][p], sn[p], T.Dx[p][0] * f2[0]);
+#pragma unroll
+          for (int j = 1; j < n; ++j) {
+            a0 = fma(T.Dx[p][j], cur[1][j], a0);
+            a1 = fma(T.Dx[p][j], f2[j], a1);
+          }
+          Ls[i][0][p] = a0;
+          Ls[i][1][p] = a1;
+        }
+        if (wi != 0.0) {
+#pragma unroll
+          for (int p = 0; p < n; ++p) F2[p] = (i == F0) ? f2[p] : fma(wi, f2[p], F2[p]);
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+          double a0 = T.Dx[p][0] * cur[0][0];
+#pragma unroll
+          for (int j = 1; j < n; ++j) a0 = fma(T.Dx[p][j], cur[0][j], a0);
+          Ls[i][0][p] = sn[p] * a0;
+        }
+      }
+    }
+    if (wi != 0.0) {
+#pragma unroll
+      for (int v = 0; v < M; ++v)
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+          V[v][p] = (i == F0) ? Ls[i][v][p] : fma(wi, Ls[i][v][p], V[v][p]);
+          U[v][p] = (i == F0) ? cur[v][p] : fma(wi, cur[v][p], U[v][p]);
+        }
+      if constexpr (IMEX) {
+        // the implicit weights b_i equal the explicit ones b~_i
+#pragma unroll
+        for (int p = 0; p < n; ++p) Sb[p] = (i == F0) ? Ss[i][p] : fma(wi, Ss[i][p], Sb[p]);
+      }
+    }
+  }
+
+  // ---- face traces ----------------------------------------------------------
+  double tr_r[NL];  // right (xi = 1) traces, same field order as sm_left
+  if constexpr (SWE) {
+    tr_r[0] = trace_r<N, GLL>(T, U[0]);
+    tr_r[1] = trace_r<N, GLL>(T, U[1]);
+    tr_r[2] = trace_r<N, GLL>(T, F2);
+    tr_r[3] = trace_r<N, GLL>(T, u0[0]);
+    tr_r[4] = trace_r<N, GLL>(T, u0[1]);
+    tr_r[5] = c_r;
+    sm_left[0][t] = trace_l<N, GLL>(T, U[0]);
+    sm_left[1][t] = trace_l<N, GLL>(T, U[1]);
+    sm_left[2][t] = trace_l<N, GLL>(T, F2);
+    sm_left[3][t] = trace_l<N, GLL>(T, u0[0]);
+    sm_left[4][t] = trace_l<N, GLL>(T, u0[1]);
+    sm_left[5][t] = c_l;
+  } else {
+    tr_r[0] = trace_r<N, GLL>(T, U[0]);
+    tr_r[1] = c_r;
+    sm_left[0][t] = trace_l<N, GLL>(T, U[0]);
+    sm_left[1][t] = c_l;
+  }
+  __syncthreads();
+
+  // ---- Riemann problem at the right face (t | t+1), both sides -------------
+  double Tm[M];  // doubled face term on this element's right face (minus side)
+  if (t < kBlock1D - 1) {
+    if constexpr (SWE) {
+      const double Hm = tr_r[0], Mm = tr_r[1], Fm = tr_r[2], hm = tr_r[3], mm = tr_r[4],
+                   bm = tr_r[5];
+      const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
+                   hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
+      const double lam = max_nonneg(swe_speed(hm, mm, T.gravity), swe_speed(hp, mp, T.gravity));
+      // F_h = U_m (the h flux is the momentum)
+      const double dFh = Mp - Mm, dUh = Hp - Hm;
+      const double dFm = Fp - Fm, dUm = Mp - Mm;
+      const double gdb = T.face_g * (bp - bm);
+      Tm[0] = fma(-lam, dUh, dFh);
+      Tm[1] = fma(hm, gdb, fma(-lam, dUm, dFm));
+      const double Tp0 = -fma(lam, dUh, dFh);
+      const double Tp1 = -fma(hp, gdb, fma(lam, dUm, dFm));
+      sm_T[0][t + 1] = Tp0;
+      sm_T[1][t + 1] = Tp1;
+    } else {
+      const double Vm = tr_r[0], am = tr_r[1];
+      const double Vp = sm_left[0][t + 1], ap = sm_left[1][t + 1];
+      const double lam = max_nonneg(fabs(am), fabs(ap));
+      const double dU = Vp - Vm;
+      Tm[0] = (am - lam) * dU;
+      sm_T[0][t + 1] = -(lam + ap) * dU;
+    }
+  }
+  __syncthreads();
+
+  // ---- correction and update (owners only) --------------------------------
+  double rate = 0.0;
+  bool bad = false;
+  if (owner) {
+    double Tp[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) Tp[v] = sm_T[v][t];
+    constexpr double b0 = TB::bref();
+    const double dtb0 = dtx * b0;
+    const double dts = dt * b0;
+    double out[M][n];
+#pragma unroll
+    for (int v = 0; v < M; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+        double R = V[v][p];
+        if (!GLL || p == N) R = fma(Tm[v], T.gRx[p], R);
+        if (!GLL || p == 0) R = fma(Tp[v], T.gLx[p], R);
+        double o = RES ? -(b0 * xs) * R : fma(-dtb0, R, u0[v][p]);
+        if (IMEX && v == SV) o = fma(RES ? b0 : dts, Sb[p], o);
+        out[v][p] = o;
+        u_out[((int64_t)v * E + e) * n + p] = o;
+      }
+    if (!RES) {
+      if constexpr (SWE) {
+#pragma unroll
+        for (int p = 0; p < n; ++p) bad |= !positive_finite(out[0][p]) || !finite(out[1][p]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < n; ++p) bad |= !finite(out[0][p]);
+      }
+      if (ctl.want_rate) {
+        double hb = T.w[0] * out[0][0];
+#pragma unroll
+        for (int p = 1; p < n; ++p) hb = fma(T.w[p], out[0][p], hb);
+        if constexpr (SWE) {
+          double mb = T.w[0] * out[1][0];
+#pragma unroll
+          for (int p = 1; p < n; ++p) mb = fma(T.w[p], out[1][p], mb);
+          rate = swe_speed(hb, mb, T.gravity) * xs;
+        } else {
+          // the speed of advection is |a| averaged over the element
+          double ab = T.w[0] * sn[0];
+#pragma unroll
+          for (int p = 1; p < n; ++p) ab = fma(T.w[p], sn[p], ab);
+          rate = fabs(ab) * xs;
+        }
+      }
+    }
+  }
+  if (!RES) {
+    if (bad) atomicOr(&st->status, 1u);
+    if (ctl.want_rate) block_max_atomic<kBlock1D>(rate, &st->rate[ctl.slot_write]);
+  }
+}
+
+template <int SYS, int N, bool GLL, bool RES, bool IMEX>
+__global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
+  step_1d_tile<SYS, N, GLL, RES, IMEX>(L.tab, L.xs, L.u_in, L.u_out, L.snode, L.sface, L.E,
+                                       blockIdx.x, L.st, L.ctl, blockIdx.x == 0);
+}
+
+// ragged ensembles: one (instance, tile) pair per block
+template <int SYS, int N, bool GLL, bool IMEX>
+__global__ void __launch_bounds__(kBlock1D) k_step_1d_batch(const LaunchBatch1D B) {
+  const WorkItem w = B.work[blockIdx.x];
+  const BatchInstance I = B.inst[w.inst];
+  step_1d_tile<SYS, N, GLL, false, IMEX>(B.tab, I.xs, B.u_in + I.u_off, B.u_out + I.u_off,
+                                         B.snode + I.sn_off, B.sface + I.sf_off, I.E, w.tile,
+                                         I.st, B.ctl, w.tile == 0);
+}
+
+template <int SYS, int N, bool GLL, bool IMEX>
+int launch_step_t(const Launch1D& L, cudaStream_t s) {
+  const int64_t blocks = (L.E + kBlock1D - 3) / (kBlock1D - 2);
+  if (L.ctl.residual)
+    k_step_1d<SYS, N, GLL, true, IMEX><<<(unsigned)blocks, kBlock1D, 0, s>>>(L);
+  else
+    k_step_1d<SYS, N, GLL, false, IMEX><<<(unsigned)blocks, kBlock1D, 0, s>>>(L);
+  return (int)cudaGetLastError();
+}
+
+template <int SYS, bool IMEX>
+int launch_step_sys(const Launch1D& L, cudaStream_t s) {
+  switch (L.N * 2 + (L.gll ? 1 : 0)) {
+    case 0: return launch_step_t<SYS, 0, false, IMEX>(L, s);
+    case 2: return launch_step_t<SYS, 1, false, IMEX>(L, s);
+    case 3: return launch_step_t<SYS, 1, true, IMEX>(L, s);
+    case 4: return launch_step_t<SYS, 2, false, IMEX>(L, s);
+    case 5: return launch_step_t<SYS, 2, true, IMEX>(L, s);
+    case 6: return launch_step_t<SYS, 3, false, IMEX>(L, s);
+    case 7: return launch_step_t<SYS, 3, true, IMEX>(L, s);
+    case 8: return launch_step_t<SYS, 4, false, IMEX>(L, s);
+    case 9: return launch_step_t<SYS, 4, true, IMEX>(L, s);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+template <int SYS, int N, bool GLL, bool IMEX>
+int launch_batch_t(const LaunchBatch1D& B, cudaStream_t s) {
+  if (B.nwork <= 0) return 0;
+  k_step_1d_batch<SYS, N, GLL, IMEX><<<(unsigned)B.nwork, kBlock1D, 0, s>>>(B);
+  return (int)cudaGetLastError();
+}
+
+template <int SYS, bool IMEX>
+int launch_batch_sys(const LaunchBatch1D& B, cudaStream_t s) {
+  switch (B.N * 2 + (B.gll ? 1 : 0)) {
+    case 0: return launch_batch_t<SYS, 0, false, IMEX>(B, s);
+    case 2: return launch_batch_t<SYS, 1, false, IMEX>(B, s);
+    case 3: return launch_batch_t<SYS, 1, true, IMEX>(B, s);
+    case 4: return launch_batch_t<SYS, 2, false, IMEX>(B, s);
+    case 5: return launch_batch_t<SYS, 2, true, IMEX>(B, s);
+    case 6: return launch_batch_t<SYS, 3, false, IMEX>(B, s);
+    case 7: return launch_batch_t<SYS, 3, true, IMEX>(B, s);
+    case 8: return launch_batch_t<SYS, 4, false, IMEX>(B, s);
+    case 9: return launch_batch_t<SYS, 4, true, IMEX>(B, s);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+}  // namespace crkfr

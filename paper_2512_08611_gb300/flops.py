@@ -22,6 +22,15 @@ two wave speeds (1/h 3 FMA, |m/h| + sqrt(g h) with the 5-instruction square
 root: 6 FMA + 4 MUL + 1 ADD each), 5 ADD + 1 MUL of differences, 6 FMA of
 face terms; corrections and update 3 FMA per variable and node; the next
 time step's rate: element means 2 (n - 1) FMA + 2 MUL, one wave speed, 1 MUL.
+
+With Chezy friction (imex=True, SSP3-IMEX(4,3,3), 2D) per node and stage:
+stage value nnz~_i FMA per variable plus nnz_i FMA per momentum; the
+closed-form implicit solve 14 FMA + 11 MUL + 1 ADD (1/h, |r| through the
+5-instruction square root, sqrt(1 + 4 k |r|), 1/(1 + q), m = r f); the
+source -C_f |m| m / h^2 4 MUL; the fluxes and local operator only on stages
+whose operator is used (their 1/h shared with the solve: 2 FMA + 5 MUL);
+time averages 11 FMA (with the two source averages) on weighted stages
+after the first; W 5 FMA per node.
 """
 import numpy as np
 
@@ -31,8 +40,35 @@ def _tableau(N):
     return stages_nnz_b(N)
 
 
-def local_flops_per_element(system, N):
+def _imex_swe2d(N):
+    from .tableau_py import imex_structure
+    t = imex_structure()
     n = N + 1
+    fma = mul = add = 0
+    first = t["b"].index(True)
+    for i in range(4):
+        fma += 3 * t["nnz_e"][i] + 2 * t["nnz_i"][i]
+        fma += 14
+        mul += 11
+        add += 1
+        mul += 4
+        if t["need_L"][i]:
+            fma += 2 + (6 * n - 1)
+            mul += 5 + 3
+        if t["b"][i] and i > first:
+            fma += 11
+    fma += 5
+    per_node = 2 * fma + mul + add
+    traces = 2 * n * 7 * 2 * (1 + 2 * (n - 1))
+    return per_node * n * n + traces
+
+
+def local_flops_per_element(system, N, imex=False):
+    n = N + 1
+    if imex:
+        if system != "swe2d":
+            raise ValueError("the IMEX operation count is written out for swe2d")
+        return _imex_swe2d(N)
     nnz, bnz = _tableau(N)
     fma = mul = 0
     if system == "swe2d":

@@ -17,6 +17,9 @@ Workloads (all periodic, FP64):
 * ``swe2d``: 2D shallow water on [0, 100]^2: b is a sum of 32 Gaussians
   (same ranges), h + b = 1 + 0.01 G(x, y) with G one unit Gaussian bump of
   width U[1, 5] at a random centre, zero velocity.
+* ``swe2d-friction``: the same fields with a uniform current, velocity
+  (0.3, 0.2), under Chezy friction C_f = 0.0025 (g / C^2 with a Chezy
+  constant C of about 63 m^(1/2)/s).
 
 Distances are periodic (d = min(|x - c|, L - |x - c|) per coordinate).  A
 seed whose minimum depth h = 1 + 0.01 p - b falls below 0.1 on the sampled
@@ -86,8 +89,10 @@ class SWE1DInput:
 class SWE2DInput:
     """Seeded 2D bathymetry / free-surface recipe on [0, L]^2."""
 
-    def __init__(self, seed=0, L=100.0, n_gauss=32, amp=(0.05, 0.3), width=(1.0, 5.0)):
+    def __init__(self, seed=0, L=100.0, n_gauss=32, amp=(0.05, 0.3), width=(1.0, 5.0),
+                 current=(0.0, 0.0)):
         self.L = L
+        self.current = tuple(float(c) for c in current)
         rng = np.random.default_rng(seed)
         self.amp = rng.uniform(amp[0], amp[1], n_gauss)
         self.width = rng.uniform(width[0], width[1], n_gauss)
@@ -117,8 +122,7 @@ class SWE2DInput:
         """(h, hu, hv) at positions (x, y) and the bathymetry b."""
         b = self.b(x, y)
         h = self.eta(x, y) - b
-        z = np.zeros_like(h)
-        return np.stack([h, z, z]), b
+        return np.stack([h, self.current[0] * h, self.current[1] * h]), b
 
 
 def accept_seed(make, positions, seed, min_depth=0.1, tries=64):

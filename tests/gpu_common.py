@@ -14,6 +14,12 @@ def golden_cfl(N, family):
         return json.load(fh)["cfl"][f"{N}_{family}"]
 
 
+def golden_cfl_imex(N, family):
+    """CFL(N) of the explicit part of the IMEX tableau (used with a source)."""
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")) as fh:
+        return json.load(fh)["cfl_imex"][f"{N}_{family}"]
+
+
 def load():
     from paper_2512_08611_gb300 import build
     build.build_library()

@@ -40,8 +40,10 @@ def test_every_declared_symbol_is_exported(crk):
 
 
 def test_config_struct_layout(crk):
-    assert ctypes.sizeof(crk.Config) == 40
+    assert ctypes.sizeof(crk.Config) == 48
+    assert crk.Config.source.offset == 12
     assert crk.Config.gravity.offset == 16
+    assert crk.Config.source_coef.offset == 40
 
 
 def test_bad_configs_are_rejected(crk):
@@ -58,6 +60,23 @@ def test_bad_configs_are_rejected(crk):
     assert e.value.status == -1
     with pytest.raises(CrkfrError):
         Solver("swe1d", 3, gravity=-1.0)
+
+
+def test_bad_source_configs_are_rejected(crk):
+    from paper_2512_08611_gb300.crkfr import Config, CrkfrError, Solver
+    for system, source in (("varadv1d", "chezy"), ("swe1d", "linear"), ("swe2d", "linear")):
+        with pytest.raises(CrkfrError) as e:
+            Solver(system, 2, source=source, source_coef=1.0)
+        assert e.value.status == -2
+    for coef in (-1.0, float("inf"), float("nan")):
+        with pytest.raises(CrkfrError) as e:
+            Solver("swe1d", 2, source="chezy", source_coef=coef)
+        assert e.value.status == -1
+    h = ctypes.c_void_p()
+    cfg = Config(1, 2, 0, 7, 9.81, 0.5, 0.0, 1.0)   # no such source
+    assert crk.lib().crkfr_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
+    # a coefficient without a source is ignored
+    Solver("swe1d", 2, source=None, source_coef=-5.0)
 
 
 def test_calls_before_mesh_are_refused(crk):
@@ -83,6 +102,23 @@ def test_nodes_and_cfl_match_oracle(crk, N, family):
     with open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")) as fh:
         want = json.load(fh)["cfl"][f"{N}_{family}"]
     assert s.cfl() == pytest.approx(want, rel=1e-8)
+
+
+@pytest.mark.parametrize("N", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("family", ["gl", "gll"])
+def test_imex_cfl_matches_oracle(crk, N, family):
+    """With a source the CFL number is that of the explicit part of
+    SSP3-IMEX(4,3,3) (stored by tests/golden/make_golden.py from the oracle)."""
+    if family == "gll" and N == 0:
+        pytest.skip("GLL needs N >= 1")
+    from paper_2512_08611_gb300.crkfr import Solver
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")) as fh:
+        want = json.load(fh)["cfl_imex"][f"{N}_{family}"]
+    s = Solver("varadv1d", N, nodes=family, source="linear", source_coef=1.0)
+    assert s.cfl() == pytest.approx(want, rel=1e-8)
+    if N >= 1:
+        s = Solver("swe2d", N, nodes=family, source="chezy", source_coef=0.01)
+        assert s.cfl() == pytest.approx(want, rel=1e-8)
 
 
 def test_explicit_cfl_number_is_used(crk):
