@@ -71,19 +71,24 @@ def tracey_2d(l, X):
 # ----------------------------------------------------------------------------
 def face_terms(flux_m, flux_p, U_m, U_p, un_m, un_p, c_m, c_p,
                speed, ncprod, nc_face=FROZEN, lam_state="n",
-               stage_m=None, stage_p=None, b=None):
+               stage_m=None, stage_p=None, b=None, dissipated=None):
     """Face term on each side, T^+- = F^num,+- - F^tot,+- (Eq. total.F.non.cons).
 
     ``*_m`` is the left (minus) side of the face, ``*_p`` the right (plus) side.
     ``stage_m/stage_p`` (lists of stage traces) are needed only for the
-    'literal' and 'stagewise' readings.  Returns (T_minus, T_plus, lam).
+    'literal' and 'stagewise' readings.  ``dissipated(U, c)``, if given, is
+    the state whose jump the Rusanov term dissipates (default U itself).
+    Returns (T_minus, T_plus, lam).
     """
     xp = xp_of(U_m, un_m, flux_m)
     if lam_state == "n":
         lam = xp.maximum(speed(un_m, c_m), speed(un_p, c_p))
     else:
         lam = xp.maximum(speed(U_m, c_m), speed(U_p, c_p))
-    Fnum = 0.5 * (flux_m + flux_p) - 0.5 * lam * (U_p - U_m)
+    if dissipated is None:
+        Fnum = 0.5 * (flux_m + flux_p) - 0.5 * lam * (U_p - U_m)
+    else:
+        Fnum = 0.5 * (flux_m + flux_p) - 0.5 * lam * (dissipated(U_p, c_p) - dissipated(U_m, c_m))
     U_num = 0.5 * (U_m + U_p)
     c_num = 0.5 * (c_m + c_p)
     if nc_face == FROZEN:
@@ -201,7 +206,7 @@ class Scheme1D:
         return face_terms(lm["F_r"], lp["F_l"], lm["U_r"], lp["U_l"],
                           lm["un_r"], lp["un_l"], lm["c_r"], lp["c_l"],
                           sy.speed, sy.ncprod, self.nc_face, self.lam_state,
-                          lm.get("st_r"), lp.get("st_l"), self.b)
+                          lm.get("st_r"), lp.get("st_l"), self.b, getattr(sy, "dissipated", None))
 
     # -- full periodic step --------------------------------------------------
     def residual(self, u, c, dt, bloch=None):
@@ -356,7 +361,8 @@ class Scheme2D:
         sy = self.sys
         return face_terms(m["F_r"], p["F_l"], m["U_r"], p["U_l"], m["un_r"], p["un_l"],
                           m["c_r"], p["c_l"], sy.speed_x, sy.ncprod_x, self.nc_face,
-                          self.lam_state, m.get("st_r"), p.get("st_l"), self.b)
+                          self.lam_state, m.get("st_r"), p.get("st_l"), self.b,
+                          getattr(sy, "dissipated", None))
 
     def _yface(self, m, p):
         """y-face between a lower element (``m``, side t) and an upper element
@@ -364,7 +370,8 @@ class Scheme2D:
         sy = self.sys
         return face_terms(m["G_t"], p["G_b"], m["U_t"], p["U_b"], m["un_t"], p["un_b"],
                           m["c_t"], p["c_b"], sy.speed_y, sy.ncprod_y, self.nc_face,
-                          self.lam_state, m.get("st_t"), p.get("st_b"), self.b)
+                          self.lam_state, m.get("st_t"), p.get("st_b"), self.b,
+                          getattr(sy, "dissipated", None))
 
     def _corrections(self, Tr, Tl, Tt, Tb):
         """Correction terms (Eq. crkfr.non.cons.final) from the face terms at

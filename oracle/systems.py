@@ -103,3 +103,59 @@ class ShallowWater2D:
         xp = xp_of(u)
         h, my = u[0], u[2]
         return xp.abs(my / h) + xp.sqrt(self.g * h)
+
+
+class ShallowWater1DWB(ShallowWater1D):
+    """Well-balanced form of 1D shallow water (the variant the paper lists as
+    open, Sec. 6): the hydrostatic pressure moves into the non-conservative
+    product,
+        h_t + m_x = 0,  m_t + (m^2/h)_x + g h (h + b)_x = 0,
+    u = (h, m), c = b, f = (m, m^2/h), B(w)(du, db) = (0, g h (du_h + db)).
+    f' + B has the same eigenvalues as before (v -+ sqrt(g h)), and the
+    Rusanov dissipation of the h equation acts on the free surface
+    eta = h + b (``dissipated``), so that a lake at rest (m = 0, eta
+    constant) has no local, flux, dissipation or fluctuation term."""
+    name = "swe1d_wb"
+
+    def flux(self, u, c):
+        h, m = u[0], u[1]
+        return xp_of(u).stack([m, m * m / h])
+
+    def ncprod(self, u, c, du, dc):
+        xp = xp_of(u, du)
+        h = u[0]
+        return xp.stack([xp.zeros_like(h * dc), self.g * h * (du[0] + dc)])
+
+    def dissipated(self, U, c):
+        return xp_of(U).stack([U[0] + c, U[1]])
+
+
+class ShallowWater2DWB(ShallowWater2D):
+    """Well-balanced form of 2D shallow water: pressure in the products,
+    B1(w)(du, db) = (0, g h (du_h + db), 0), B2(w)(du, db) = (0, 0,
+    g h (du_h + db)), f = (hu, (hu)^2/h, (hu)(hv)/h), g = (hv, (hu)(hv)/h,
+    (hv)^2/h); dissipation of the h equation on eta = h + b."""
+    name = "swe2d_wb"
+
+    def flux_x(self, u, c):
+        h, mx, my = u[0], u[1], u[2]
+        return xp_of(u).stack([mx, mx * mx / h, mx * my / h])
+
+    def flux_y(self, u, c):
+        h, mx, my = u[0], u[1], u[2]
+        return xp_of(u).stack([my, mx * my / h, my * my / h])
+
+    def ncprod_x(self, u, c, du, dc):
+        xp = xp_of(u, du)
+        h = u[0]
+        z = xp.zeros_like(h * dc)
+        return xp.stack([z, self.g * h * (du[0] + dc), z])
+
+    def ncprod_y(self, u, c, du, dc):
+        xp = xp_of(u, du)
+        h = u[0]
+        z = xp.zeros_like(h * dc)
+        return xp.stack([z, z, self.g * h * (du[0] + dc)])
+
+    def dissipated(self, U, c):
+        return xp_of(U).stack([U[0] + c, U[1], U[2]])
