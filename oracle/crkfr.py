@@ -80,6 +80,19 @@ def face_terms(flux_m, flux_p, U_m, U_p, un_m, un_p, c_m, c_p,
     the state whose jump the Rusanov term dissipates (default U itself).
     Returns (T_minus, T_plus, lam).
     """
+    Fn_m, Fn_p, Ft_m, Ft_p, lam = face_fluxes(flux_m, flux_p, U_m, U_p, un_m, un_p, c_m, c_p,
+                                             speed, ncprod, nc_face, lam_state, stage_m,
+                                             stage_p, b, dissipated)
+    return Fn_m - Ft_m, Fn_p - Ft_p, lam
+
+
+def face_fluxes(flux_m, flux_p, U_m, U_p, un_m, un_p, c_m, c_p,
+                speed, ncprod, nc_face=FROZEN, lam_state="n",
+                stage_m=None, stage_p=None, b=None, dissipated=None):
+    """The two parts of the face terms: the time-averaged numerical fluxes
+    F^num,+- = F^num + F^num,nc,+- and the extrapolated total fluxes
+    F^tot,+- = F^+- + F^nc,+- (Eq. total.F.non.cons), and lam.
+    Returns (F^num,-, F^num,+, F^tot,-, F^tot,+, lam)."""
     xp = xp_of(U_m, un_m, flux_m)
     if lam_state == "n":
         lam = xp.maximum(speed(un_m, c_m), speed(un_p, c_p))
@@ -109,9 +122,7 @@ def face_terms(flux_m, flux_p, U_m, U_p, un_m, un_p, c_m, c_p,
                            for bj, sm, sp in zip(b, stage_m, stage_p))
         else:
             raise ValueError(nc_face)
-    T_m = (Fnum + num_nc_m) - (flux_m + ext_nc_m)
-    T_p = (Fnum + num_nc_p) - (flux_p + ext_nc_p)
-    return T_m, T_p, lam
+    return Fnum + num_nc_m, Fnum + num_nc_p, flux_m + ext_nc_m, flux_p + ext_nc_p, lam
 
 
 def _set_tableau(obj, N, tableau, source):

@@ -41,6 +41,8 @@ class ShallowWater1D:
     with v = m / h, so the spectral radius is |v| + sqrt(g h)."""
     M = 2
     name = "swe1d"
+    # admissibility constraints P(u) > 0 (Sec. 2, Eq. uad.form): h > 0
+    admissibility = [lambda u: u[0]]
 
     def __init__(self, g=9.81):
         self.g = g
