@@ -1,7 +1,7 @@
 """Benchmark of the cRK-FR hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload swe2d|swe1d|swe2d-friction|ensemble|adjoint]
+                    [--workload swe2d|swe1d|swe2d-friction|swe2d-wb|ensemble|adjoint]
 
 A step is one cRK-FR time step (element-local inner stages, time averages,
 face Riemann problems with non-conservative fluctuations, FR corrections,
@@ -60,10 +60,12 @@ class Workload:
     def __init__(self, name, mesh=None):
         self.name = name
         self.source, self.source_coef, self.current = None, 0.0, (0.0, 0.0)
-        if name in ("swe2d", "swe2d-friction"):
+        if name in ("swe2d", "swe2d-friction", "swe2d-wb"):
             side = mesh or 1024
             self.system, self.N, self.E, self.L = "swe2d", 3, (side, side), 100.0
             self.M, self.dim = 3, 2
+            if name == "swe2d-wb":
+                self.system = "swe2d_wb"
             if name == "swe2d-friction":
                 self.source, self.source_coef, self.current = "chezy", 0.0025, (0.3, 0.2)
         elif name == "swe1d":
@@ -86,6 +88,11 @@ class Workload:
 
     def cfl_key(self):
         return "cfl_imex" if self.source else "cfl"
+
+    def oracle_system(self):
+        from oracle.systems import ShallowWater1D, ShallowWater2D, ShallowWater2DWB
+        return {"swe2d": ShallowWater2D, "swe2d_wb": ShallowWater2DWB,
+                "swe1d": ShallowWater1D}[self.system](G)
 
     def oracle_source(self):
         from oracle.sources import ChezyFriction
@@ -192,7 +199,6 @@ def profiled_traffic(summary, files, scale):
 def oracle_patch(wl, side):
     from oracle.basis import Basis
     from oracle.crkfr import Scheme1D, Scheme2D
-    from oracle.systems import ShallowWater1D, ShallowWater2D
     bs = Basis(wl.N)
     if wl.dim == 2:
         dx = wl.L / wl.E[0]
@@ -200,13 +206,13 @@ def oracle_patch(wl, side):
         y = (np.arange(side)[:, None, None, None] + bs.xi[None, None, :, None]) * dx
         x, y = np.broadcast_arrays(x, y)
         u, b = wl.inputs((x, y))
-        sch = Scheme2D(ShallowWater2D(G), wl.N, dx, dx, source=wl.oracle_source())
+        sch = Scheme2D(wl.oracle_system(), wl.N, dx, dx, source=wl.oracle_source())
         dof = side * side * wl.nodes_per_elem * wl.M
     else:
         dx = wl.L / wl.E[0]
         x = (np.arange(side)[:, None] + bs.xi[None, :]) * dx
         u, b = wl.inputs((x,))
-        sch = Scheme1D(ShallowWater1D(G), wl.N, dx)
+        sch = Scheme1D(wl.oracle_system(), wl.N, dx)
         dof = side * wl.nodes_per_elem * wl.M
     return sch, u, b, dof
 
@@ -396,7 +402,9 @@ def run_ours(args, wl):
     hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
     if wl.dim == 2:
         kname, files = "local_2d", ["local_2d.cuh", "device_common.cuh", "tableau.h"]
-        summary = "k_local_2d__swe2d_friction_N3.md" if wl.source else "k_local_2d__swe2d_N3.md"
+        summary = ("k_local_2d__swe2d_friction_N3.md" if wl.source else
+                   "k_local_2d__swe2d_wb_N3.md" if wl.system == "swe2d_wb" else
+                   "k_local_2d__swe2d_N3.md")
     else:
         kname, files, summary = "step_1d", ["step_1d.cuh", "device_common.cuh", "tableau.h"], \
             "k_step_1d__swe1d_N4.md"
@@ -611,7 +619,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="swe2d",
-                    choices=["swe2d", "swe1d", "swe2d-friction", "ensemble", "adjoint"])
+                    choices=["swe2d", "swe1d", "swe2d-friction", "swe2d-wb", "ensemble", "adjoint"])
     ap.add_argument("--mesh", type=int, default=None,
                     help="elements per side (2D) or elements (1D); profiling of small cases")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")

@@ -29,7 +29,8 @@
  *   returned by crkfr_get_nodes (position of node p of element e:
  *   lo + (e + xi_p) * dx).
  * - Variables: advection (v); 1D shallow water (h, hu); 2D shallow water
- *   (h, hu, hv).  Degree N is 0..4 (1D) or 1..4 (2D).
+ *   (h, hu, hv) (the same for the well-balanced forms).  Degree N is 0..4
+ *   (1D) or 1..4 (2D).
  * - Pointers named *_dev are device pointers on the current CUDA device;
  *   *_host are host pointers.  The caller owns every pointer it passes; the
  *   library never frees them and keeps none of them past the call.
@@ -64,10 +65,20 @@ typedef enum {
   CRKFR_ERR_ALLOC = -7         /* device or host allocation failed             */
 } crkfr_status;
 
+/* The well-balanced forms move the hydrostatic pressure into the
+ * non-conservative product, g h (h + b)_x, and dissipate the free surface
+ * eta = h + b in the Rusanov flux of the h equation, so that a lake at rest
+ * (hu = 0, eta constant) is kept to round-off; the paper lists well-balanced
+ * cRK methods as open (Sec. 6).  Same variables and layouts as the standard
+ * forms. */
 typedef enum {
   CRKFR_SYS_VARADV_1D = 0,     /* v_t + a(x) v_x = 0, c = a (Sec. 5.1.3)        */
   CRKFR_SYS_SWE_1D = 1,        /* shallow water, c = b, B(w)(du,db) = (0, g h db) */
-  CRKFR_SYS_SWE_2D = 2         /* 2D shallow water, B1 = (0,g h db,0), B2 = (0,0,g h db) */
+  CRKFR_SYS_SWE_2D = 2,        /* 2D shallow water, B1 = (0,g h db,0), B2 = (0,0,g h db) */
+  CRKFR_SYS_SWE_1D_WB = 3,     /* well-balanced 1D: f = (hu, (hu)^2/h),
+                                  B(w)(du,db) = (0, g h (du_h + db))               */
+  CRKFR_SYS_SWE_2D_WB = 4      /* well-balanced 2D: pressure-free fluxes,
+                                  B1 = (0, g h (du_h+db), 0), B2 = (0, 0, g h (du_h+db)) */
 } crkfr_system;
 
 typedef enum {
@@ -204,8 +215,8 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** s
 crkfr_status crkfr_step_local(crkfr_ctx* ctx, const double* u_dev, double dt, void* stream);
 crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
 
-/* Adjoint of one 2D shallow-water step with fixed dt > 0 (GL nodes, no
- * source term, context not in subdomain mode; otherwise
+/* Adjoint of one 2D shallow-water step with fixed dt > 0 (standard form,
+ * GL nodes, no source term, context not in subdomain mode; otherwise
  * CRKFR_ERR_UNSUPPORTED or CRKFR_ERR_STATE).  With u^{n+1} = S(u^n; b) the step of crkfr_step
  * and a scalar J: given ubar1 = dJ/du^{n+1} (device, state layout), writes
  * ubar0 = (dS/du^n)^T ubar1 and adds (dS/db)^T ubar1 to bbar (device,
@@ -274,7 +285,7 @@ crkfr_status crkfr_math_check(const double* x_dev, double* out_dev, int64_t n, i
  * no cudaFree and no allocating library routine, and launches the same
  * kernels as crkfr_step.
  *
- * cfg: as for crkfr_create (CRKFR_SYS_VARADV_1D or CRKFR_SYS_SWE_1D);
+ * cfg: as for crkfr_create (a 1D system);
  * a uniform periodic mesh of n_elem elements on [lo, hi]; c_dev: the
  * coefficient field [elem][p]; u_in_dev, u_out_dev: the state
  * [var][elem][p], the same buffer or not overlapping at all; dt > 0: fixed
@@ -300,8 +311,7 @@ crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n_elem, doub
  * of (instance, 126-element tile) pairs running the same fused step as
  * crkfr_step, so instances of any size share the GPU.
  *
- * crkfr_batch_create: cfg->system CRKFR_SYS_VARADV_1D or CRKFR_SYS_SWE_1D
- * (cfg->degree ignored); n instances with degrees[i], n_elem[i] elements on
+ * crkfr_batch_create: cfg->system a 1D system (cfg->degree ignored); n instances with degrees[i], n_elem[i] elements on
  * [lo[i], hi[i]] (host arrays).  Allocates the batch's device buffers.
  * crkfr_batch_layout: offsets (n+1 values each, host) of every instance in
  * the packed state (instance i's u[var][elem][p] starts at state_offsets[i])

@@ -20,8 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libcrkfr.so"
 
-SOURCES = ["api.cu", "kernels_1d.cu", "kernels_2d.cu", "kernels_imex.cu", "noalloc.cu", "batch.cu",
-           "kernels_adj2d.cu", "basis.cpp"]
+SOURCES = ["api.cu", "kernels_1d.cu", "kernels_2d.cu", "kernels_imex.cu", "kernels_wb.cu",
+           "noalloc.cu", "batch.cu", "kernels_adj2d.cu", "basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 

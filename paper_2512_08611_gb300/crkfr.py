@@ -18,13 +18,15 @@ from .build import library_path
 CRKFR_OK = 0
 STATUS = {0: "CRKFR_OK", -1: "CRKFR_ERR_ARG", -2: "CRKFR_ERR_UNSUPPORTED", -3: "CRKFR_ERR_CUDA",
           -4: "CRKFR_ERR_NONPHYSICAL", -6: "CRKFR_ERR_STATE", -7: "CRKFR_ERR_ALLOC"}
-SYSTEMS = {"varadv1d": 0, "swe1d": 1, "swe2d": 2}
+# the *_wb systems are the well-balanced shallow-water forms (pressure in the
+# non-conservative product, free-surface dissipation)
+SYSTEMS = {"varadv1d": 0, "swe1d": 1, "swe2d": 2, "swe1d_wb": 3, "swe2d_wb": 4}
 NODES = {"gl": 0, "gll": 1}
 # source terms (crkfr_source): None, linear damping -K v (advection), Chezy
 # friction -C_f |v| v on the momentum (shallow water)
 SOURCES = {None: 0, "linear": 1, "chezy": 2}
-NVARS = {"varadv1d": 1, "swe1d": 2, "swe2d": 3}
-DIM = {"varadv1d": 1, "swe1d": 1, "swe2d": 2}
+NVARS = {"varadv1d": 1, "swe1d": 2, "swe2d": 3, "swe1d_wb": 2, "swe2d_wb": 3}
+DIM = {"varadv1d": 1, "swe1d": 1, "swe2d": 2, "swe1d_wb": 1, "swe2d_wb": 2}
 
 
 class CrkfrError(RuntimeError):
@@ -161,7 +163,8 @@ def step_1d_noalloc(system, degree, n_elem, lo, hi, c, u_in, u_out, dt=0.0, nste
 class Solver:
     """One library context: a system, degree and node family on one mesh.
 
-    ``system``: 'varadv1d', 'swe1d' or 'swe2d'; ``nodes``: 'gl' (Radau
+    ``system``: 'varadv1d', 'swe1d', 'swe2d', or the well-balanced
+    shallow-water forms 'swe1d_wb', 'swe2d_wb'; ``nodes``: 'gl' (Radau
     correction) or 'gll' (g_2 correction).  ``cfl_number`` <= 0 takes the
     library's own von Neumann CFL(N).  ``source``: None, 'linear' (s = -K v,
     advection) or 'chezy' (s = -C_f |v| v on the momentum, shallow water),

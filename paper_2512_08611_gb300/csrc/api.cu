@@ -175,6 +175,7 @@ Launch2D make2d(crkfr_ctx* c) {
   L.N = c->cfg.degree;
   L.gll = c->cfg.nodes == CRKFR_NODES_GLL;
   L.imex = c->cfg.source != CRKFR_SRC_NONE;
+  L.wb = sys_is_wb(c->cfg.system);
   L.Ex = c->Ex;
   L.Ey = c->Ey;
   L.w = c->d_work;
@@ -281,7 +282,7 @@ crkfr_status check_source(const crkfr_config* cfg) {
   if (cfg->source != CRKFR_SRC_LINEAR_DAMPING && cfg->source != CRKFR_SRC_CHEZY)
     return CRKFR_ERR_ARG;
   if (!(cfg->source_coef >= 0.0) || !std::isfinite(cfg->source_coef)) return CRKFR_ERR_ARG;
-  const bool swe = cfg->system == CRKFR_SYS_SWE_1D || cfg->system == CRKFR_SYS_SWE_2D;
+  const bool swe = sys_is_swe(cfg->system);
   if (cfg->source == CRKFR_SRC_LINEAR_DAMPING && cfg->system != CRKFR_SYS_VARADV_1D)
     return CRKFR_ERR_UNSUPPORTED;
   if (cfg->source == CRKFR_SRC_CHEZY && !swe) return CRKFR_ERR_UNSUPPORTED;
@@ -318,18 +319,17 @@ crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg) {
   if (!out) return CRKFR_ERR_ARG;
   *out = nullptr;
   if (!cfg) return CRKFR_ERR_ARG;
-  if (cfg->system < CRKFR_SYS_VARADV_1D || cfg->system > CRKFR_SYS_SWE_2D)
-    return CRKFR_ERR_UNSUPPORTED;
+  if (!sys_valid(cfg->system)) return CRKFR_ERR_UNSUPPORTED;
   if (crkfr_status st = check_source(cfg); st != CRKFR_OK) return st;
   if (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL) return CRKFR_ERR_UNSUPPORTED;
-  const int minN = (cfg->system == CRKFR_SYS_SWE_2D || cfg->nodes == CRKFR_NODES_GLL) ? 1 : 0;
+  const int minN = (sys_is_2d(cfg->system) || cfg->nodes == CRKFR_NODES_GLL) ? 1 : 0;
   if (cfg->degree < minN || cfg->degree > kMaxN) return CRKFR_ERR_UNSUPPORTED;
   if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
   if (cfg->system != CRKFR_SYS_VARADV_1D && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
   crkfr_ctx* c = new (std::nothrow) crkfr_ctx();
   if (!c) return CRKFR_ERR_ALLOC;
   c->cfg = *cfg;
-  c->M = cfg->system == CRKFR_SYS_VARADV_1D ? 1 : cfg->system == CRKFR_SYS_SWE_1D ? 2 : 3;
+  c->M = sys_vars(cfg->system);
   if (!build_basis(cfg->degree, cfg->nodes == CRKFR_NODES_GLL, &c->basis)) {
     delete c;
     return CRKFR_ERR_UNSUPPORTED;
@@ -361,7 +361,7 @@ void crkfr_destroy(crkfr_ctx* c) {
 crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, const double* lo,
                             const double* hi) {
   if (!c || !n_elem || !lo || !hi) return fail(c, CRKFR_ERR_ARG, "null argument");
-  const int want = c->cfg.system == CRKFR_SYS_SWE_2D ? 2 : 1;
+  const int want = sys_is_2d(c->cfg.system) ? 2 : 1;
   if (dim != want) return fail(c, CRKFR_ERR_ARG, "dimension does not match the system");
   for (int d = 0; d < dim; ++d) {
     if (n_elem[d] <= 0) return fail(c, CRKFR_ERR_ARG, "element count must be positive");
@@ -665,7 +665,8 @@ crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* uba
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
   if (c->dim != 2 || c->cfg.system != CRKFR_SYS_SWE_2D)
-    return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step is built for 2D shallow water");
+    return fail(c, CRKFR_ERR_UNSUPPORTED,
+                "the adjoint step is built for 2D shallow water in its standard form");
   if (c->cfg.nodes != CRKFR_NODES_GL) return fail(c, CRKFR_ERR_UNSUPPORTED, "GL nodes only");
   if (c->cfg.source != CRKFR_SRC_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step has no source term");

@@ -214,6 +214,8 @@ void fill_tables(const HostBasis& b, double dx, double dy, double gravity, bool 
   T->half_gravity = 0.5 * gravity;
   T->b0 = host_bref(b.N, imex);
   T->face_g = gravity / T->b0;
+  T->inv_b0 = 1.0 / T->b0;
+  T->inv_gravity = gravity > 0.0 ? 1.0 / gravity : 0.0;
   T->src_coef = src_coef;
 }
 

@@ -179,19 +179,18 @@ crkfr_status crkfr_batch_create(crkfr_batch** out, const crkfr_config* cfg, int3
   if (!out) return CRKFR_ERR_ARG;
   *out = nullptr;
   if (!cfg || !degrees || !n_elem || !lo || !hi || n <= 0) return CRKFR_ERR_ARG;
-  if (cfg->system != CRKFR_SYS_VARADV_1D && cfg->system != CRKFR_SYS_SWE_1D)
-    return CRKFR_ERR_UNSUPPORTED;
+  if (!sys_valid(cfg->system) || sys_is_2d(cfg->system)) return CRKFR_ERR_UNSUPPORTED;
   if (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL) return CRKFR_ERR_ARG;
   if (crkfr_status sst = check_source(cfg); sst != CRKFR_OK) return sst;
   const bool imex = cfg->source != CRKFR_SRC_NONE;
   if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
-  if (cfg->system == CRKFR_SYS_SWE_1D && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
+  if (sys_is_swe(cfg->system) && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
   const bool gll = cfg->nodes == CRKFR_NODES_GLL;
   crkfr_batch* b = new (std::nothrow) crkfr_batch();
   if (!b) return CRKFR_ERR_ALLOC;
   b->cfg = *cfg;
   b->n_inst = n;
-  b->M = cfg->system == CRKFR_SYS_SWE_1D ? 2 : 1;
+  b->M = sys_vars(cfg->system);
   const double g = cfg->system == CRKFR_SYS_VARADV_1D ? 0.0 : cfg->gravity;
   std::vector<std::vector<WorkItem>> work(kMaxNodes);
   for (int i = 0; i < n; ++i) {

@@ -11,6 +11,16 @@ namespace crkfr {
 constexpr int kMaxN = 4;
 constexpr int kMaxNodes = kMaxN + 1;
 
+// properties of a crkfr_system value (valid values only)
+inline bool sys_is_swe(int s) {
+  return s == CRKFR_SYS_SWE_1D || s == CRKFR_SYS_SWE_2D || s == CRKFR_SYS_SWE_1D_WB ||
+         s == CRKFR_SYS_SWE_2D_WB;
+}
+inline bool sys_is_wb(int s) { return s == CRKFR_SYS_SWE_1D_WB || s == CRKFR_SYS_SWE_2D_WB; }
+inline bool sys_is_2d(int s) { return s == CRKFR_SYS_SWE_2D || s == CRKFR_SYS_SWE_2D_WB; }
+inline int sys_vars(int s) { return s == CRKFR_SYS_VARADV_1D ? 1 : sys_is_2d(s) ? 3 : 2; }
+inline bool sys_valid(int s) { return s >= CRKFR_SYS_VARADV_1D && s <= CRKFR_SYS_SWE_2D_WB; }
+
 // Reference-element and mesh tables passed to every kernel by value, so they
 // live in the kernel parameter bank (read through the constant cache) and
 // several contexts with different degrees or meshes can coexist.
@@ -32,6 +42,8 @@ struct Tables {
   // time average, uses g / b_ref.
   double b0;       // b_ref
   double face_g;   // g / b_ref
+  double inv_b0;   // 1 / b_ref
+  double inv_gravity;  // 1 / g (0 without gravity)
   double src_coef; // source coefficient: K (linear damping) or C_f (Chezy)
 };
 
@@ -144,6 +156,7 @@ struct Launch2D {
   int N;
   bool gll;
   bool imex;             // Chezy friction with SSP3-IMEX(4,3,3)
+  bool wb;               // well-balanced form
   int64_t Ex, Ey;
   const double* u_in;
   double* u_out;         // step: may equal u_in
@@ -183,6 +196,11 @@ int launch_adjoint_2d(const Launch2DAdj& A, void* stream);
 int launch_local_2d(const Launch2D& L, void* stream);
 int launch_local_2d_imex(const Launch2D& L, void* stream);   // kernels_imex.cu
 int launch_face_2d(const Launch2D& L, void* stream);
+// well-balanced instantiations (kernels_wb.cu)
+int launch_step_1d_wb(const Launch1D& L, void* stream);
+int launch_step_1d_batch_wb(const LaunchBatch1D& B, void* stream);
+int launch_local_2d_wb(const Launch2D& L, void* stream);
+int launch_face_2d_wb(const Launch2D& L, void* stream);
 int launch_rate_2d(const Launch2D& L, int slot, void* stream);
 // c: [Ey][Ex][n][n] (periodic in y) or, with halo_rows, [Ey+2][Ex][n][n]
 // holding the row below and the row above the mesh as rows 0 and Ey+1

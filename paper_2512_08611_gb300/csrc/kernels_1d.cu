@@ -144,9 +144,16 @@ int launch_coef_sys(int N, int64_t E, const double* c, double* snode, double* sf
   return (int)cudaGetLastError();
 }
 
+// the rate and the static terms of the well-balanced form are those of the
+// standard form
+int base_system(int system) {
+  return system == CRKFR_SYS_SWE_1D_WB ? CRKFR_SYS_SWE_1D : system;
+}
+
 }  // namespace
 
 int launch_step_1d(const Launch1D& L, void* stream) {
+  if (L.system == CRKFR_SYS_SWE_1D_WB) return launch_step_1d_wb(L, stream);
   if (L.imex) return launch_step_1d_imex(L, stream);
   cudaStream_t s = (cudaStream_t)stream;
   if (L.system == CRKFR_SYS_SWE_1D) return launch_step_sys<CRKFR_SYS_SWE_1D, false>(L, s);
@@ -155,6 +162,7 @@ int launch_step_1d(const Launch1D& L, void* stream) {
 }
 
 int launch_step_1d_batch(const LaunchBatch1D& B, void* stream) {
+  if (B.system == CRKFR_SYS_SWE_1D_WB) return launch_step_1d_batch_wb(B, stream);
   if (B.imex) return launch_step_1d_batch_imex(B, stream);
   cudaStream_t s = (cudaStream_t)stream;
   if (B.system == CRKFR_SYS_SWE_1D) return launch_batch_sys<CRKFR_SYS_SWE_1D, false>(B, s);
@@ -164,7 +172,7 @@ int launch_step_1d_batch(const LaunchBatch1D& B, void* stream) {
 
 int launch_rate_1d_batch(const LaunchBatch1D& B, int slot, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (B.system == CRKFR_SYS_SWE_1D) return launch_batch_rate_sys<CRKFR_SYS_SWE_1D>(B, slot, s);
+  if (base_system(B.system) == CRKFR_SYS_SWE_1D) return launch_batch_rate_sys<CRKFR_SYS_SWE_1D>(B, slot, s);
   if (B.system == CRKFR_SYS_VARADV_1D)
     return launch_batch_rate_sys<CRKFR_SYS_VARADV_1D>(B, slot, s);
   return (int)cudaErrorInvalidValue;
@@ -172,7 +180,7 @@ int launch_rate_1d_batch(const LaunchBatch1D& B, int slot, void* stream) {
 
 int launch_rate_1d(const Launch1D& L, int slot, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (L.system == CRKFR_SYS_SWE_1D) return launch_rate_sys<CRKFR_SYS_SWE_1D>(L, slot, s);
+  if (base_system(L.system) == CRKFR_SYS_SWE_1D) return launch_rate_sys<CRKFR_SYS_SWE_1D>(L, slot, s);
   if (L.system == CRKFR_SYS_VARADV_1D) return launch_rate_sys<CRKFR_SYS_VARADV_1D>(L, slot, s);
   return (int)cudaErrorInvalidValue;
 }
@@ -180,7 +188,7 @@ int launch_rate_1d(const Launch1D& L, int slot, void* stream) {
 int launch_coef_1d(int system, int N, int64_t E, const double* c, double* snode, double* sface,
                    const Tables& tab, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (system == CRKFR_SYS_SWE_1D)
+  if (base_system(system) == CRKFR_SYS_SWE_1D)
     return launch_coef_sys<CRKFR_SYS_SWE_1D>(N, E, c, snode, sface, tab, s);
   if (system == CRKFR_SYS_VARADV_1D)
     return launch_coef_sys<CRKFR_SYS_VARADV_1D>(N, E, c, snode, sface, tab, s);

@@ -26,7 +26,7 @@ int launch_step_1d_batch_imex(const LaunchBatch1D& B, void* stream) {
 }
 
 int launch_local_2d_imex(const Launch2D& L, void* stream) {
-  return launch_local_dispatch<true>(L, (cudaStream_t)stream);
+  return launch_local_dispatch<true, false>(L, (cudaStream_t)stream);
 }
 
 }  // namespace crkfr

@@ -11,6 +11,10 @@
 // the Riemann problem needs: the time-averaged solution U, the
 // time-averaged normal flux and h^n and the normal momentum at t^n (Eqs.
 // time.avg.soln, combined.wave.speed, good.numflux.non.cons).
+//
+// The well-balanced form (WB) has pressure-free fluxes and the
+// non-conservative terms g h D_x (h + b), g h D_y (h + b): D_x h is a row
+// chain, D_y h reads the other rows of h through shared memory.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,7 +40,7 @@ constexpr int kTrFields = 7;
 // hu and hv), h^n, hu^n.  y-face trace fields: U_h, U_hu, U_hv, G_hu, G_hv,
 // h^n, hv^n.  (The time-averaged h fluxes are U_hu and U_hv.)
 
-template <int N, bool GLL, bool RES, bool IMEX>
+template <int N, bool GLL, bool RES, bool IMEX, bool WB>
 __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(const Launch2D L) {
   using TB = Tab<N, IMEX>;
   constexpr int n = N + 1;
@@ -132,10 +136,15 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
         const double h = cur[0][p], mx = cur[1][p], my = cur[2][p];
         const double r = drcp(h);
         const double vx = mx * r, vy = my * r;
-        const double ph = (h * h) * T.half_gravity;
-        f2[p] = fma(mx, vx, ph);
+        if (WB) {
+          f2[p] = mx * vx;
+          g3[p] = my * vy;
+        } else {
+          const double ph = (h * h) * T.half_gravity;
+          f2[p] = fma(mx, vx, ph);
+          g3[p] = fma(my, vy, ph);
+        }
         f3[p] = mx * vy;
-        g3[p] = fma(my, vy, ph);
       }
       // y-fluxes (hv, hu hv / h, hv^2/h + g h^2/2) go through shared memory
       __syncwarp();
@@ -145,14 +154,29 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
           X[0][q][p] = cur[2][p];
           X[1][q][p] = f3[p];
           X[2][q][p] = g3[p];
+          if (WB) X[3][q][p] = cur[0][p];
         }
       }
       __syncwarp();
 #pragma unroll
       for (int p = 0; p < n; ++p) {
+        // non-conservative factors: g b_x, g b_y, and for the well-balanced
+        // form also g h_x, g h_y
+        double nbx = gbx[p], nby = gby[p];
+        if (WB) {
+          double hx = T.Dx[p][0] * cur[0][0];
+          double hy = T.Dy[q][0] * X[3][0][p];
+#pragma unroll
+          for (int j = 1; j < n; ++j) {
+            hx = fma(T.Dx[p][j], cur[0][j], hx);
+            hy = fma(T.Dy[q][j], X[3][j][p], hy);
+          }
+          nbx = fma(T.gravity, hx, nbx);
+          nby = fma(T.gravity, hy, nby);
+        }
         double a0 = T.Dy[q][0] * X[0][0][p];
-        double a1 = fma(cur[0][p], gbx[p], T.Dy[q][0] * X[1][0][p]);
-        double a2 = fma(cur[0][p], gby[p], T.Dy[q][0] * X[2][0][p]);
+        double a1 = fma(cur[0][p], nbx, T.Dy[q][0] * X[1][0][p]);
+        double a2 = fma(cur[0][p], nby, T.Dy[q][0] * X[2][0][p]);
 #pragma unroll
         for (int j = 1; j < n; ++j) {
           a0 = fma(T.Dy[q][j], X[0][j][p], a0);
@@ -302,29 +326,29 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
   }
 }
 
-template <int N, bool GLL, bool IMEX>
+template <int N, bool GLL, bool IMEX, bool WB>
 int launch_local_t(const Launch2D& L, cudaStream_t s) {
   constexpr int per_block = kWarpsLocal * (32 / (N + 1));
   const int64_t blocks = (L.Ex * L.Ey + per_block - 1) / per_block;
   if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
   if (L.ctl.residual)
-    k_local_2d<N, GLL, true, IMEX><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
+    k_local_2d<N, GLL, true, IMEX, WB><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
   else
-    k_local_2d<N, GLL, false, IMEX><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
+    k_local_2d<N, GLL, false, IMEX, WB><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
   return (int)cudaGetLastError();
 }
 
-template <bool IMEX>
+template <bool IMEX, bool WB>
 int launch_local_dispatch(const Launch2D& L, cudaStream_t s) {
   switch (L.N * 2 + (L.gll ? 1 : 0)) {
-    case 2: return launch_local_t<1, false, IMEX>(L, s);
-    case 3: return launch_local_t<1, true, IMEX>(L, s);
-    case 4: return launch_local_t<2, false, IMEX>(L, s);
-    case 5: return launch_local_t<2, true, IMEX>(L, s);
-    case 6: return launch_local_t<3, false, IMEX>(L, s);
-    case 7: return launch_local_t<3, true, IMEX>(L, s);
-    case 8: return launch_local_t<4, false, IMEX>(L, s);
-    case 9: return launch_local_t<4, true, IMEX>(L, s);
+    case 2: return launch_local_t<1, false, IMEX, WB>(L, s);
+    case 3: return launch_local_t<1, true, IMEX, WB>(L, s);
+    case 4: return launch_local_t<2, false, IMEX, WB>(L, s);
+    case 5: return launch_local_t<2, true, IMEX, WB>(L, s);
+    case 6: return launch_local_t<3, false, IMEX, WB>(L, s);
+    case 7: return launch_local_t<3, true, IMEX, WB>(L, s);
+    case 8: return launch_local_t<4, false, IMEX, WB>(L, s);
+    case 9: return launch_local_t<4, true, IMEX, WB>(L, s);
   }
   return (int)cudaErrorInvalidValue;
 }

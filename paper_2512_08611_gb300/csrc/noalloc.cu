@@ -54,15 +54,14 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
                                               const double* u_in_dev, double* u_out_dev,
                                               double dt, int64_t nsteps, void* stream) {
   if (!cfg || !c_dev || !u_in_dev || !u_out_dev) return CRKFR_ERR_ARG;
-  if (cfg->system != CRKFR_SYS_VARADV_1D && cfg->system != CRKFR_SYS_SWE_1D)
-    return CRKFR_ERR_UNSUPPORTED;
+  if (!sys_valid(cfg->system) || sys_is_2d(cfg->system)) return CRKFR_ERR_UNSUPPORTED;
   if (cfg->nodes < CRKFR_NODES_GL || cfg->nodes > CRKFR_NODES_GLL) return CRKFR_ERR_ARG;
   if (crkfr_status sst = check_source(cfg); sst != CRKFR_OK) return sst;
   const bool imex = cfg->source != CRKFR_SRC_NONE;
   const bool gll = cfg->nodes == CRKFR_NODES_GLL;
   if (cfg->degree < (gll ? 1 : 0) || cfg->degree > kMaxN) return CRKFR_ERR_UNSUPPORTED;
   if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
-  if (cfg->system == CRKFR_SYS_SWE_1D && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
+  if (sys_is_swe(cfg->system) && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
   if (n_elem <= 0 || nsteps < 0 || !(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
     return CRKFR_ERR_ARG;
   if (!std::isfinite(dt) && dt > 0.0) return CRKFR_ERR_ARG;
@@ -70,7 +69,7 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
   HostBasis b;
   if (!build_basis(cfg->degree, gll, &b)) return CRKFR_ERR_UNSUPPORTED;
   const int n = b.n;
-  const int M = cfg->system == CRKFR_SYS_SWE_1D ? 2 : 1;
+  const int M = sys_vars(cfg->system);
   const int64_t E = n_elem;
   // scratch layout (in doubles): snode [E n] | sface [2E] | state [M E n] | DevState
   const int64_t o_sface = round_up(E * n, 32);

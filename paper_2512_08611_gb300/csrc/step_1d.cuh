@@ -27,6 +27,11 @@
 // dt sum_i b_i s(u^(i)).  Sources: linear damping s = -K v for advection
 // (the model problem of App. A), Chezy friction s = (0, -C_f |v| v) for
 // shallow water (the friction term of Sec. 5.5).
+//
+// The well-balanced shallow-water form (SYS = CRKFR_SYS_SWE_1D_WB) drops the
+// pressure from the momentum flux, adds g h D h to the local
+// non-conservative term (g h D (h + b)), and dissipates and fluctuates the
+// free surface eta = h + b instead of h at the faces.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -52,6 +57,8 @@ struct Sys1D<CRKFR_SYS_SWE_1D> {
   static constexpr int NLEFT = 6;   // H, M (time averages), F_m, h^n, m^n, b
   static constexpr int SV = 1;      // variable carrying the source (hu)
 };
+template <>
+struct Sys1D<CRKFR_SYS_SWE_1D_WB> : Sys1D<CRKFR_SYS_SWE_1D> {};
 
 template <int N, bool GLL>
 __device__ __forceinline__ double trace_r(const Tables& T, const double* X) {
@@ -91,7 +98,8 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   constexpr int SV = Sys1D<SYS>::SV;
   constexpr int S = TB::S;
   constexpr int F0 = TB::first();
-  constexpr bool SWE = (SYS == CRKFR_SYS_SWE_1D);
+  constexpr bool SWE = (SYS == CRKFR_SYS_SWE_1D || SYS == CRKFR_SYS_SWE_1D_WB);
+  constexpr bool WB = (SYS == CRKFR_SYS_SWE_1D_WB);
   const int t = threadIdx.x;
   const int64_t e_raw = tile * (kBlock1D - 2) + t - 1;
   int64_t e = e_raw % E;
@@ -180,12 +188,19 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
         for (int p = 0; p < n; ++p) {
           const double h = cur[0][p], m = cur[1][p];
           const double vel = m * drcp(h);
-          f2[p] = fma(h * h, T.half_gravity, m * vel);
+          f2[p] = WB ? m * vel : fma(h * h, T.half_gravity, m * vel);
         }
 #pragma unroll
         for (int p = 0; p < n; ++p) {
           double a0 = T.Dx[p][0] * cur[1][0];
-          double a1 = fma(cur[0][p], sn[p], T.Dx[p][0] * f2[0]);
+          double nc = sn[p];   // g D b, and for the well-balanced form + g D h
+          if (WB) {
+            double dh = T.Dx[p][0] * cur[0][0];
+#pragma unroll
+            for (int j = 1; j < n; ++j) dh = fma(T.Dx[p][j], cur[0][j], dh);
+            nc = fma(T.gravity, dh, nc);
+          }
+          double a1 = fma(cur[0][p], nc, T.Dx[p][0] * f2[0]);
 #pragma unroll
           for (int j = 1; j < n; ++j) {
             a0 = fma(T.Dx[p][j], cur[1][j], a0);
@@ -257,9 +272,13 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
                    hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
       const double lam = max_nonneg(swe_speed(hm, mm, T.gravity), swe_speed(hp, mp, T.gravity));
       // F_h = U_m (the h flux is the momentum)
-      const double dFh = Mp - Mm, dUh = Hp - Hm;
+      const double dFh = Mp - Mm;
       const double dFm = Fp - Fm, dUm = Mp - Mm;
-      const double gdb = T.face_g * (bp - bm);
+      // jump of the dissipated and fluctuating state: h, or eta = h + b for
+      // the well-balanced form (b is static, so in the units of the time
+      // averages, divided by b_ref, its jump carries 1 / b_ref)
+      const double dUh = WB ? fma(T.inv_b0, bp - bm, Hp - Hm) : Hp - Hm;
+      const double gdb = WB ? T.gravity * dUh : T.face_g * (bp - bm);
       Tm[0] = fma(-lam, dUh, dFh);
       Tm[1] = fma(hm, gdb, fma(-lam, dUm, dFm));
       const double Tp0 = -fma(lam, dUh, dFh);

@@ -31,6 +31,11 @@ source -C_f |m| m / h^2 4 MUL; the fluxes and local operator only on stages
 whose operator is used (their 1/h shared with the solve: 2 FMA + 5 MUL);
 time averages 11 FMA (with the two source averages) on weighted stages
 after the first; W 5 FMA per node.
+
+Well-balanced 2D form (system swe2d_wb): the fluxes lose the pressure
+(3 FMA + 5 MUL: 1/h, u, v, and the three products), the local operator gains
+D_x h and D_y h (2 MUL + 2 (n - 1) FMA) and g h_x + g b_x, g h_y + g b_y
+(2 FMA).
 """
 import numpy as np
 
@@ -63,8 +68,25 @@ def _imex_swe2d(N):
     return per_node * n * n + traces
 
 
+def _swe2d_wb(N):
+    n = N + 1
+    nnz, bnz = _tableau(N)
+    fma = mul = 0
+    for i, (k, bz) in enumerate(zip(nnz, bnz)):
+        fma += 3 * k + 3 + (6 * n - 1) + 2 * (n - 1) + 2
+        mul += 5 + 3 + 2
+        if bz and i > 0:
+            fma += 9
+    fma += 3
+    per_node = 2 * fma + mul
+    traces = 2 * n * 7 * 2 * (1 + 2 * (n - 1))
+    return per_node * n * n + traces
+
+
 def local_flops_per_element(system, N, imex=False):
     n = N + 1
+    if system == "swe2d_wb" and not imex:
+        return _swe2d_wb(N)
     if imex:
         if system != "swe2d":
             raise ValueError("the IMEX operation count is written out for swe2d")

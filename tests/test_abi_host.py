@@ -121,6 +121,28 @@ def test_imex_cfl_matches_oracle(crk, N, family):
         assert s.cfl() == pytest.approx(want, rel=1e-8)
 
 
+@pytest.mark.parametrize("system", ["swe1d_wb", "swe2d_wb"])
+def test_well_balanced_systems_configure_like_standard(crk, system):
+    """The well-balanced forms have the standard forms' variables, degrees,
+    CFL numbers and sources."""
+    from paper_2512_08611_gb300.crkfr import CrkfrError, Solver
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")) as fh:
+        g = json.load(fh)
+    for N in (1, 3):
+        assert Solver(system, N).cfl() == pytest.approx(g["cfl"][f"{N}_gl"], rel=1e-8)
+        s = Solver(system, N, source="chezy", source_coef=0.1)
+        assert s.cfl() == pytest.approx(g["cfl_imex"][f"{N}_gl"], rel=1e-8)
+    with pytest.raises(CrkfrError) as e:
+        Solver(system, 2, source="linear", source_coef=1.0)
+    assert e.value.status == -2
+    if system == "swe2d_wb":
+        with pytest.raises(CrkfrError):
+            Solver(system, 0)
+    with pytest.raises(CrkfrError) as e:
+        Solver(system, 2, gravity=0.0)
+    assert e.value.status == -1
+
+
 def test_explicit_cfl_number_is_used(crk):
     from paper_2512_08611_gb300.crkfr import Solver
     assert Solver("swe1d", 3, cfl_number=0.05).cfl() == 0.05
