@@ -1,7 +1,7 @@
 """Benchmark of the cRK-FR hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload swe2d|swe1d|swe2d-friction|swe2d-wb|ensemble|adjoint]
+                    [--workload swe2d|swe1d|swe1d-limited|swe2d-friction|swe2d-wb|ensemble|adjoint]
 
 A step is one cRK-FR time step (element-local inner stages, time averages,
 face Riemann problems with non-conservative fluctuations, FR corrections,
@@ -60,6 +60,7 @@ class Workload:
     def __init__(self, name, mesh=None):
         self.name = name
         self.source, self.source_coef, self.current = None, 0.0, (0.0, 0.0)
+        self.limiter = None
         if name in ("swe2d", "swe2d-friction", "swe2d-wb"):
             side = mesh or 1024
             self.system, self.N, self.E, self.L = "swe2d", 3, (side, side), 100.0
@@ -68,9 +69,11 @@ class Workload:
                 self.system = "swe2d_wb"
             if name == "swe2d-friction":
                 self.source, self.source_coef, self.current = "chezy", 0.0025, (0.3, 0.2)
-        elif name == "swe1d":
+        elif name in ("swe1d", "swe1d-limited"):
             self.system, self.N, self.E, self.L = "swe1d", 4, (mesh or 100000,), 100.0
             self.M, self.dim = 2, 1
+            if name == "swe1d-limited":
+                self.limiter = "blend"
         else:
             raise ValueError(name)
         n = self.N + 1
@@ -84,7 +87,8 @@ class Workload:
     def label(self):
         e = "x".join(str(v) for v in self.E)
         fr = f"-chezy{self.source_coef:g}" if self.source else ""
-        return f"{self.system}-{e}-N{self.N}{fr}"
+        lim = "-limited" if self.limiter else ""
+        return f"{self.system}-{e}-N{self.N}{fr}{lim}"
 
     def cfl_key(self):
         return "cfl_imex" if self.source else "cfl"
@@ -310,6 +314,8 @@ def run_ours(args, wl):
         Ey = wl.E[1]
         b = np.ascontiguousarray(b[[Ey - 1] + list(range(Ey)) + [0]])
     s.set_coefficients(torch.tensor(b, dtype=torch.float64, device="cuda"))
+    if wl.limiter:
+        s.set_limiter(wl.limiter)
     u_init = u.clone()
     stepper = None
     dt_fixed = 0.0
@@ -406,8 +412,8 @@ def run_ours(args, wl):
                    "k_local_2d__swe2d_wb_N3.md" if wl.system == "swe2d_wb" else
                    "k_local_2d__swe2d_N3.md")
     else:
-        kname, files, summary = "step_1d", ["step_1d.cuh", "device_common.cuh", "tableau.h"], \
-            "k_step_1d__swe1d_N4.md"
+        kname, files = "step_1d", ["step_1d.cuh", "device_common.cuh", "tableau.h"]
+        summary = "k_step_1d__swe1d_N4_limited.md" if wl.limiter else "k_step_1d__swe1d_N4.md"
     nk, ms_k = prof.get(kname, (0, float("nan")))
     avg_ms = ms_k / max(nk, 1)
     flops = wl.local_flops_per_element() * wl.elements
@@ -431,7 +437,9 @@ def run_ours(args, wl):
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic, "avg_launch_ms": avg_ms,
                      "flops_per_launch": flops,
-                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"},
+                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
+                     **({"flops_note": "the unlimited step's operation count: a lower bound "
+                                       "of the limited kernel's work"} if wl.limiter else {})},
         "hbm": {"min_bytes_per_step": wl.min_bytes,
                 "achieved_gbs": wl.min_bytes / (ms_per_step / 1e3) / 1e9,
                 "peak_gbs": hbm_peak,
@@ -467,16 +475,25 @@ def run_ensemble(args):
     """Ragged ensemble: 256 independent 1D shallow-water meshes, element counts
     log-uniform in [2^10, 2^16], degrees from {2, 3, 4}, own seeded
     bathymetry and surface each; K CFL steps of all of them in one graph
-    launch, against looping the single-mesh step over the instances."""
+    launch, against looping the single-mesh step over the instances.  Under
+    torchrun every rank runs its own 256-instance ensemble (seeded by its
+    rank) with no communication but the timing barrier and maximum (weak
+    scaling)."""
     import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
     from paper_2512_08611_gb300.build import build_library
     build_library()
     from paper_2512_08611_gb300 import crkfr
     from paper_2512_08611_gb300.flops import local_flops_per_element
     from paper_2512_08611_gb300.workloads import SWE1DInput, accept_seed, ensemble_members
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(local)
     L = 100.0
-    mem = ensemble_members(256, seed=0)
+    mem = ensemble_members(256, seed=rank)
     nodes = {N: crkfr.Solver("swe1d", N).nodes()[0] for N in (2, 3, 4)}
     members, us, cs = [], [], []
     for m in mem:
@@ -499,16 +516,29 @@ def run_ensemble(args):
     batch.step(u, 0.0, args.warmup, graph=False)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local)
     clocks.start()
     n0 = batch.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     ev0.record()
     batch.step(u, 0.0, args.steps, graph=True)
     ev1.record()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
     batch.status()
     ms = ev0.elapsed_time(ev1)
+    tot_dof = dof
+    if world > 1:
+        t = torch.tensor([ms, float(dof)], dtype=torch.float64, device="cuda")
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t[1:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, tot_dof = float(mx.item()), float(sm.item())
     launches = batch.launch_count() - n0
     # looping the single-mesh step over the instances
     solvers, states = [], []
@@ -527,11 +557,15 @@ def run_ensemble(args):
     ev1.record()
     torch.cuda.synchronize()
     ms_loop = ev0.elapsed_time(ev1)
-    value = dof * args.steps / (ms / 1e3)
+    value = tot_dof * args.steps / (ms / 1e3)
     looped = dof * args.steps / (ms_loop / 1e3)
     achieved = flops_step * args.steps / (ms / 1e3) / 1e12
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     print(json.dumps({
-        "metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": 1,
+        "metric": METRIC, "value": value, "unit": "DoF-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -540,8 +574,8 @@ def run_ensemble(args):
                    "l2": "state 250 MB > 129 MB L2, no flush",
                    "mode": "one CUDA graph of K steps, one launch per degree class per step"},
         "looped": {"value": looped, "ms_per_step": ms_loop / args.steps,
-                   "mode": "crkfr_step of K steps per instance, instances in sequence"},
-        "speedup_vs_looped": value / looped,
+                   "mode": "crkfr_step of K steps per instance, instances in sequence (rank 0)"},
+        "speedup_vs_looped": (dof * args.steps / (ms / 1e3)) / looped,
         "roofline": {"bound": "alu", "kernel": "k_step_1d_batch (all kernels of the step)",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None},
@@ -619,7 +653,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="swe2d",
-                    choices=["swe2d", "swe1d", "swe2d-friction", "swe2d-wb", "ensemble", "adjoint"])
+                    choices=["swe2d", "swe1d", "swe1d-limited", "swe2d-friction", "swe2d-wb",
+                             "ensemble", "adjoint"])
     ap.add_argument("--mesh", type=int, default=None,
                     help="elements per side (2D) or elements (1D); profiling of small cases")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")

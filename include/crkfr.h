@@ -230,6 +230,37 @@ crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
 crkfr_status crkfr_step_adjoint(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
                                 double* ubar0_dev, double* bbar_dev, double dt, void* stream);
 
+/* Subcell blending limiter of the 1D step (Sec. 4).  Each element blends the
+ * cRK-FR update with a first-order finite-volume update on its N+1 subcells
+ * of widths w_p dx (Eqs. subcell.defn, low.order.update; non-conservative
+ * Rusanov fluxes of Eq. combined.num.flux; a source, if any, by backward
+ * Euler), u = (1 - alpha_e) u^H + alpha_e u^L (Eq. blended.scheme).  Both
+ * schemes use the face flux (1 - alpha_f) F^HO + alpha_f f^LO with alpha_f
+ * the mean of the two elements' alpha (Eq. Fblend).  For shallow water the
+ * face flux is limited so that the two low-order node updates next to the
+ * face keep h above a tenth of their first-order values (Algorithm 1), and
+ * each element's blend is limited towards its first-order update so that h
+ * stays above a tenth of the smallest first-order depth (Algorithm 2);
+ * h > 0 then holds when the first-order scheme on the smallest subcell is
+ * positive, lam dt <= w_min dx / 2 (choose C_s accordingly).
+ *
+ * mode CRKFR_LIMITER_BLEND: alpha_e from the smoothness indicator of
+ * Hennemann et al. (2021), on v (advection) or h (shallow water), raised to
+ * half the larger neighbour value; CRKFR_LIMITER_FIXED: alpha_e = alpha for
+ * every element (for checks); CRKFR_LIMITER_NONE switches it off.  1D
+ * contexts with N >= 1 only (else CRKFR_ERR_UNSUPPORTED); call after
+ * crkfr_set_mesh, which switches the limiter off.  Applies to crkfr_step,
+ * crkfr_advance and crkfr_step_host; crkfr_residual stays that of the
+ * unlimited step.  crkfr_limiter_alpha copies the alpha_e of the last
+ * limited step into alpha_dev (n_elem doubles, device). */
+typedef enum {
+  CRKFR_LIMITER_NONE = 0,
+  CRKFR_LIMITER_BLEND = 1,
+  CRKFR_LIMITER_FIXED = 2
+} crkfr_limiter;
+crkfr_status crkfr_set_limiter(crkfr_ctx* ctx, int32_t mode, double alpha);
+crkfr_status crkfr_limiter_alpha(crkfr_ctx* ctx, double* alpha_dev, void* stream);
+
 /* Simulated time and the size of the last step taken (synchronises). */
 crkfr_status crkfr_get_time(crkfr_ctx* ctx, double* t_host, double* last_dt_host, void* stream);
 
@@ -256,7 +287,8 @@ typedef enum {
   CRKFR_KERNEL_RATE = 3,       /* wave-speed rate of a state (time step)     */
   CRKFR_KERNEL_COEF = 4,       /* static coefficient terms                   */
   CRKFR_KERNEL_ADJOINT_2D = 5, /* 2D adjoint step (face and local kernels)   */
-  CRKFR_KERNEL_KINDS = 6
+  CRKFR_KERNEL_INDICATOR = 6,  /* smoothness indicator of the 1D limiter      */
+  CRKFR_KERNEL_KINDS = 7
 } crkfr_kernel_kind;
 crkfr_status crkfr_profile_enable(crkfr_ctx* ctx, int32_t enable);
 crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms);

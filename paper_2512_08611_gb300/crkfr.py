@@ -79,6 +79,8 @@ SIGNATURES = {
     "crkfr_get_status": (_I32, [_P, _P]),
     "crkfr_launch_count": (_I64, [_P]),
     "crkfr_profile_enable": (_I32, [_P, _I32]),
+    "crkfr_set_limiter": (_I32, [_P, _I32, _D]),
+    "crkfr_limiter_alpha": (_I32, [_P, _P, _P]),
     "crkfr_profile_read": (_I32, [_P, _I32, _PI64, _PD]),
     "crkfr_math_check": (_I32, [_P, _P, _I64, _I32, _P]),
     "crkfr_step_1d_noalloc": (_I32, [ctypes.POINTER(Config), _I64, _D, _D, _P, _P, _P, _D, _I64,
@@ -354,7 +356,21 @@ class Solver:
     def launch_count(self):
         return lib().crkfr_launch_count(self.h)
 
-    KERNELS = {"step_1d": 0, "local_2d": 1, "face_2d": 2, "rate": 3, "coef": 4, "adjoint_2d": 5}
+    KERNELS = {"step_1d": 0, "local_2d": 1, "face_2d": 2, "rate": 3, "coef": 4, "adjoint_2d": 5,
+               "indicator": 6}
+    LIMITERS = {None: 0, "blend": 1, "fixed": 2}
+
+    def set_limiter(self, mode="blend", alpha=0.0):
+        """Subcell blending limiter of a 1D step: 'blend' (smoothness
+        indicator), 'fixed' (alpha for every element) or None (off)."""
+        self._check(lib().crkfr_set_limiter(self.h, self.LIMITERS[mode], float(alpha)))
+
+    def limiter_alpha(self):
+        """alpha_e of the last limited step (cuda float64 tensor)."""
+        import torch
+        out = torch.empty(self.n_elem[0], dtype=torch.float64, device="cuda")
+        self._check(lib().crkfr_limiter_alpha(self.h, ctypes.c_void_p(out.data_ptr()), _stream()))
+        return out
 
     def profile(self, enable=True):
         """Start (clearing earlier values) or stop per-kernel event timing."""

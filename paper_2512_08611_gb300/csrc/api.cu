@@ -35,6 +35,11 @@ struct crkfr_ctx {
   double* d_atrx = nullptr;   // adjoint traces and face-jump adjoints (crkfr_step_adjoint)
   double* d_atry = nullptr;
   double* d_gbar = nullptr;
+  double* d_cnode = nullptr;      // 1D: nodal coefficient field (subcell limiter)
+  double* d_alpha_raw = nullptr;  // 1D: indicator per element before smoothing
+  double* d_alpha = nullptr;      // 1D: blending coefficient of the last limited step
+  int limit_mode = CRKFR_LIMITER_NONE;
+  double alpha_fixed = 0.0;
   DevState* d_state = nullptr;
   bool coef_set = false;
   bool subdomain = false;   // 2D slab of a larger mesh: halo rows come from outside
@@ -83,6 +88,10 @@ void free_buffers(crkfr_ctx* c) {
   cudaFree(c->d_atrx);
   cudaFree(c->d_atry);
   cudaFree(c->d_gbar);
+  cudaFree(c->d_cnode);
+  cudaFree(c->d_alpha_raw);
+  cudaFree(c->d_alpha);
+  c->d_cnode = c->d_alpha_raw = c->d_alpha = nullptr;
   c->d_atrx = c->d_atry = c->d_gbar = nullptr;
   c->d_snode = c->d_sface = c->d_work = c->d_trx = c->d_try = c->d_stage = nullptr;
   c->d_state = nullptr;
@@ -167,6 +176,11 @@ Launch1D make1d(crkfr_ctx* c) {
   L.st = c->d_state;
   L.tab = c->tab;
   L.xs = c->xs;
+  L.lim.mode = c->limit_mode;
+  L.lim.alpha_fixed = c->alpha_fixed;
+  L.lim.alpha_raw = c->d_alpha_raw;
+  L.lim.cnode = c->d_cnode;
+  L.lim.alpha_out = c->d_alpha;
   return L;
 }
 
@@ -247,6 +261,12 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
       L.ctl = ctl;
       L.u_in = bufs[cur];
       L.u_out = bufs[cur ^ 1];
+      if (c->limit_mode == CRKFR_LIMITER_BLEND) {
+        int ea = timed(c, CRKFR_KERNEL_INDICATOR, s,
+                       [&] { return launch_alpha_1d(L, c->d_alpha_raw, s); });
+        if (ea) return cuda_fail(c, ea, "indicator kernel");
+        c->launches += 1;
+      }
       int e = timed(c, CRKFR_KERNEL_STEP_1D, s, [&] { return launch_step_1d(L, s); });
       if (e) return cuda_fail(c, e, "1D step kernel");
       c->launches += 1;
@@ -413,6 +433,17 @@ crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, co
     cudaGetLastError();
     return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
   }
+  c->limit_mode = CRKFR_LIMITER_NONE;
+  if (dim == 1) {
+    if (cudaMalloc(&c->d_cnode, sizeof(double) * Ne * n) != cudaSuccess ||
+        cudaMalloc(&c->d_alpha_raw, sizeof(double) * Ne) != cudaSuccess ||
+        cudaMalloc(&c->d_alpha, sizeof(double) * Ne) != cudaSuccess) {
+      free_buffers(c);
+      cudaGetLastError();
+      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+    }
+    CK(c, cudaMemset(c->d_alpha, 0, sizeof(double) * Ne));
+  }
   if (dim == 2) {
     const size_t trx = (size_t)7 * 2 * Ne * n;
     const size_t try_ = (size_t)7 * 2 * (Ey + 2) * Ex * n;
@@ -468,7 +499,34 @@ crkfr_status crkfr_set_coefficients(crkfr_ctx* c, const double* coef, void* stre
   });
   if (e) return cuda_fail(c, e, "coefficient kernel");
   c->launches += 1;
+  if (c->dim == 1)
+    CK(c, cudaMemcpyAsync(c->d_cnode, coef, sizeof(double) * c->n_coef, cudaMemcpyDeviceToDevice,
+                          s));
   c->coef_set = true;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_set_limiter(crkfr_ctx* c, int32_t mode, double alpha) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
+  if (mode < CRKFR_LIMITER_NONE || mode > CRKFR_LIMITER_FIXED)
+    return fail(c, CRKFR_ERR_ARG, "unknown limiter mode");
+  if (mode != CRKFR_LIMITER_NONE) {
+    if (c->dim != 1) return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter is built for 1D meshes");
+    if (c->cfg.degree < 1) return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter needs N >= 1");
+  }
+  if (mode == CRKFR_LIMITER_FIXED && !(alpha >= 0.0 && alpha <= 1.0))
+    return fail(c, CRKFR_ERR_ARG, "alpha must lie in [0, 1]");
+  c->limit_mode = mode;
+  c->alpha_fixed = mode == CRKFR_LIMITER_FIXED ? alpha : 0.0;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_limiter_alpha(crkfr_ctx* c, double* alpha_dev, void* stream) {
+  if (!c || !alpha_dev) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (c->dim != 1) return fail(c, CRKFR_ERR_STATE, "no 1D mesh set");
+  CK(c, cudaMemcpyAsync(alpha_dev, c->d_alpha, sizeof(double) * c->Ex, cudaMemcpyDeviceToDevice,
+                        (cudaStream_t)stream));
   return CRKFR_OK;
 }
 

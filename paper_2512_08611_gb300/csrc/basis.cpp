@@ -26,6 +26,7 @@
 #include <complex>
 #include <cstring>
 #include <mutex>
+#include <utility>
 
 #include "crkfr_internal.h"
 #include "tableau.h"
@@ -217,6 +218,51 @@ void fill_tables(const HostBasis& b, double dx, double dy, double gravity, bool 
   T->inv_b0 = 1.0 / T->b0;
   T->inv_gravity = gravity > 0.0 ? 1.0 / gravity : 0.0;
   T->src_coef = src_coef;
+  // smoothness indicator (Hennemann et al. 2021): inverse Vandermonde of the
+  // orthonormal Legendre polynomials sqrt((2j+1)/2) P_j(2 xi - 1) at the
+  // nodes, threshold a 10^(-c (N+1)^(1/4)) with a = 0.5, c = 1.8, and the
+  // logistic sharpness s / T, s = ln((1 - 1e-4) / 1e-4)
+  {
+    long double V[kMaxNodes][2 * kMaxNodes] = {};
+    for (int p = 0; p < n; ++p) {
+      const long double x = 2.0L * (long double)b.xi[p] - 1.0L;
+      long double p0 = 1.0L, p1 = x;
+      for (int j = 0; j < n; ++j) {
+        long double pj;
+        if (j == 0) {
+          pj = 1.0L;
+        } else if (j == 1) {
+          pj = x;
+        } else {
+          const long double p2 = ((2 * (j - 1) + 1) * x * p1 - (j - 1) * p0) / j;
+          p0 = p1;
+          p1 = p2;
+          pj = p2;
+        }
+        V[p][j] = std::sqrt((2.0L * j + 1.0L) / 2.0L) * pj;
+      }
+      V[p][n + p] = 1.0L;
+    }
+    // Gauss-Jordan with partial pivoting on [V | I]
+    for (int col = 0; col < n; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < n; ++r)
+        if (std::fabs(V[r][col]) > std::fabs(V[piv][col])) piv = r;
+      for (int k = 0; k < 2 * n; ++k) std::swap(V[col][k], V[piv][k]);
+      const long double d = V[col][col];
+      for (int k = 0; k < 2 * n; ++k) V[col][k] /= d;
+      for (int r = 0; r < n; ++r) {
+        if (r == col) continue;
+        const long double f = V[r][col];
+        for (int k = 0; k < 2 * n; ++k) V[r][k] -= f * V[col][k];
+      }
+    }
+    for (int j = 0; j < n; ++j)
+      for (int p = 0; p < n; ++p) T->Vinv[j][p] = (double)V[j][n + p];
+    const double Nn = (double)b.N;
+    T->ind_T = 0.5 * std::pow(10.0, -1.8 * std::pow(Nn + 1.0, 0.25));
+    T->ind_sharp = std::log((1.0 - 1e-4) / 1e-4) / T->ind_T;
+  }
 }
 
 namespace {

@@ -45,6 +45,19 @@ struct Tables {
   double inv_b0;   // 1 / b_ref
   double inv_gravity;  // 1 / g (0 without gravity)
   double src_coef; // source coefficient: K (linear damping) or C_f (Chezy)
+  // smoothness indicator of the subcell limiter: nodal values -> coefficients
+  // in the orthonormal Legendre basis, threshold T(N) and s / T
+  double Vinv[kMaxNodes][kMaxNodes];
+  double ind_T, ind_sharp;
+};
+
+// Subcell blending limiter of a 1D step (kernels_limit.cu).
+struct LimitArgs {
+  int mode;                 // CRKFR_LIMITER_*: 0 none, 1 indicator, 2 fixed alpha
+  double alpha_fixed;       // alpha of mode 2
+  const double* alpha_raw;  // [E] indicator before smoothing (mode 1)
+  const double* cnode;      // [E][n] nodal coefficient field c
+  double* alpha_out;        // [E] blending coefficient each owner used
 };
 
 // Device-resident stepping state of a context.
@@ -111,8 +124,11 @@ struct Launch1D {
   Tables tab;            // reference element (dx = 1)
   double xs;             // 1 / dx
   StepCtl ctl;
+  LimitArgs lim;         // mode 0: no limiter
 };
 int launch_step_1d(const Launch1D& L, void* stream);
+int launch_step_1d_limit(const Launch1D& L, void* stream);   // kernels_limit.cu
+int launch_alpha_1d(const Launch1D& L, double* alpha_raw, void* stream);
 int launch_step_1d_imex(const Launch1D& L, void* stream);   // kernels_imex.cu
 int launch_rate_1d(const Launch1D& L, int slot, void* stream);
 int launch_coef_1d(int system, int N, int64_t E, const double* c, double* snode, double* sface,

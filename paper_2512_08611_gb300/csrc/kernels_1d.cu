@@ -153,6 +153,7 @@ int base_system(int system) {
 }  // namespace
 
 int launch_step_1d(const Launch1D& L, void* stream) {
+  if (L.lim.mode != 0 && !L.ctl.residual) return launch_step_1d_limit(L, stream);
   if (L.system == CRKFR_SYS_SWE_1D_WB) return launch_step_1d_wb(L, stream);
   if (L.imex) return launch_step_1d_imex(L, stream);
   cudaStream_t s = (cudaStream_t)stream;

@@ -32,6 +32,14 @@
 // pressure from the momentum flux, adds g h D h to the local
 // non-conservative term (g h D (h + b)), and dissipates and fluctuates the
 // free surface eta = h + b instead of h at the faces.
+//
+// With the subcell blending limiter (LIMIT = true; Sec. 4) each element also
+// takes a first-order finite-volume step on its N+1 subcells of widths
+// w_p dx (Eqs. subcell.defn, low.order.update) with the non-conservative
+// Rusanov fluxes of Eq. combined.num.flux, both schemes share the blended
+// face flux of Eq. Fblend limited by Algorithm 1 so that the two adjacent
+// low-order node updates keep h > 0, and the blend of Eq. blended.scheme is
+// limited per element by Algorithm 2.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -78,19 +86,72 @@ __device__ __forceinline__ double trace_l(const Tables& T, const double* X) {
   return s;
 }
 
+// First-order non-conservative Rusanov fluxes (Eq. combined.num.flux) between
+// the nodal states L and R: fm = f^num + B(w_L) w^num, fp = f^num + B(w_R) w^num,
+// f^num = (f_L + f_R)/2 - lam/2 (jump), lam the larger spectral radius, the
+// jump that of h, or of eta = h + b for the well-balanced form.
+template <int SYS>
+__device__ __forceinline__ void lo_flux(const double* uL, const double* uR, double cL, double cR,
+                                        const Tables& T, double* fm, double* fp) {
+  if constexpr (SYS == CRKFR_SYS_VARADV_1D) {
+    const double lam = max_nonneg(fabs(cL), fabs(cR));
+    const double f = -0.5 * lam * (uR[0] - uL[0]);
+    const double un = 0.5 * (uL[0] + uR[0]);
+    fm[0] = f + cL * un;
+    fp[0] = f + cR * un;
+  } else {
+    constexpr bool WB = (SYS == CRKFR_SYS_SWE_1D_WB);
+    const double g = T.gravity;
+    const double hL = uL[0], mL = uL[1], hR = uR[0], mR = uR[1];
+    const double lam = max_nonneg(swe_speed(hL, mL, g), swe_speed(hR, mR, g));
+    const double vL = mL * drcp(hL), vR = mR * drcp(hR);
+    const double fL = WB ? mL * vL : fma(0.5 * g * hL, hL, mL * vL);
+    const double fR = WB ? mR * vR : fma(0.5 * g * hR, hR, mR * vR);
+    const double jh = WB ? (hR + cR) - (hL + cL) : hR - hL;
+    const double f0 = fma(-0.5 * lam, jh, 0.5 * (mL + mR));
+    const double f1 = fma(-0.5 * lam, mR - mL, 0.5 * (fL + fR));
+    const double wn = WB ? 0.5 * (hL + hR) + 0.5 * (cL + cR) : 0.5 * (cL + cR);
+    fm[0] = f0;
+    fp[0] = f0;
+    fm[1] = f1 + g * hL * wn;
+    fp[1] = f1 + g * hR * wn;
+  }
+}
+
+// Weight of the candidate b in theta b + (1 - theta) a for the linear
+// constraint P (Eq. theta.formula): 1 unless P(b) < eps.
+__device__ __forceinline__ double theta_lin(double eps, double Pa, double Pb) {
+  if (!(Pb < eps)) return 1.0;
+  const double den = Pb - Pa;
+  return den != 0.0 ? fmin(1.0, fabs((eps - Pa) / den)) : 1.0;
+}
+
+// Point-implicit backward-Euler source step of the low-order update
+// (Eq. low.order.update): u - dt s(u) = r, in closed form.
+template <int SYS>
+__device__ __forceinline__ void lo_source(const Tables& T, double dt, double* u) {
+  if constexpr (SYS == CRKFR_SYS_VARADV_1D) {
+    u[0] *= drcp(fma(dt, T.src_coef, 1.0));
+  } else {
+    const double ih = drcp(u[0]);
+    const double q = dsqrt_pos(fma(4.0 * dt * T.src_coef * ih * ih, fabs(u[1]), 1.0));
+    u[1] *= 2.0 * drcp(1.0 + q);
+  }
+}
+
 // One tile (126 elements plus a halo element on each side) of the fused 1D
 // step of one mesh.  T holds reference-element tables (dx = 1: D, l(0), l(1),
 // 0.5 g'); xs = 1/dx scales the local operator and the corrections through
 // the scalar coefficients only (stage coefficients dt a_ij xs, update
 // coefficient dt b_ref xs), so one table serves meshes of any dx.
-template <int SYS, int N, bool GLL, bool RES, bool IMEX>
+template <int SYS, int N, bool GLL, bool RES, bool IMEX, bool LIMIT = false>
 __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
                                              const double* __restrict__ u_in,
                                              double* __restrict__ u_out,
                                              const double* __restrict__ snode,
                                              const double* __restrict__ sface, int64_t E,
                                              int64_t tile, DevState* st, const StepCtl& ctl,
-                                             bool first_tile) {
+                                             bool first_tile, const LimitArgs& LA = LimitArgs{}) {
   using TB = Tab<N, IMEX>;
   constexpr int n = N + 1;
   constexpr int M = Sys1D<SYS>::M;
@@ -123,6 +184,53 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
 #pragma unroll
   for (int p = 0; p < n; ++p) sn[p] = snode[e * n + p];
   const double c_l = sface[2 * e], c_r = sface[2 * e + 1];
+
+  // ---- limiter: alpha_e, nodal c, first-order fluxes of the inner subfaces --
+  static_assert(!LIMIT || (N >= 1 && !RES), "the limiter needs N >= 1 and a step");
+  constexpr int LM = LIMIT ? M : 1, LN = LIMIT ? N : 1, LB = LIMIT ? kBlock1D : 1;
+  double alpha = 0.0;
+  double cn[n];
+  double fim[LM][LN];   // right flux of node p (B at node p)
+  double fip[LM][LN];   // left flux of node p+1 (B at node p+1)
+  __shared__ double sm_u0[LM][LB];
+  __shared__ double sm_fi0[LM][LB];
+  __shared__ double sm_c0[LB];
+  __shared__ double sm_al[LB];
+  __shared__ double sm_F[LM][LB];
+  if constexpr (LIMIT) {
+#pragma unroll
+    for (int p = 0; p < n; ++p) cn[p] = LA.cnode[e * n + p];
+    if (LA.mode == 2) {
+      alpha = LA.alpha_fixed;
+    } else {
+      const int64_t em = e == 0 ? E - 1 : e - 1, ep = e == E - 1 ? 0 : e + 1;
+      const double r0 = LA.alpha_raw[e];
+      const double rn = fmax(LA.alpha_raw[em], LA.alpha_raw[ep]);
+      alpha = fmax(r0, 0.5 * rn);
+    }
+#pragma unroll
+    for (int p = 0; p < LN; ++p) {
+      double a[M], b[M], fm_[M], fp_[M];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        a[v] = u0[v][p];
+        b[v] = u0[v][p + 1];
+      }
+      lo_flux<SYS>(a, b, cn[p], cn[p + 1], T, fm_, fp_);
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        fim[v][p] = fm_[v];
+        fip[v][p] = fp_[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      sm_u0[v][t] = u0[v][0];
+      sm_fi0[v][t] = fim[v][0];
+    }
+    sm_c0[t] = cn[0];
+    sm_al[t] = alpha;
+  }
 
   // ---- inner stages (element-local) ----------------------------------------
   // Time averages are accumulated with the weights b_j / b_ref (the first
@@ -263,8 +371,85 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   __syncthreads();
 
   // ---- Riemann problem at the right face (t | t+1), both sides -------------
-  double Tm[M];  // doubled face term on this element's right face (minus side)
-  if (t < kBlock1D - 1) {
+  double Tm[M];        // doubled face term on this element's right face (minus side)
+  double Fm_lim[LM];   // limiter: blended, limited flux F^- of that face
+  if (LIMIT && t < kBlock1D - 1) {
+    // time-averaged numerical and total fluxes in the units of the time
+    // averages (divided by b_ref), Eqs. numflux.cons, good.numflux.non.cons,
+    // total.F.non.cons; the first-order face flux from the nodal values next
+    // to the face; Eq. Fblend; Algorithm 1 (h > 0) for shallow water
+    constexpr double b0 = TB::bref();
+    double FHm[M], FHp[M], FTm[M], FTp[M];
+    if constexpr (SWE) {
+      const double Hm = tr_r[0], Mm = tr_r[1], Fm = tr_r[2], hm = tr_r[3], mm = tr_r[4],
+                   bm = tr_r[5];
+      const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
+                   hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
+      const double g = T.gravity;
+      const double lam = max_nonneg(swe_speed(hm, mm, g), swe_speed(hp, mp, g));
+      const double dUh = WB ? (Hp + bp * T.inv_b0) - (Hm + bm * T.inv_b0) : Hp - Hm;
+      const double Fn0 = fma(-0.5 * lam, dUh, 0.5 * (Mm + Mp));
+      const double Fn1 = fma(-0.5 * lam, Mp - Mm, 0.5 * (Fm + Fp));
+      const double bn = 0.5 * (bm + bp) * T.inv_b0;
+      const double Wn = WB ? 0.5 * (Hm + Hp) + bn : bn;
+      const double Wm = WB ? Hm + bm * T.inv_b0 : bm * T.inv_b0;
+      const double Wp = WB ? Hp + bp * T.inv_b0 : bp * T.inv_b0;
+      FHm[0] = Fn0;
+      FHp[0] = Fn0;
+      FHm[1] = Fn1 + g * hm * Wn;
+      FHp[1] = Fn1 + g * hp * Wn;
+      FTm[0] = Mm;
+      FTp[0] = Mp;
+      FTm[1] = Fm + g * hm * Wm;
+      FTp[1] = Fp + g * hp * Wp;
+    } else {
+      const double Vm = tr_r[0], am = tr_r[1];
+      const double Vp = sm_left[0][t + 1], ap = sm_left[1][t + 1];
+      const double lam = max_nonneg(fabs(am), fabs(ap));
+      const double Fn = -0.5 * lam * (Vp - Vm);
+      const double Vn = 0.5 * (Vm + Vp);
+      FHm[0] = Fn + am * Vn;
+      FHp[0] = Fn + ap * Vn;
+      FTm[0] = am * Vm;
+      FTp[0] = ap * Vp;
+    }
+    double uN[M], u0R[M], fLm[M], fLp[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      uN[v] = u0[v][N];
+      u0R[v] = sm_u0[v][t + 1];
+    }
+    lo_flux<SYS>(uN, u0R, cn[N], sm_c0[t + 1], T, fLm, fLp);
+    const double af = 0.5 * (alpha + sm_al[t + 1]);
+    double Fm_[M], Fp_[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      Fm_[v] = (1.0 - af) * (b0 * FHm[v]) + af * fLm[v];
+      Fp_[v] = (1.0 - af) * (b0 * FHp[v]) + af * fLp[v];
+    }
+    if constexpr (SWE) {
+      const double c0 = dtx / T.w[0], cN = dtx / T.w[N];
+      const double fi0R = sm_fi0[0][t + 1], fiNL = fip[0][LN - 1];
+      const double low0 = u0R[0] - c0 * (fi0R - fLp[0]);
+      const double lowN = uN[0] - cN * (fLm[0] - fiNL);
+      const double t0 = u0R[0] - c0 * (fi0R - Fp_[0]);
+      const double tN = uN[0] - cN * (Fm_[0] - fiNL);
+      const double th = fmin(theta_lin(0.1 * low0, low0, t0), theta_lin(0.1 * lowN, lowN, tN));
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        Fm_[v] = th * Fm_[v] + (1.0 - th) * fLm[v];
+        Fp_[v] = th * Fp_[v] + (1.0 - th) * fLp[v];
+      }
+    }
+    // face terms in the doubled units of the corrections: 2 (F - F^tot) / b_ref
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      Fm_lim[v] = Fm_[v];
+      Tm[v] = 2.0 * (Fm_[v] * T.inv_b0 - FTm[v]);
+      sm_T[v][t + 1] = 2.0 * (Fp_[v] * T.inv_b0 - FTp[v]);
+      sm_F[v][t + 1] = Fp_[v];
+    }
+  } else if (!LIMIT && t < kBlock1D - 1) {
     if constexpr (SWE) {
       const double Hm = tr_r[0], Mm = tr_r[1], Fm = tr_r[2], hm = tr_r[3], mm = tr_r[4],
                    bm = tr_r[5];
@@ -317,8 +502,47 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
         double o = RES ? -(b0 * xs) * R : fma(-dtb0, R, u0[v][p]);
         if (IMEX && v == SV) o = fma(RES ? b0 : dts, Sb[p], o);
         out[v][p] = o;
-        u_out[((int64_t)v * E + e) * n + p] = o;
+        if (!LIMIT) u_out[((int64_t)v * E + e) * n + p] = o;
       }
+    if constexpr (LIMIT) {
+      // first-order subcell update (Eq. low.order.update), then
+      // Eq. blended.scheme and Algorithm 2 (h > 0)
+      double lo[M][n];
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+        double x[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const double right = p < N ? fim[v][p < N ? p : 0] : Fm_lim[v];
+          const double left = p > 0 ? fip[v][p > 0 ? p - 1 : 0] : sm_F[v][t];
+          x[v] = u0[v][p] - (dtx / T.w[p]) * (right - left);
+        }
+        if constexpr (IMEX) lo_source<SYS>(T, dt, x);
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          lo[v][p] = x[v];
+          out[v][p] = (1.0 - alpha) * out[v][p] + alpha * x[v];
+        }
+      }
+      if constexpr (SWE) {
+        double lmin = lo[0][0];
+#pragma unroll
+        for (int p = 1; p < n; ++p) lmin = fmin(lmin, lo[0][p]);
+        const double eps = 0.1 * lmin;
+        double th = 1.0;
+#pragma unroll
+        for (int p = 0; p < n; ++p) th = fmin(th, theta_lin(eps, lo[0][p], out[0][p]));
+#pragma unroll
+        for (int v = 0; v < M; ++v)
+#pragma unroll
+          for (int p = 0; p < n; ++p) out[v][p] = th * out[v][p] + (1.0 - th) * lo[v][p];
+      }
+#pragma unroll
+      for (int v = 0; v < M; ++v)
+#pragma unroll
+        for (int p = 0; p < n; ++p) u_out[((int64_t)v * E + e) * n + p] = out[v][p];
+      LA.alpha_out[e] = alpha;
+    }
     if (!RES) {
       if constexpr (SWE) {
 #pragma unroll
@@ -352,10 +576,11 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   }
 }
 
-template <int SYS, int N, bool GLL, bool RES, bool IMEX>
+template <int SYS, int N, bool GLL, bool RES, bool IMEX, bool LIMIT = false>
 __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
-  step_1d_tile<SYS, N, GLL, RES, IMEX>(L.tab, L.xs, L.u_in, L.u_out, L.snode, L.sface, L.E,
-                                       blockIdx.x, L.st, L.ctl, blockIdx.x == 0);
+  step_1d_tile<SYS, N, GLL, RES, IMEX, LIMIT>(L.tab, L.xs, L.u_in, L.u_out, L.snode, L.sface,
+                                              L.E, blockIdx.x, L.st, L.ctl, blockIdx.x == 0,
+                                              L.lim);
 }
 
 // ragged ensembles: one (instance, tile) pair per block

@@ -25,8 +25,9 @@ def case(N, Ex, Ey, L):
     return u, b
 
 
-def mono(crk, N, Ex, Ey, L, u, b, dt, steps):
-    s = crk.Solver("swe2d", N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+def mono(crk, N, Ex, Ey, L, u, b, dt, steps, system="swe2d", source=None):
+    s = crk.Solver(system, N, gravity=G, cfl_number=golden_cfl(N, "gl"), source=source,
+                   source_coef=0.5 if source else 0.0)
     s.set_mesh([Ex, Ey], [0.0, 0.0], [L, L])
     s.set_coefficients(to_dev(b))
     du = to_dev(u)
@@ -34,9 +35,10 @@ def mono(crk, N, Ex, Ey, L, u, b, dt, steps):
     return to_host(du)
 
 
-def slab(crk, N, Ex, Ey, L, b, first, count):
+def slab(crk, N, Ex, Ey, L, b, first, count, system="swe2d", source=None):
     dy = L / Ey
-    s = crk.Solver("swe2d", N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+    s = crk.Solver(system, N, gravity=G, cfl_number=golden_cfl(N, "gl"), source=source,
+                   source_coef=0.5 if source else 0.0)
     s.set_mesh([Ex, count], [0.0, first * dy], [L, (first + count) * dy])
     s.set_subdomain(True)
     rows = [(first - 1) % Ey] + list(range(first, first + count)) + [(first + count) % Ey]
@@ -44,14 +46,18 @@ def slab(crk, N, Ex, Ey, L, b, first, count):
     return s
 
 
-@pytest.mark.parametrize("N", [1, 3])
-def test_two_slabs_equal_single_domain(N):
+@pytest.mark.parametrize("N,system,source", [(1, "swe2d", None), (3, "swe2d", None),
+                                             (3, "swe2d_wb", None), (2, "swe2d", "chezy"),
+                                             (3, "swe2d_wb", "chezy")])
+def test_two_slabs_equal_single_domain(N, system, source):
+    """Also for the well-balanced form and with Chezy friction: the slab
+    kernels are the same instantiations as the single-domain ones."""
     crk = load()
     Ex, Ey, L, dt, steps = 16, 16, 64.0, 0.02, 5      # dx = dy = 4: exact slab bounds
     u, b = case(N, Ex, Ey, L)
-    want = mono(crk, N, Ex, Ey, L, u, b, dt, steps)
+    want = mono(crk, N, Ex, Ey, L, u, b, dt, steps, system, source)
     parts = [(0, 7), (7, 9)]
-    solvers = [slab(crk, N, Ex, Ey, L, b, f, c) for f, c in parts]
+    solvers = [slab(crk, N, Ex, Ey, L, b, f, c, system, source) for f, c in parts]
     states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
     bufs = [s.halo_buffers() for s in solvers]       # (send_bottom, send_top, recv_bottom, recv_top)
     for _ in range(steps):

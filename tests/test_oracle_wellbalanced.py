@@ -147,3 +147,30 @@ def test_wb_and_standard_forms_agree_to_design_order(flat):
     d = np.array([np.max(np.abs(x - y)) for x, y in zip(a, b)])
     rates = np.log2(d[:-1] / d[1:])
     assert rates[-1] > N + 1 - 0.4, rates
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_standard_form_lake_at_rest_defect_converges(N):
+    """The standard form does not keep a lake at rest (the paper does not
+    claim it does, Sec. 6); its defect after t = 0.05 over a Gaussian bump
+    falls at about the design order N+1 on 25..200 elements (measured:
+    N = 1: 2.3, N = 2: 3.0, N = 3: 3.9 on the finest pair)."""
+    cfl = fourier.cfl_number(N, halvings=30)
+    errs = []
+    for E in (25, 50, 100, 200):
+        bs = Basis(N)
+        dx = 1.0 / E
+        x = (np.arange(E)[:, None] + bs.xi[None, :]) * dx
+        b = 0.2 * np.exp(-((x - 0.5) ** 2) / (2 * 0.08 ** 2))
+        u0 = np.stack([1.0 - b, np.zeros_like(b)])
+        sch = Scheme1D(ShallowWater1D(G), N, dx)
+        T = 0.05
+        n = int(np.ceil(T / (0.5 * cfl * dx / np.sqrt(G))))
+        u = u0.copy()
+        for _ in range(n):
+            u = sch.step(u, b, T / n)
+        errs.append(np.max(np.abs(u - u0)))
+    errs = np.array(errs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(errs > 1e-10)
+    assert rates[-1] > N + 1 - 0.8, rates
