@@ -511,6 +511,11 @@ def run_ensemble(args):
     c = torch.cat([torch.tensor(x.ravel()) for x in cs]).cuda()
     u0 = u.clone()
     batch.set_coefficients(c)
+    # launch shape chosen by the library's autotuner (times the shapes as
+    # captured graphs on a scratch copy of the state)
+    t_tune = time.perf_counter()
+    tpb, order, parallel, tune_ms = batch.autotune(u, steps=5)
+    t_tune = time.perf_counter() - t_tune
     batch.step(u, 0.0, args.steps, graph=True)     # capture + warm-up
     u.copy_(u0)
     batch.step(u, 0.0, args.warmup, graph=False)
@@ -572,7 +577,10 @@ def run_ensemble(args):
         "config": {"workload": "ensemble-256-swe1d-E2^10..2^16-N2..4", "instances": len(members),
                    "elements": int(sum(m[1] for m in members)), "dof": int(dof),
                    "l2": "state 250 MB > 129 MB L2, no flush",
-                   "mode": "one CUDA graph of K steps, one launch per degree class per step"},
+                   "mode": "one CUDA graph of K steps, one launch per degree class per step",
+                   "tuning": {"tiles_per_block": tpb, "order": ["instance", "largest first"][order],
+                              "degree_classes": "concurrent branches" if parallel else "serial",
+                              "autotune_s": t_tune, "tuned_ms_per_step": tune_ms}},
         "looped": {"value": looped, "ms_per_step": ms_loop / args.steps,
                    "mode": "crkfr_step of K steps per instance, instances in sequence (rank 0)"},
         "speedup_vs_looped": (dof * args.steps / (ms / 1e3)) / looped,

@@ -366,6 +366,26 @@ crkfr_status crkfr_batch_set_coefficients(crkfr_batch* batch, const double* c_de
 crkfr_status crkfr_batch_step(crkfr_batch* batch, double* u_dev, double dt, int64_t nsteps,
                               int32_t use_graph, void* stream);
 crkfr_status crkfr_batch_get_times(crkfr_batch* batch, double* t_host, void* stream);
+
+/* Launch shape of a batch step (no counterpart in the paper; it changes only
+ * how the work is scheduled, never the result, which stays bitwise the same):
+ * tiles_per_block (1..1024) tiles of the work list run in turn by each block
+ * of a step launch; order 0 keeps the work lists in instance order, 1 puts
+ * the tiles of the largest instances first; parallel 1 runs the degree
+ * classes, which share no data, as concurrent branches (one stream each,
+ * forked and joined around the whole call) instead of one serial chain.
+ * crkfr_batch_autotune times every combination of tiles_per_block in
+ * {1, 2, 4, 8}, both orders and both modes as a captured graph of `steps`
+ * CFL steps of the state u_dev, on a scratch copy (u_dev and the instances'
+ * times are left unchanged), keeps the fastest, and reports its time per
+ * step through crkfr_batch_get_tuning.  Synchronises the stream; allocates a
+ * state-sized scratch buffer for the duration of the call. */
+crkfr_status crkfr_batch_set_tuning(crkfr_batch* batch, int32_t tiles_per_block, int32_t order,
+                                    int32_t parallel);
+crkfr_status crkfr_batch_get_tuning(const crkfr_batch* batch, int32_t* tiles_per_block,
+                                    int32_t* order, int32_t* parallel, double* ms_per_step);
+crkfr_status crkfr_batch_autotune(crkfr_batch* batch, const double* u_dev, int32_t steps,
+                                  void* stream);
 crkfr_status crkfr_batch_get_status(crkfr_batch* batch, void* stream);
 int64_t crkfr_batch_launch_count(const crkfr_batch* batch);
 const char* crkfr_batch_last_error(const crkfr_batch* batch);

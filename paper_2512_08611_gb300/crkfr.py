@@ -80,6 +80,10 @@ SIGNATURES = {
     "crkfr_launch_count": (_I64, [_P]),
     "crkfr_profile_enable": (_I32, [_P, _I32]),
     "crkfr_set_limiter": (_I32, [_P, _I32, _D]),
+    "crkfr_batch_set_tuning": (_I32, [_P, _I32, _I32, _I32]),
+    "crkfr_batch_get_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                      ctypes.POINTER(_I32), _PD]),
+    "crkfr_batch_autotune": (_I32, [_P, _P, _I32, _P]),
     "crkfr_limiter_alpha": (_I32, [_P, _P, _P]),
     "crkfr_profile_read": (_I32, [_P, _I32, _PI64, _PD]),
     "crkfr_math_check": (_I32, [_P, _P, _I64, _I32, _P]),
@@ -348,6 +352,30 @@ class Solver:
     def set_time(self, t):
         self._check(lib().crkfr_set_time(self.h, float(t), _stream()))
 
+    def state_dict(self, u):
+        """Checkpoint of a run: the state (a copy), the simulated time and
+        the configuration it belongs to.  The CFL step is recomputed from the
+        state at every call, so resuming from a checkpoint repeats the run."""
+        t, dt_last = self.time()
+        return {"u": u.detach().clone(), "t": t, "dt_last": dt_last, "system": self.system,
+                "degree": self.degree, "nodes": self.family, "n_elem": list(self.n_elem),
+                "lo": list(self.lo), "hi": list(self.hi), "source": self.source,
+                "source_coef": self.source_coef}
+
+    def load_state_dict(self, sd, u):
+        """Restore a checkpoint into the device tensor u and the context's
+        time; the context must hold the same system, degree, nodes and mesh
+        (and coefficients)."""
+        for k in ("system", "degree", "nodes"):
+            want = {"system": self.system, "degree": self.degree, "nodes": self.family}[k]
+            if sd[k] != want:
+                raise ValueError(f"checkpoint {k} {sd[k]!r} differs from {want!r}")
+        if list(sd["n_elem"]) != list(self.n_elem):
+            raise ValueError("checkpoint mesh differs")
+        u.copy_(sd["u"])
+        self.set_time(sd["t"])
+        return u
+
     def status(self):
         """Raises CrkfrError(CRKFR_ERR_NONPHYSICAL) if a non-physical state was
         produced since the last call."""
@@ -445,6 +473,24 @@ class Batch:
         self._check(lib().crkfr_batch_step(self.h, ctypes.c_void_p(u.data_ptr()), float(dt),
                                            int(nsteps), 1 if graph else 0, _stream()))
         return u
+
+    def set_tuning(self, tiles_per_block=1, order=0, parallel=False):
+        """Launch shape of a step (never changes the result)."""
+        self._check(lib().crkfr_batch_set_tuning(self.h, int(tiles_per_block), int(order),
+                                                 1 if parallel else 0))
+
+    def tuning(self):
+        """(tiles_per_block, order, parallel, ms per step of the tuned shape)."""
+        t, o, p, ms = _I32(), _I32(), _I32(), ctypes.c_double()
+        self._check(lib().crkfr_batch_get_tuning(self.h, ctypes.byref(t), ctypes.byref(o),
+                                                 ctypes.byref(p), ctypes.byref(ms)))
+        return t.value, o.value, bool(p.value), ms.value
+
+    def autotune(self, u, steps=3):
+        """Time the launch shapes on a scratch copy of u and keep the fastest."""
+        self._check(lib().crkfr_batch_autotune(self.h, ctypes.c_void_p(u.data_ptr()), int(steps),
+                                               _stream()))
+        return self.tuning()
 
     def times(self):
         t = (ctypes.c_double * len(self.members))()

@@ -1,6 +1,7 @@
 // C ABI of libcrkfr (declared in include/crkfr.h): context, mesh, static
 // coefficient terms, time-step control and the stepping entry points.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstring>
@@ -122,6 +123,15 @@ cudaEvent_t take_event(crkfr_ctx* c) {
 // it with an event pair on the launch stream.
 template <class F>
 int timed(crkfr_ctx* c, int kind, cudaStream_t s, F launch) {
+  // an NVTX range per launch, named by kernel kind (visible to ncu --nvtx;
+  // a no-op without a tool attached)
+  static const char* const names[CRKFR_KERNEL_KINDS] = {
+      "crkfr step 1d", "crkfr local 2d", "crkfr face 2d", "crkfr rate",
+      "crkfr coef",    "crkfr adjoint 2d", "crkfr indicator"};
+  struct Range {
+    explicit Range(const char* n) { nvtxRangePushA(n); }
+    ~Range() { nvtxRangePop(); }
+  } range(names[kind]);
   if (!c->prof) return launch();
   cudaEvent_t a = take_event(c), b = take_event(c);
   if (!a || !b) return launch();

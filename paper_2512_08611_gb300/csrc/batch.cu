@@ -8,6 +8,14 @@
 // single-mesh step, with the instance's 1/dx as a scalar, so small instances
 // do not leave the GPU idle and no per-instance launch is needed.  A call of
 // many steps can be captured once into a CUDA graph and replayed.
+//
+// Launch shape (tuned per ensemble by crkfr_batch_autotune, which times the
+// candidates as captured graphs on a scratch copy of the state): the number
+// of tiles each block runs in turn (tiles per block), the order of the work
+// lists (instance order, or the tiles of the largest instances first so that
+// the last wave is made of small tiles), and whether the degree classes,
+// which share no data, run as one serial chain of launches or as concurrent
+// branches (one stream each, forked and joined around the K steps).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,6 +55,14 @@ struct crkfr_batch {
   int device = -1;
   int64_t launches = 0;
   std::string err;
+  // launch shape (crkfr_batch_set_tuning / crkfr_batch_autotune)
+  std::vector<WorkItem> work_h[kMaxNodes];   // work lists in instance order
+  int tpb = 1;            // tiles per block
+  int order = 0;          // 0 instance order, 1 largest instances first
+  int parallel = 0;       // 1: degree classes on concurrent branches
+  double tune_ms = 0.0;   // time per step of the chosen shape (autotune), 0 if not tuned
+  cudaStream_t side[kMaxNodes] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxNodes] = {};
   // graph of the last captured call
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
@@ -82,10 +98,23 @@ __global__ void k_batch_finish(DevState* st, int n) {
   if (i < n) st[i].time[0] = st[i].time[1];
 }
 
-void free_all(crkfr_batch* b) {
+void drop_graph(crkfr_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->g_u = nullptr;
+  b->g_nsteps = -1;
+}
+
+void free_all(crkfr_batch* b) {
+  drop_graph(b);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int k = 0; k < kMaxNodes; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   cudaFree(b->d_inst);
   for (int k = 0; k < kMaxNodes; ++k) cudaFree(b->d_work[k]);
   cudaFree(b->d_snode);
@@ -103,13 +132,41 @@ LaunchBatch1D make(crkfr_batch* b, int N) {
   B.inst = b->d_inst;
   B.work = b->d_work[N];
   B.nwork = b->nwork[N];
+  B.grid = (b->nwork[N] + b->tpb - 1) / b->tpb;
   B.snode = b->d_snode;
   B.sface = b->d_sface;
   B.tab = b->tab[N];
   return B;
 }
 
-// the launches of one call: [prepare + rates], [copy], nsteps x classes, [finish]
+// rate launch of one degree class
+crkfr_status class_rates(crkfr_batch* b, int N, double* u, cudaStream_t s) {
+  LaunchBatch1D B = make(b, N);
+  B.u_in = u;
+  if (launch_rate_1d_batch(B, 0, s)) return bfail(b, CRKFR_ERR_CUDA, "batch rate kernel");
+  b->launches += 1;
+  return CRKFR_OK;
+}
+
+// step k of one degree class
+crkfr_status class_step(crkfr_batch* b, int N, StepCtl ctl, int64_t k, double* const* bufs,
+                        int cur, cudaStream_t s) {
+  ctl.slot_read = (int)(k % 3);
+  ctl.slot_write = (int)((k + 1) % 3);
+  ctl.slot_reset = (int)((k + 2) % 3);
+  ctl.tslot = (int)(k % 2);
+  ctl.cs_cfl = b->cfg.cfl_safety * b->cfl[N];
+  LaunchBatch1D B = make(b, N);
+  B.ctl = ctl;
+  B.u_in = bufs[cur];
+  B.u_out = bufs[cur ^ 1];
+  if (launch_step_1d_batch(B, s)) return bfail(b, CRKFR_ERR_CUDA, "batch step kernel");
+  b->launches += 1;
+  return CRKFR_OK;
+}
+
+// the launches of one call: [prepare], [copy], per class [rates] and nsteps
+// steps (interleaved by step, or one concurrent branch per class), [finish]
 crkfr_status record(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaStream_t s) {
   const bool cfl_mode = !(dt > 0.0);
   const int nb = (b->n_inst + 127) / 128;
@@ -117,40 +174,53 @@ crkfr_status record(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaSt
     k_batch_prepare<<<nb, 128, 0, s>>>(b->d_states, b->n_inst);
     BCK(b, cudaGetLastError());
     b->launches += 1;
-    for (int N = 0; N < kMaxNodes; ++N) {
-      if (!b->nwork[N]) continue;
-      LaunchBatch1D B = make(b, N);
-      B.u_in = u;
-      if (launch_rate_1d_batch(B, 0, s)) return bfail(b, CRKFR_ERR_CUDA, "batch rate kernel");
-      b->launches += 1;
-    }
   }
   double* bufs[2] = {u, b->d_swap};
-  int cur = 0;
+  int cur0 = 0;
   if (nsteps % 2 == 1) {
     BCK(b, cudaMemcpyAsync(b->d_swap, u, sizeof(double) * b->n_state, cudaMemcpyDeviceToDevice, s));
-    cur = 1;
+    cur0 = 1;
   }
   StepCtl ctl{};
   ctl.dt_fixed = cfl_mode ? 0.0 : dt;
   ctl.t_end = std::numeric_limits<double>::infinity();
   ctl.want_rate = cfl_mode ? 1 : 0;
-  for (int64_t k = 0; k < nsteps; ++k) {
-    ctl.slot_read = (int)(k % 3);
-    ctl.slot_write = (int)((k + 1) % 3);
-    ctl.slot_reset = (int)((k + 2) % 3);
-    ctl.tslot = (int)(k % 2);
+  if (b->parallel) {
+    BCK(b, cudaEventRecord(b->ev_fork, s));
     for (int N = 0; N < kMaxNodes; ++N) {
       if (!b->nwork[N]) continue;
-      LaunchBatch1D B = make(b, N);
-      ctl.cs_cfl = b->cfg.cfl_safety * b->cfl[N];
-      B.ctl = ctl;
-      B.u_in = bufs[cur];
-      B.u_out = bufs[cur ^ 1];
-      if (launch_step_1d_batch(B, s)) return bfail(b, CRKFR_ERR_CUDA, "batch step kernel");
-      b->launches += 1;
+      cudaStream_t q = b->side[N];
+      BCK(b, cudaStreamWaitEvent(q, b->ev_fork, 0));
+      if (cfl_mode) {
+        crkfr_status st = class_rates(b, N, u, q);
+        if (st != CRKFR_OK) return st;
+      }
+      int cur = cur0;
+      for (int64_t k = 0; k < nsteps; ++k) {
+        crkfr_status st = class_step(b, N, ctl, k, bufs, cur, q);
+        if (st != CRKFR_OK) return st;
+        cur ^= 1;
+      }
+      BCK(b, cudaEventRecord(b->ev_join[N], q));
+      BCK(b, cudaStreamWaitEvent(s, b->ev_join[N], 0));
     }
-    cur ^= 1;
+  } else {
+    if (cfl_mode) {
+      for (int N = 0; N < kMaxNodes; ++N) {
+        if (!b->nwork[N]) continue;
+        crkfr_status st = class_rates(b, N, u, s);
+        if (st != CRKFR_OK) return st;
+      }
+    }
+    int cur = cur0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+      for (int N = 0; N < kMaxNodes; ++N) {
+        if (!b->nwork[N]) continue;
+        crkfr_status st = class_step(b, N, ctl, k, bufs, cur, s);
+        if (st != CRKFR_OK) return st;
+      }
+      cur ^= 1;
+    }
   }
   if (nsteps % 2 == 1) {
     k_batch_finish<<<nb, 128, 0, s>>>(b->d_states, b->n_inst);
@@ -158,6 +228,52 @@ crkfr_status record(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaSt
     b->launches += 1;
   }
   return CRKFR_OK;
+}
+
+// capture one call into a graph (on the batch's capture stream)
+crkfr_status capture(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaGraph_t* graph,
+                     cudaGraphExec_t* exec) {
+  *graph = nullptr;
+  *exec = nullptr;
+  BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  crkfr_status st = record(b, u, dt, nsteps, b->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (st != CRKFR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return bfail(b, CRKFR_ERR_CUDA, "graph capture failed");
+  if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return bfail(b, CRKFR_ERR_CUDA, "graph instantiation failed");
+  }
+  *graph = g;
+  return CRKFR_OK;
+}
+
+// upload the work lists in the chosen order
+crkfr_status apply_order(crkfr_batch* b) {
+  for (int N = 0; N < kMaxNodes; ++N) {
+    if (!b->nwork[N]) continue;
+    std::vector<WorkItem> w = b->work_h[N];
+    if (b->order == 1)
+      std::stable_sort(w.begin(), w.end(), [&](const WorkItem& x, const WorkItem& y) {
+        return b->E[x.inst] > b->E[y.inst];
+      });
+    BCK(b, cudaMemcpy(b->d_work[N], w.data(), sizeof(WorkItem) * w.size(),
+                      cudaMemcpyHostToDevice));
+  }
+  return CRKFR_OK;
+}
+
+int64_t launches_per_call(const crkfr_batch* b, double dt, int64_t nsteps) {
+  int64_t classes = 0;
+  for (int N = 0; N < kMaxNodes; ++N) classes += b->nwork[N] ? 1 : 0;
+  int64_t k = nsteps * classes + (nsteps % 2 == 1 ? 1 : 0);
+  if (!(dt > 0.0)) k += 1 + classes;
+  return k;
 }
 
 crkfr_status ready(crkfr_batch* b) {
@@ -239,7 +355,12 @@ crkfr_status crkfr_batch_create(crkfr_batch** out, const crkfr_config* cfg, int3
             cudaMalloc(&b->d_swap, sizeof(double) * b->n_state) == cudaSuccess &&
             cudaMalloc(&b->d_states, sizeof(DevState) * n) == cudaSuccess &&
             cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int N = 0; ok && N < kMaxNodes; ++N)
+    ok = cudaStreamCreateWithFlags(&b->side[N], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_join[N], cudaEventDisableTiming) == cudaSuccess;
   for (int N = 0; ok && N < kMaxNodes; ++N) {
+    b->work_h[N] = work[N];
     b->nwork[N] = (int64_t)work[N].size();
     if (b->nwork[N]) {
       ok = cudaMalloc(&b->d_work[N], sizeof(WorkItem) * b->nwork[N]) == cudaSuccess &&
@@ -314,37 +435,116 @@ crkfr_status crkfr_batch_step(crkfr_batch* b, double* u, double dt, int64_t nste
   const bool same = b->gexec && b->g_u == u && b->g_nsteps == nsteps &&
                     ((dt > 0.0) == (b->g_dt > 0.0)) && (!(dt > 0.0) || dt == b->g_dt);
   if (!same) {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    b->gexec = nullptr;
-    b->graph = nullptr;
+    drop_graph(b);
     const int64_t before = b->launches;
-    BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    st = record(b, u, dt, nsteps, b->cap);
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
-    if (st != CRKFR_OK) {
-      if (g) cudaGraphDestroy(g);
-      return st;
-    }
-    if (e != cudaSuccess) return bfail(b, CRKFR_ERR_CUDA, "graph capture failed");
-    b->graph = g;
-    BCK(b, cudaGraphInstantiate(&b->gexec, g, 0));
+    st = capture(b, u, dt, nsteps, &b->graph, &b->gexec);
+    b->launches = before;   // counted when the graph runs
+    if (st != CRKFR_OK) return st;
     b->g_u = u;
     b->g_dt = dt;
     b->g_nsteps = nsteps;
-    b->launches = before;   // counted when the graph runs
   }
-  const int64_t per_call = [&] {
-    int64_t k = 0, classes = 0;
-    for (int N = 0; N < kMaxNodes; ++N) classes += b->nwork[N] ? 1 : 0;
-    k = nsteps * classes + (nsteps % 2 == 1 ? 1 : 0);
-    if (!(dt > 0.0)) k += 1 + classes;
-    return k;
-  }();
   BCK(b, cudaGraphLaunch(b->gexec, s));
-  b->launches += per_call;
+  b->launches += launches_per_call(b, dt, nsteps);
   return CRKFR_OK;
+}
+
+crkfr_status crkfr_batch_set_tuning(crkfr_batch* b, int32_t tiles_per_block, int32_t order,
+                                    int32_t parallel) {
+  if (!b) return CRKFR_ERR_ARG;
+  if (tiles_per_block < 1 || tiles_per_block > 1024 || order < 0 || order > 1 || parallel < 0 ||
+      parallel > 1)
+    return bfail(b, CRKFR_ERR_ARG, "bad tuning");
+  b->tpb = tiles_per_block;
+  b->order = order;
+  b->parallel = parallel;
+  b->tune_ms = 0.0;
+  drop_graph(b);
+  return apply_order(b);
+}
+
+crkfr_status crkfr_batch_get_tuning(const crkfr_batch* b, int32_t* tiles_per_block,
+                                    int32_t* order, int32_t* parallel, double* ms_per_step) {
+  if (!b) return CRKFR_ERR_ARG;
+  if (tiles_per_block) *tiles_per_block = b->tpb;
+  if (order) *order = b->order;
+  if (parallel) *parallel = b->parallel;
+  if (ms_per_step) *ms_per_step = b->tune_ms;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_batch_autotune(crkfr_batch* b, const double* u, int32_t steps, void* stream) {
+  crkfr_status st = ready(b);
+  if (st != CRKFR_OK) return st;
+  if (!u || steps < 1) return bfail(b, CRKFR_ERR_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch state and a copy of the stepping states, restored afterwards
+  double* scratch = nullptr;
+  DevState* saved = nullptr;
+  if (cudaMalloc(&scratch, sizeof(double) * b->n_state) != cudaSuccess ||
+      cudaMalloc(&saved, sizeof(DevState) * b->n_inst) != cudaSuccess) {
+    cudaFree(scratch);
+    cudaGetLastError();
+    return bfail(b, CRKFR_ERR_ALLOC, "device allocation failed");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  BCK(b, cudaMemcpyAsync(saved, b->d_states, sizeof(DevState) * b->n_inst,
+                         cudaMemcpyDeviceToDevice, s));
+  const int64_t launches0 = b->launches;
+  const int tpbs[] = {1, 2, 4, 8};
+  double best = std::numeric_limits<double>::infinity();
+  int bt = 1, bo = 0, bp = 0;
+  st = CRKFR_OK;
+  for (int par = 0; par <= 1 && st == CRKFR_OK; ++par)
+    for (int ord = 0; ord <= 1 && st == CRKFR_OK; ++ord)
+      for (int t : tpbs) {
+        b->tpb = t;
+        b->order = ord;
+        b->parallel = par;
+        st = apply_order(b);
+        if (st != CRKFR_OK) break;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        st = capture(b, scratch, 0.0, steps, &g, &x);
+        if (st != CRKFR_OK) break;
+        float ms = 0.0f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {   // warm, then timed
+          ok = cudaMemcpyAsync(scratch, u, sizeof(double) * b->n_state, cudaMemcpyDeviceToDevice,
+                               s) == cudaSuccess &&
+               cudaMemcpyAsync(b->d_states, saved, sizeof(DevState) * b->n_inst,
+                               cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+               cudaEventRecord(e0, s) == cudaSuccess && cudaGraphLaunch(x, s) == cudaSuccess &&
+               cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+               cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        }
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        if (!ok) {
+          cudaGetLastError();
+          st = bfail(b, CRKFR_ERR_CUDA, "autotune trial failed");
+          break;
+        }
+        if (ms / steps < best) {
+          best = ms / steps;
+          bt = t;
+          bo = ord;
+          bp = par;
+        }
+      }
+  cudaMemcpyAsync(b->d_states, saved, sizeof(DevState) * b->n_inst, cudaMemcpyDeviceToDevice, s);
+  cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  cudaFree(saved);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->launches = launches0;
+  if (st != CRKFR_OK) return st;
+  st = crkfr_batch_set_tuning(b, bt, bo, bp);
+  b->tune_ms = best;
+  return st;
 }
 
 crkfr_status crkfr_batch_get_times(crkfr_batch* b, double* t_host, void* stream) {

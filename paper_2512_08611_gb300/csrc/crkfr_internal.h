@@ -156,6 +156,7 @@ struct LaunchBatch1D {
   const BatchInstance* inst;
   const WorkItem* work;
   int64_t nwork;
+  int64_t grid;       // blocks of the step launch (<= 0 or >= nwork: one per item)
   const double* u_in;
   double* u_out;
   const double* snode;

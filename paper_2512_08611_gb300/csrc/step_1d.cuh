@@ -583,14 +583,19 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
                                               L.lim);
 }
 
-// ragged ensembles: one (instance, tile) pair per block
+// ragged ensembles: (instance, tile) pairs of a work list, a block taking
+// items blockIdx.x, blockIdx.x + gridDim.x, ... (the grid size is a tuning
+// parameter; the tile body's shared-memory phases are separated by barriers,
+// so a block may run several tiles in turn)
 template <int SYS, int N, bool GLL, bool IMEX>
 __global__ void __launch_bounds__(kBlock1D) k_step_1d_batch(const LaunchBatch1D B) {
-  const WorkItem w = B.work[blockIdx.x];
-  const BatchInstance I = B.inst[w.inst];
-  step_1d_tile<SYS, N, GLL, false, IMEX>(B.tab, I.xs, B.u_in + I.u_off, B.u_out + I.u_off,
-                                         B.snode + I.sn_off, B.sface + I.sf_off, I.E, w.tile,
-                                         I.st, B.ctl, w.tile == 0);
+  for (int64_t wi = blockIdx.x; wi < B.nwork; wi += gridDim.x) {
+    const WorkItem w = B.work[wi];
+    const BatchInstance I = B.inst[w.inst];
+    step_1d_tile<SYS, N, GLL, false, IMEX>(B.tab, I.xs, B.u_in + I.u_off, B.u_out + I.u_off,
+                                           B.snode + I.sn_off, B.sface + I.sf_off, I.E, w.tile,
+                                           I.st, B.ctl, w.tile == 0);
+  }
 }
 
 template <int SYS, int N, bool GLL, bool IMEX>
@@ -622,7 +627,8 @@ int launch_step_sys(const Launch1D& L, cudaStream_t s) {
 template <int SYS, int N, bool GLL, bool IMEX>
 int launch_batch_t(const LaunchBatch1D& B, cudaStream_t s) {
   if (B.nwork <= 0) return 0;
-  k_step_1d_batch<SYS, N, GLL, IMEX><<<(unsigned)B.nwork, kBlock1D, 0, s>>>(B);
+  const int64_t blocks = B.grid > 0 && B.grid < B.nwork ? B.grid : B.nwork;
+  k_step_1d_batch<SYS, N, GLL, IMEX><<<(unsigned)blocks, kBlock1D, 0, s>>>(B);
   return (int)cudaGetLastError();
 }
 

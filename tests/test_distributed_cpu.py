@@ -149,3 +149,41 @@ def test_slab_rows_cover_the_mesh():
             parts = [slab_rows(G, r, W) for r in range(W)]
             assert sum(c for _, c in parts) == G
             assert all(parts[i][0] + parts[i][1] == parts[i + 1][0] for i in range(W - 1))
+
+
+def _worker_drop(rank, world, port, out):
+    """Rank 1 leaves between steps (it raises before its exchange); rank 0's
+    exchange must end with an error (peer gone, or the short process-group
+    timeout), not wait forever."""
+    import datetime
+    import time
+    from paper_2512_08611_gb300.distributed import halo_exchange
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    bufs = [torch.zeros(4, dtype=torch.float64) for _ in range(4)]
+    halo_exchange(*bufs)                       # step 1: both ranks present
+    if rank == 1:
+        out[rank] = "left"
+        raise SystemExit(3)                    # leaves before step 2
+    t0 = time.time()
+    try:
+        halo_exchange(*bufs)                   # step 2: the peer is gone
+        out[rank] = "no error"
+    except Exception as e:                     # noqa: BLE001
+        out[rank] = "error after %.1f s: %s" % (time.time() - t0, type(e).__name__)
+
+
+def test_rank_drop_is_detected():
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_drop, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert procs[1].exitcode == 3
+    assert out[1] == "left"
+    assert str(out[0]).startswith("error after"), out[0]

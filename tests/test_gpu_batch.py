@@ -79,3 +79,44 @@ def test_batch_instance_matches_oracle():
     for _ in range(5):
         v = sch.step(v, cs[i], sch.compute_dt(v, cs[i], golden_cfl(N, "gl"), 0.5))
     assert rel_l2(to_host(batch.state_view(u, i)), v) < 1e-11
+
+
+@pytest.mark.parametrize("tpb,order,parallel", [(1, 1, False), (3, 0, True), (8, 1, True),
+                                                (2, 0, False)])
+@pytest.mark.parametrize("graph", [False, True])
+def test_launch_shapes_give_the_same_bits(tpb, order, parallel, graph):
+    """Tiles per block, work-list order and concurrent degree classes change
+    only the schedule: every instance still equals its standalone run."""
+    crk = load()
+    us, cs = inputs(MEMBERS)
+    batch = crk.Batch("swe1d", MEMBERS, gravity=G, cfl_safety=0.5)
+    batch.set_tuning(tpb, order, parallel)
+    assert batch.tuning()[:3] == (tpb, order, parallel)
+    u, c = packed(batch, us, cs)
+    batch.set_coefficients(c)
+    batch.step(u, 0.0, 7, graph=graph)
+    batch.step(u, 0.0, 7, graph=graph)
+    times = batch.times()
+    for i, (N, E, lo, hi) in enumerate(MEMBERS):
+        want, t = alone(crk, N, E, lo, hi, us[i], cs[i], 0.0, 14)
+        assert np.array_equal(to_host(batch.state_view(u, i)), want), i
+        assert times[i] == t
+
+
+def test_autotune_leaves_state_and_times_and_keeps_the_bits():
+    crk = load()
+    us, cs = inputs(MEMBERS)
+    batch = crk.Batch("swe1d", MEMBERS, gravity=G, cfl_safety=0.5)
+    u, c = packed(batch, us, cs)
+    batch.set_coefficients(c)
+    batch.step(u, 0.0, 3)
+    u_before = u.clone()
+    t_before = batch.times()
+    tpb, order, parallel, ms = batch.autotune(u, steps=3)
+    assert tpb in (1, 2, 4, 8) and order in (0, 1) and ms > 0.0
+    assert torch.equal(u, u_before)
+    assert np.array_equal(batch.times(), t_before)
+    batch.step(u, 0.0, 4)
+    for i, (N, E, lo, hi) in enumerate(MEMBERS):
+        want, _ = alone(crk, N, E, lo, hi, us[i], cs[i], 0.0, 7)
+        assert np.array_equal(to_host(batch.state_view(u, i)), want), i
