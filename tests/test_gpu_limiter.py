@@ -176,3 +176,28 @@ def test_limiter_configuration_errors(crk):
     with pytest.raises(crk.CrkfrError) as e:
         s1.set_limiter("fixed", 1.5)
     assert e.value.status == -1
+
+
+def test_config2_size_with_limiter(crk):
+    """The 1D workload's size (1e5 elements, N = 4, GL, [0, 100]) with the
+    indicator-driven limiter: one CFL step against the oracle on the whole
+    mesh (smooth data: the indicator stays off almost everywhere, the step
+    is then the plain cRK-FR step)."""
+    from paper_2512_08611_gb300.workloads import SWE1DInput, accept_seed
+    N, E = 4, 100000
+    bs = Basis(N)
+    x, dx = positions_1d(bs, E, 0.0, 100.0)
+    inp, _ = accept_seed(lambda s: SWE1DInput(seed=s, L=100.0), (x,), 0)
+    u, b = inp.state(x)
+    sch = Scheme1D(ShallowWater1D(G), N, dx)
+    lim = Blending1D(sch)
+    dt = sch.compute_dt(u, b, golden_cfl(N, "gl"), 0.5)
+    want = lim.step(u, b, dt)
+    s = crk.Solver("swe1d", N, gravity=G, cfl_safety=0.5, cfl_number=golden_cfl(N, "gl"))
+    s.set_mesh([E], [0.0], [100.0])
+    s.set_coefficients(to_dev(b))
+    s.set_limiter("blend")
+    du = to_dev(u)
+    s.step(du, 0.0, 1)
+    assert rel_l2(to_host(du), want) < TOL_STEP
+    assert np.max(np.abs(to_host(s.limiter_alpha()) - lim.last_alpha)) < 1e-12

@@ -170,3 +170,41 @@ def test_adjoint_of_wb_is_refused(crk):
     with pytest.raises(crk.CrkfrError) as e:
         s.step_adjoint(to_dev(u), to_dev(np.ones_like(u)), 1e-3)
     assert e.value.status == -2
+
+
+def test_full_size_sampled_step_wb_and_friction(crk):
+    """The 1024^2, N = 3 workload in its well-balanced form with Chezy
+    friction and a current, one CFL step as the benchmark launches it; the
+    oracle recomputes 128 sampled elements (incl. the corners)."""
+    N, E = 3, 1024
+    u, b, dx, dy = case_2d(N, "gl", E, E)
+    Cf = 0.0025
+    sch = Scheme2D(ShallowWater2DWB(G), N, dx, dy, source=ChezyFriction(Cf))
+    dt = sch.compute_dt(u, b, golden_cfl_imex(N, "gl"), 0.5)
+    s = solver(crk, "swe2d_wb", N, "gl", [E, E], 100.0, b, "chezy", Cf)
+    du = to_dev(u)
+    s.step(du, 0.0, 1)
+    got = to_host(du)
+    rng = np.random.default_rng(12)
+    ey = np.concatenate([[0, 0, E - 1, E - 1], rng.integers(0, E, 124)])
+    ex = np.concatenate([[0, E - 1, 0, E - 1], rng.integers(0, E, 124)])
+    want = sch.step_elements(u, b, dt, ey, ex)
+    assert rel_l2(got[:, ey, ex], want) < TOL_STEP
+    s.status()
+
+
+def test_thousand_steps_wb_with_friction(crk):
+    """1000 CFL steps of the well-balanced 1D form with friction: 1e-10
+    relative L2 against the oracle's loop."""
+    N, E = 3, 256
+    u, b, dx = case_1d(N, "gl", E)
+    sch = Scheme1D(ShallowWater1DWB(G), N, dx, source=ChezyFriction(0.2))
+    cfl = golden_cfl_imex(N, "gl")
+    v = u
+    for _ in range(1000):
+        v = sch.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
+    s = solver(crk, "swe1d_wb", N, "gl", [E], 100.0, b, "chezy", 0.2)
+    du = to_dev(u)
+    s.step(du, 0.0, 1000)
+    assert rel_l2(to_host(du), v) < 1e-10
+    s.status()
