@@ -1,5 +1,5 @@
-"""Subcell blending limiter with admissibility preservation, 1D (test
-infrastructure only).
+"""Subcell blending limiter with admissibility preservation, 1D and its
+tensor-product 2D extension (test infrastructure only).
 
 Sec. 4 of the paper, in its order:
 
@@ -193,5 +193,161 @@ class Blending1D:
             eps = 0.1 * np.min(P(uL), axis=-1, keepdims=True)
             th = np.min(theta_linear(P, eps, uL, out), axis=-1)
             out = th[:, None] * out + (1.0 - th)[:, None] * uL
+        self.last_alpha = alpha
+        return out
+
+
+# ----------------------------------------------------------------------------
+# 2D (tensor-product subcells)
+# ----------------------------------------------------------------------------
+def hennemann_alpha_2d(basis, X, a=0.5, c=1.8, alpha_min=1e-3, alpha_max=1.0, smooth=True):
+    """alpha per element from the nodal indicator variable X[ey, ex, q, p]
+    (periodic mesh): the tensor-product modal coefficients m_ij; the energy
+    share of the modes with i = N or j = N, and (N >= 2) of those with
+    max(i, j) = N - 1 among the modes below N; the same logistic map as in
+    1D; smoothing with half the largest of the four face neighbours."""
+    N = len(basis.xi) - 1
+    n = N + 1
+    V = np.stack([legendre_orthonormal(j, 2.0 * basis.xi - 1.0) for j in range(n)], axis=1)
+    Vi = np.linalg.inv(V)
+    m = np.einsum("iq,jp,...qp->...ij", Vi, Vi, X)
+    m2 = m * m
+    tot = np.sum(m2, axis=(-2, -1))
+    clip1 = np.sum(m2[..., :N, :N], axis=(-2, -1))
+    e1 = np.where(tot > 0.0, (tot - clip1) / np.where(tot > 0.0, tot, 1.0), 0.0)
+    if N >= 2:
+        clip2 = np.sum(m2[..., :N - 1, :N - 1], axis=(-2, -1))
+        e2 = np.where(clip1 > 0.0, (clip1 - clip2) / np.where(clip1 > 0.0, clip1, 1.0), 0.0)
+        energy = np.maximum(e1, e2)
+    else:
+        energy = e1
+    T = a * 10.0 ** (-c * (N + 1) ** 0.25)
+    s = np.log((1.0 - 1e-4) / 1e-4)
+    alpha = 1.0 / (1.0 + np.exp(-s / T * (energy - T)))
+    alpha = np.where(alpha < alpha_min, 0.0, alpha)
+    alpha = np.where(alpha > 1.0 - alpha_min, 1.0, alpha)
+    alpha = np.minimum(alpha, alpha_max)
+    if smooth:
+        nb = np.maximum(np.maximum(np.roll(alpha, 1, 0), np.roll(alpha, -1, 0)),
+                        np.maximum(np.roll(alpha, 1, 1), np.roll(alpha, -1, 1)))
+        alpha = np.maximum(alpha, 0.5 * nb)
+    return alpha
+
+
+class _Dir:
+    """The x or y direction of a 2D system, seen as a 1D system for the
+    first-order fluxes."""
+
+    def __init__(self, sy, d):
+        self.flux = sy.flux_x if d == 0 else sy.flux_y
+        self.ncprod = sy.ncprod_x if d == 0 else sy.ncprod_y
+        self.speed = sy.speed_x if d == 0 else sy.speed_y
+        if hasattr(sy, "dissipated"):
+            self.dissipated = sy.dissipated
+
+
+class Blending2D:
+    """Blended cRK-FR / subcell FV step of a Scheme2D, the tensor-product
+    extension of Sec. 4 (reading): subcells of w_p dx x w_q dy, first-order
+    fluxes of Eq. combined.num.flux across every x- and y-subface, Eq. Fblend
+    per face node.  The first-order update splits as
+        u^L = 1/2 (u - 2 dt/(w_p dx) dx-differences) + 1/2 (u - 2 dt/(w_q dy) dy-differences),
+    so Algorithm 1 limits each face's flux so that the doubled-dt
+    one-direction updates of its two adjacent nodes stay admissible (their
+    average then is); Algorithm 2 acts per element on all n^2 nodes."""
+
+    def __init__(self, scheme, alpha=None, indicator_var=0, admissible=True):
+        self.sch = scheme
+        self.alpha = alpha
+        self.var = indicator_var
+        self.admissible = admissible
+
+    def coefficients(self, u, c):
+        if self.alpha is None:
+            return hennemann_alpha_2d(self.sch.basis, u[self.var])
+        return np.broadcast_to(np.asarray(self.alpha, dtype=float), u.shape[1:3]).copy()
+
+    def step(self, u, c, dt):
+        sch, bs = self.sch, self.sch.basis
+        sy = sch.sys
+        N = len(bs.xi) - 1
+        w = bs.w
+        alpha = self.coefficients(u, c)
+        constraints = getattr(sy, "admissibility", []) if self.admissible else []
+        diss = getattr(sy, "dissipated", None)
+        loc = sch.local(u, c, dt)
+        rx = lambda X: np.roll(X, 1, axis=-2)   # element (ey, ex-1) of trace arrays (.., ey, ex, n)
+        ry = lambda X: np.roll(X, 1, axis=-3)   # element (ey-1, ex)
+        dirs = (_Dir(sy, 0), _Dir(sy, 1))
+
+        # high-order face fluxes: x-face (ey, k) between (ey, k-1) | (ey, k),
+        # y-face (k, ex) between (k-1, ex) | (k, ex); one value per face node
+        Hx = face_fluxes(rx(loc["F_r"]), loc["F_l"], rx(loc["U_r"]), loc["U_l"], rx(loc["un_r"]),
+                         loc["un_l"], rx(loc["c_r"]), loc["c_l"], sy.speed_x, sy.ncprod_x,
+                         dissipated=diss)
+        Hy = face_fluxes(ry(loc["G_t"]), loc["G_b"], ry(loc["U_t"]), loc["U_b"], ry(loc["un_t"]),
+                         loc["un_b"], ry(loc["c_t"]), loc["c_b"], sy.speed_y, sy.ncprod_y,
+                         dissipated=diss)
+        # first-order fluxes at element faces (nodal values next to the face)
+        # and across the inner subfaces
+        ex_ = lambda X, p: X[..., :, p]            # column p of every element: (.., ey, ex, q)
+        ey_ = lambda X, q: X[..., q, :]            # row q: (.., ey, ex, p)
+        fxo = low_order_fluxes(dirs[0], rx(ex_(u, N)), ex_(u, 0), rx(ex_(c, N)), ex_(c, 0))
+        fyo = low_order_fluxes(dirs[1], ry(ey_(u, N)), ey_(u, 0), ry(ey_(c, N)), ey_(c, 0))
+        fxi = low_order_fluxes(dirs[0], u[..., :, :-1], u[..., :, 1:], c[..., :, :-1], c[..., :, 1:])
+        fyi = low_order_fluxes(dirs[1], u[..., :-1, :], u[..., 1:, :], c[..., :-1, :], c[..., 1:, :])
+
+        # Eq. Fblend
+        ax = (0.5 * (np.roll(alpha, 1, axis=1) + alpha))[..., None]
+        ay = (0.5 * (np.roll(alpha, 1, axis=0) + alpha))[..., None]
+        Fx = [(1.0 - ax) * Hx[k] + ax * fxo[k] for k in (0, 1)]
+        Fy = [(1.0 - ay) * Hy[k] + ay * fyo[k] for k in (0, 1)]
+
+        # Algorithm 1 with doubled-dt one-direction updates
+        for P in constraints:
+            for F, fo, fi, width, d in ((Fx, fxo, fxi, sch.dx, 0), (Fy, fyo, fyi, sch.dy, 1)):
+                if d == 0:
+                    u0, uN = ex_(u, 0), rx(ex_(u, N))
+                    f0_in = fi[0][..., :, 0]                 # right flux of node p = 0
+                    fN_in = rx(fi[1][..., :, N - 1])         # left flux of node p = N of (ey, ex-1)
+                else:
+                    u0, uN = ey_(u, 0), ry(ey_(u, N))
+                    f0_in = fi[0][..., 0, :]
+                    fN_in = ry(fi[1][..., N - 1, :])
+                c0 = 2.0 * dt / (w[0] * width)
+                cN = 2.0 * dt / (w[N] * width)
+                low0 = u0 - c0 * (f0_in - fo[1])
+                lowN = uN - cN * (fo[0] - fN_in)
+                t0 = u0 - c0 * (f0_in - F[1])
+                tN = uN - cN * (F[0] - fN_in)
+                th = np.minimum(theta_linear(P, 0.1 * P(low0), low0, t0),
+                                theta_linear(P, 0.1 * P(lowN), lowN, tN))
+                F[0] = th * F[0] + (1.0 - th) * fo[0]
+                F[1] = th * F[1] + (1.0 - th) * fo[1]
+
+        # high-order update with the face fluxes (corrections of Scheme2D)
+        Tx_m, Tx_p = Fx[0] - Hx[2], Fx[1] - Hx[3]
+        Ty_m, Ty_p = Fy[0] - Hy[2], Fy[1] - Hy[3]
+        Tr = np.roll(Tx_m, -1, axis=-2)
+        Tt = np.roll(Ty_m, -1, axis=-3)
+        uH = u - dt * (loc["vol"] + sch._corrections(Tr, Tx_p, Tt, Ty_p))
+
+        # first-order update
+        right = np.concatenate([fxi[0], np.roll(Fx[0], -1, axis=-2)[..., :, None]], axis=-1)
+        left = np.concatenate([Fx[1][..., :, None], fxi[1]], axis=-1)
+        top = np.concatenate([fyi[0], np.roll(Fy[0], -1, axis=-3)[..., None, :]], axis=-2)
+        bottom = np.concatenate([Fy[1][..., None, :], fyi[1]], axis=-2)
+        uL = (u - dt / (w[None, :] * sch.dx) * (right - left)
+              - dt / (w[:, None] * sch.dy) * (top - bottom))
+        if sch.source is not None:
+            uL = point_implicit_solve(sch.source, uL, c, dt)
+
+        # Eq. blended.scheme and Algorithm 2 per element
+        a4 = alpha[..., None, None]
+        out = (1.0 - a4) * uH + a4 * uL
+        for P in constraints:
+            eps = 0.1 * np.min(P(uL), axis=(-2, -1), keepdims=True)
+            th = np.min(theta_linear(P, eps, uL, out), axis=(-2, -1))[..., None, None]
+            out = th * out + (1.0 - th) * uL
         self.last_alpha = alpha
         return out

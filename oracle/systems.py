@@ -70,6 +70,7 @@ class ShallowWater2D:
     Spectral radii: |u| + sqrt(g h) in x, |v| + sqrt(g h) in y."""
     M = 3
     name = "swe2d"
+    admissibility = [lambda u: u[0]]
 
     def __init__(self, g=9.81):
         self.g = g

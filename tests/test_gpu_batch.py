@@ -120,3 +120,41 @@ def test_autotune_leaves_state_and_times_and_keeps_the_bits():
     for i, (N, E, lo, hi) in enumerate(MEMBERS):
         want, _ = alone(crk, N, E, lo, hi, us[i], cs[i], 0.0, 7)
         assert np.array_equal(to_host(batch.state_view(u, i)), want), i
+
+
+def test_full_size_ensemble_sampled():
+    """The 256-instance ensemble of the benchmark (element counts
+    log-uniform in [2^10, 2^16], N in {2, 3, 4}), autotuned as the benchmark
+    does, 3 CFL steps in a graph: 8 sampled instances equal their standalone
+    runs bitwise and one matches the oracle."""
+    from paper_2512_08611_gb300.workloads import ensemble_members
+    crk = load()
+    L = 100.0
+    mem = ensemble_members(256, seed=0)
+    members, us, cs = [], [], []
+    for m in mem:
+        N, E = m["N"], m["E"]
+        x, _ = positions_1d(Basis(N), E, 0.0, L)
+        inp, _ = accept_seed(lambda s: SWE1DInput(seed=s, L=L), (x,), m["seed"])
+        u, b = inp.state(x)
+        members.append((N, E, 0.0, L))
+        us.append(u)
+        cs.append(b)
+    batch = crk.Batch("swe1d", members, gravity=G, cfl_safety=0.5)
+    u, c = packed(batch, us, cs)
+    batch.set_coefficients(c)
+    batch.autotune(u, steps=3)
+    batch.step(u, 0.0, 3, graph=True)
+    batch.status()
+    rng = np.random.default_rng(5)
+    for i in rng.choice(len(members), 8, replace=False):
+        N, E, lo, hi = members[i]
+        want, _ = alone(crk, N, E, lo, hi, us[i], cs[i], 0.0, 3)
+        assert np.array_equal(to_host(batch.state_view(u, i)), want), i
+    i = int(np.argmin([m[1] for m in members]))
+    N, E, lo, hi = members[i]
+    sch = Scheme1D(ShallowWater1D(G), N, (hi - lo) / E)
+    v = us[i]
+    for _ in range(3):
+        v = sch.step(v, cs[i], sch.compute_dt(v, cs[i], golden_cfl(N, "gl"), 0.5))
+    assert rel_l2(to_host(batch.state_view(u, i)), v) < 1e-12
