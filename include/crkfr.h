@@ -230,29 +230,37 @@ crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
 crkfr_status crkfr_step_adjoint(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
                                 double* ubar0_dev, double* bbar_dev, double dt, void* stream);
 
-/* Subcell blending limiter of the 1D step (Sec. 4).  Each element blends the
- * cRK-FR update with a first-order finite-volume update on its N+1 subcells
- * of widths w_p dx (Eqs. subcell.defn, low.order.update; non-conservative
- * Rusanov fluxes of Eq. combined.num.flux; a source, if any, by backward
+/* Subcell blending limiter of the step (Sec. 4; in 2D its tensor-product
+ * extension).  Each element blends the cRK-FR update with a first-order
+ * finite-volume update on its subcells of widths w_p dx (x w_q dy in 2D)
+ * (Eqs. subcell.defn, low.order.update; non-conservative Rusanov fluxes of
+ * Eq. combined.num.flux across every subface; a source, if any, by backward
  * Euler), u = (1 - alpha_e) u^H + alpha_e u^L (Eq. blended.scheme).  Both
  * schemes use the face flux (1 - alpha_f) F^HO + alpha_f f^LO with alpha_f
  * the mean of the two elements' alpha (Eq. Fblend).  For shallow water the
  * face flux is limited so that the two low-order node updates next to the
- * face keep h above a tenth of their first-order values (Algorithm 1), and
- * each element's blend is limited towards its first-order update so that h
- * stays above a tenth of the smallest first-order depth (Algorithm 2);
- * h > 0 then holds when the first-order scheme on the smallest subcell is
- * positive, lam dt <= w_min dx / 2 (choose C_s accordingly).
+ * face keep h above a tenth of their first-order values (Algorithm 1; in 2D
+ * on the one-direction updates with 2 dt, whose mean is the first-order
+ * update), and each element's blend is limited towards its first-order
+ * update so that h stays above a tenth of the smallest first-order depth
+ * (Algorithm 2); h > 0 then holds when the first-order scheme on the
+ * smallest subcell is positive, lam dt <= w_min dx / 2 in 1D, and in 2D the
+ * same for each one-direction update with 2 dt (choose C_s accordingly).
  *
  * mode CRKFR_LIMITER_BLEND: alpha_e from the smoothness indicator of
- * Hennemann et al. (2021), on v (advection) or h (shallow water), raised to
- * half the larger neighbour value; CRKFR_LIMITER_FIXED: alpha_e = alpha for
- * every element (for checks); CRKFR_LIMITER_NONE switches it off.  1D
- * contexts with N >= 1 only (else CRKFR_ERR_UNSUPPORTED); call after
- * crkfr_set_mesh, which switches the limiter off.  Applies to crkfr_step,
- * crkfr_advance and crkfr_step_host; crkfr_residual stays that of the
- * unlimited step.  crkfr_limiter_alpha copies the alpha_e of the last
- * limited step into alpha_dev (n_elem doubles, device). */
+ * Hennemann et al. (2021), on v (advection) or h (shallow water; in 2D on
+ * the tensor-product modes), raised to half the largest neighbour value;
+ * CRKFR_LIMITER_FIXED: alpha_e = alpha for every element (for checks);
+ * CRKFR_LIMITER_NONE switches it off.  Contexts with N >= 1 only, 2D meshes
+ * whole and periodic (not in subdomain mode) (else CRKFR_ERR_UNSUPPORTED);
+ * call after crkfr_set_mesh, which switches the limiter off.  Applies to
+ * crkfr_step, crkfr_advance and crkfr_step_host; crkfr_residual stays that
+ * of the unlimited step; crkfr_step_local, crkfr_step_faces and
+ * crkfr_step_adjoint refuse limited contexts.  A 2D context allocates the
+ * limiter's buffers (one more state and 32 (Ey + 1) Ex (N+1) doubles of face
+ * data) on the first call that switches it on.  crkfr_limiter_alpha copies
+ * the alpha_e of the last limited step into alpha_dev (n_elem doubles,
+ * element (ey, ex) at ey Ex + ex, device). */
 typedef enum {
   CRKFR_LIMITER_NONE = 0,
   CRKFR_LIMITER_BLEND = 1,

@@ -389,14 +389,17 @@ class Solver:
     LIMITERS = {None: 0, "blend": 1, "fixed": 2}
 
     def set_limiter(self, mode="blend", alpha=0.0):
-        """Subcell blending limiter of a 1D step: 'blend' (smoothness
-        indicator), 'fixed' (alpha for every element) or None (off)."""
+        """Subcell blending limiter of the step (1D, or 2D on a whole periodic
+        mesh): 'blend' (smoothness indicator), 'fixed' (alpha for every
+        element) or None (off)."""
         self._check(lib().crkfr_set_limiter(self.h, self.LIMITERS[mode], float(alpha)))
 
     def limiter_alpha(self):
-        """alpha_e of the last limited step (cuda float64 tensor)."""
+        """alpha_e of the last limited step (cuda float64 tensor: (E,) in 1D,
+        (Ey, Ex) in 2D)."""
         import torch
-        out = torch.empty(self.n_elem[0], dtype=torch.float64, device="cuda")
+        shape = tuple(reversed(self.n_elem))
+        out = torch.empty(shape, dtype=torch.float64, device="cuda")
         self._check(lib().crkfr_limiter_alpha(self.h, ctypes.c_void_p(out.data_ptr()), _stream()))
         return out
 

@@ -36,9 +36,12 @@ struct crkfr_ctx {
   double* d_atrx = nullptr;   // adjoint traces and face-jump adjoints (crkfr_step_adjoint)
   double* d_atry = nullptr;
   double* d_gbar = nullptr;
-  double* d_cnode = nullptr;      // 1D: nodal coefficient field (subcell limiter)
-  double* d_alpha_raw = nullptr;  // 1D: indicator per element before smoothing
-  double* d_alpha = nullptr;      // 1D: blending coefficient of the last limited step
+  double* d_cnode = nullptr;      // nodal coefficient field (subcell limiter)
+  double* d_alpha_raw = nullptr;  // indicator per element before smoothing
+  double* d_alpha = nullptr;      // blending coefficient of the last limited step
+  double* d_ulo = nullptr;        // 2D limiter: first-order update without face terms
+  double* d_lx = nullptr;         // 2D limiter: x- and y-face data
+  double* d_ly = nullptr;
   int limit_mode = CRKFR_LIMITER_NONE;
   double alpha_fixed = 0.0;
   DevState* d_state = nullptr;
@@ -92,7 +95,10 @@ void free_buffers(crkfr_ctx* c) {
   cudaFree(c->d_cnode);
   cudaFree(c->d_alpha_raw);
   cudaFree(c->d_alpha);
-  c->d_cnode = c->d_alpha_raw = c->d_alpha = nullptr;
+  cudaFree(c->d_ulo);
+  cudaFree(c->d_lx);
+  cudaFree(c->d_ly);
+  c->d_cnode = c->d_alpha_raw = c->d_alpha = c->d_ulo = c->d_lx = c->d_ly = nullptr;
   c->d_atrx = c->d_atry = c->d_gbar = nullptr;
   c->d_snode = c->d_sface = c->d_work = c->d_trx = c->d_try = c->d_stage = nullptr;
   c->d_state = nullptr;
@@ -285,6 +291,15 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
     }
   } else {
     Launch2D L = make2d(c);
+    if (c->limit_mode != CRKFR_LIMITER_NONE) {
+      L.lim.mode = c->limit_mode;
+      L.lim.alpha_fixed = c->alpha_fixed;
+      L.lim.alpha = c->d_alpha;
+      L.lim.cnode = c->d_cnode;
+      L.lim.ulo = c->d_ulo;
+      L.lim.lx = c->d_lx;
+      L.lim.ly = c->d_ly;
+    }
     for (int64_t k = 0; k < nsteps; ++k) {
       ctl.slot_read = (int)(c->nstep % 3);
       ctl.slot_write = (int)((c->nstep + 1) % 3);
@@ -293,6 +308,12 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
       L.ctl = ctl;
       L.u_in = u;
       L.u_out = u;
+      if (c->limit_mode != CRKFR_LIMITER_NONE) {
+        int ea = timed(c, CRKFR_KERNEL_INDICATOR, s,
+                       [&] { return launch_alpha_2d(L, c->d_alpha_raw, c->d_alpha, s); });
+        if (ea) return cuda_fail(c, ea, "indicator kernels");
+        c->launches += c->limit_mode == CRKFR_LIMITER_BLEND ? 2 : 1;
+      }
       int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
       if (!e) e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
       if (e) return cuda_fail(c, e, "2D step kernels");
@@ -444,8 +465,9 @@ crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, co
     return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
   }
   c->limit_mode = CRKFR_LIMITER_NONE;
-  if (dim == 1) {
-    if (cudaMalloc(&c->d_cnode, sizeof(double) * Ne * n) != cudaSuccess ||
+  {
+    const size_t cn = dim == 1 ? (size_t)Ne * n : (size_t)Ne * n * n;
+    if (cudaMalloc(&c->d_cnode, sizeof(double) * cn) != cudaSuccess ||
         cudaMalloc(&c->d_alpha_raw, sizeof(double) * Ne) != cudaSuccess ||
         cudaMalloc(&c->d_alpha, sizeof(double) * Ne) != cudaSuccess) {
       free_buffers(c);
@@ -509,7 +531,9 @@ crkfr_status crkfr_set_coefficients(crkfr_ctx* c, const double* coef, void* stre
   });
   if (e) return cuda_fail(c, e, "coefficient kernel");
   c->launches += 1;
-  if (c->dim == 1)
+  // the limiter's first-order fluxes read the nodal field (a subdomain's
+  // coefficients carry halo rows, and a subdomain has no limiter)
+  if (!c->subdomain)
     CK(c, cudaMemcpyAsync(c->d_cnode, coef, sizeof(double) * c->n_coef, cudaMemcpyDeviceToDevice,
                           s));
   c->coef_set = true;
@@ -522,11 +546,26 @@ crkfr_status crkfr_set_limiter(crkfr_ctx* c, int32_t mode, double alpha) {
   if (mode < CRKFR_LIMITER_NONE || mode > CRKFR_LIMITER_FIXED)
     return fail(c, CRKFR_ERR_ARG, "unknown limiter mode");
   if (mode != CRKFR_LIMITER_NONE) {
-    if (c->dim != 1) return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter is built for 1D meshes");
     if (c->cfg.degree < 1) return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter needs N >= 1");
+    if (c->subdomain)
+      return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter is built for whole periodic meshes");
   }
   if (mode == CRKFR_LIMITER_FIXED && !(alpha >= 0.0 && alpha <= 1.0))
     return fail(c, CRKFR_ERR_ARG, "alpha must lie in [0, 1]");
+  if (mode != CRKFR_LIMITER_NONE && c->dim == 2 && !c->d_ulo) {
+    const int64_t n = c->basis.n, Ne = c->Ex * c->Ey;
+    const size_t lx = (size_t)8 * 2 * Ne * n, ly = (size_t)8 * 2 * (c->Ey + 2) * c->Ex * n;
+    if (cudaMalloc(&c->d_ulo, sizeof(double) * c->n_state) != cudaSuccess ||
+        cudaMalloc(&c->d_lx, sizeof(double) * lx) != cudaSuccess ||
+        cudaMalloc(&c->d_ly, sizeof(double) * ly) != cudaSuccess) {
+      cudaFree(c->d_ulo);
+      cudaFree(c->d_lx);
+      cudaFree(c->d_ly);
+      c->d_ulo = c->d_lx = c->d_ly = nullptr;
+      cudaGetLastError();
+      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+    }
+  }
   c->limit_mode = mode;
   c->alpha_fixed = mode == CRKFR_LIMITER_FIXED ? alpha : 0.0;
   return CRKFR_OK;
@@ -534,9 +573,9 @@ crkfr_status crkfr_set_limiter(crkfr_ctx* c, int32_t mode, double alpha) {
 
 crkfr_status crkfr_limiter_alpha(crkfr_ctx* c, double* alpha_dev, void* stream) {
   if (!c || !alpha_dev) return fail(c, CRKFR_ERR_ARG, "null argument");
-  if (c->dim != 1) return fail(c, CRKFR_ERR_STATE, "no 1D mesh set");
-  CK(c, cudaMemcpyAsync(alpha_dev, c->d_alpha, sizeof(double) * c->Ex, cudaMemcpyDeviceToDevice,
-                        (cudaStream_t)stream));
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
+  CK(c, cudaMemcpyAsync(alpha_dev, c->d_alpha, sizeof(double) * c->Ex * c->Ey,
+                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return CRKFR_OK;
 }
 
@@ -661,6 +700,8 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
 crkfr_status crkfr_set_subdomain(crkfr_ctx* c, int32_t enable) {
   if (!c) return CRKFR_ERR_ARG;
   if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "subdomains are 2D slabs");
+  if (enable && c->limit_mode != CRKFR_LIMITER_NONE)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter is built for whole periodic meshes");
   c->subdomain = enable != 0;
   c->coef_set = false;
   return CRKFR_OK;
@@ -686,6 +727,8 @@ crkfr_status crkfr_step_local(crkfr_ctx* c, const double* u, double dt, void* st
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
   if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "phased steps are 2D");
+  if (c->limit_mode != CRKFR_LIMITER_NONE)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
   cudaStream_t s = (cudaStream_t)stream;
@@ -711,6 +754,8 @@ crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
   if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "phased steps are 2D");
+  if (c->limit_mode != CRKFR_LIMITER_NONE)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   StepCtl ctl{};
@@ -739,6 +784,8 @@ crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* uba
   if (c->cfg.source != CRKFR_SRC_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step has no source term");
   if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "no adjoint in subdomain mode");
+  if (c->limit_mode != CRKFR_LIMITER_NONE)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step has no limiter");
   if (!u || !ubar1 || !ubar0 || !bbar) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
   const size_t bytes = sizeof(double) * c->n_state;

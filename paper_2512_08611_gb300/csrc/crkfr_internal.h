@@ -169,6 +169,19 @@ int launch_step_1d_batch_imex(const LaunchBatch1D& B, void* stream);   // kernel
 int launch_rate_1d_batch(const LaunchBatch1D& B, int slot, void* stream);
 constexpr int kTile1D = 126;   // elements a 1D block owns (128 threads, 2 halo)
 
+// Subcell blending limiter of a 2D step (kernels_limit2d.cu).
+struct LimitArgs2D {
+  int mode;                 // CRKFR_LIMITER_*: 0 none, 1 indicator, 2 fixed alpha
+  double alpha_fixed;       // alpha of mode 2
+  const double* alpha;      // [Ey][Ex] blending coefficient of the step (smoothed)
+  const double* cnode;      // [Ey][Ex][n][n] nodal coefficient field c
+  double* ulo;              // [3][Ey][Ex][n][n] first-order update without the
+                            // element-face terms (local kernel -> face kernel)
+  double* lx;               // x-face data [8][2][Ey][Ex][n]: side 0 the element's
+                            // node p = 0, side 1 node p = N
+  double* ly;               // y-face data [Ey+2][2][8][Ex][n], rows as the y traces
+};
+
 struct Launch2D {
   int N;
   bool gll;
@@ -188,6 +201,7 @@ struct Launch2D {
   DevState* st;
   Tables tab;
   StepCtl ctl;
+  LimitArgs2D lim;       // mode 0: no limiter
 };
 // Adjoint of one 2D step (kernels_adj2d.cu); the forward local kernel must
 // have written the traces of u^n first.
@@ -219,6 +233,14 @@ int launch_step_1d_batch_wb(const LaunchBatch1D& B, void* stream);
 int launch_local_2d_wb(const Launch2D& L, void* stream);
 int launch_face_2d_wb(const Launch2D& L, void* stream);
 int launch_rate_2d(const Launch2D& L, int slot, void* stream);
+// limited instantiations (kernels_limit2d.cu, kernels_limit2d_wb.cu) and the
+// blending coefficients of a 2D step: indicator into alpha_raw (mode 1), then
+// the smoothed (mode 1) or fixed (mode 2) coefficients into alpha
+int launch_local_2d_limit(const Launch2D& L, void* stream);
+int launch_face_2d_limit(const Launch2D& L, void* stream);
+int launch_local_2d_limit_wb(const Launch2D& L, void* stream);
+int launch_face_2d_limit_wb(const Launch2D& L, void* stream);
+int launch_alpha_2d(const Launch2D& L, double* alpha_raw, double* alpha, void* stream);
 // c: [Ey][Ex][n][n] (periodic in y) or, with halo_rows, [Ey+2][Ex][n][n]
 // holding the row below and the row above the mesh as rows 0 and Ey+1
 int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, bool halo_rows,

@@ -106,6 +106,14 @@ __device__ __forceinline__ void step_bookkeeping(const StepCtl& c, DevState* st,
   if (dt > 0.0) st->nadv += 1ull;
 }
 
+// Weight of the candidate b in theta b + (1 - theta) a for the linear
+// constraint P (Eq. theta.formula): 1 unless P(b) < eps.
+__device__ __forceinline__ double theta_lin(double eps, double Pa, double Pb) {
+  if (!(Pb < eps)) return 1.0;
+  const double den = Pb - Pa;
+  return den != 0.0 ? fmin(1.0, fabs((eps - Pa) / den)) : 1.0;
+}
+
 // Block-wide max of a non-negative double, then one atomicMax on the bit
 // pattern.  Every thread of the block must call it.
 template <int BLOCK>

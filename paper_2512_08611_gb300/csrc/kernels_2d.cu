@@ -128,12 +128,14 @@ __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c, 
 
 
 int launch_local_2d(const Launch2D& L, void* stream) {
+  if (L.lim.mode != CRKFR_LIMITER_NONE && !L.ctl.residual) return launch_local_2d_limit(L, stream);
   if (L.wb) return launch_local_2d_wb(L, stream);
   if (L.imex) return launch_local_2d_imex(L, stream);
   return launch_local_dispatch<false, false>(L, (cudaStream_t)stream);
 }
 
 int launch_face_2d(const Launch2D& L, void* stream) {
+  if (L.lim.mode != CRKFR_LIMITER_NONE && !L.ctl.residual) return launch_face_2d_limit(L, stream);
   if (L.wb) return launch_face_2d_wb(L, stream);
   return launch_face_dispatch<false>(L, (cudaStream_t)stream);
 }

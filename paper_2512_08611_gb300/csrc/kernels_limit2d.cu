@@ -1,0 +1,125 @@
+// Subcell blending limiter of the 2D shallow-water step (the tensor-product
+// extension of Sec. 4): the smoothness indicator and coefficient kernels and
+// the limited instantiations of the standard form's local and face kernels
+// (local_2d.cuh, face_2d.cuh), with and without Chezy friction.
+//
+// Indicator (Hennemann et al. (2021), as in 1D, on the tensor-product
+// orthonormal Legendre modes m_ij of h, i the y and j the x degree): the
+// energy share of the modes with max(i, j) = N, and for N >= 2 the share of
+// the modes with max(i, j) = N - 1 among those below N; the larger one goes
+// through the same logistic map and cut-offs as in 1D.  The coefficient of
+// the step is the larger of an element's value and half the largest value of
+// its four face neighbours.
+#include <cuda_runtime.h>
+
+#include "face_2d.cuh"
+#include "local_2d.cuh"
+
+namespace crkfr {
+namespace {
+
+constexpr int kBlockAlpha = 128;
+
+template <int N>
+__global__ void __launch_bounds__(kBlockAlpha) k_alpha_2d(int64_t Ne, const double* __restrict__ h,
+                                                          const Tables T,
+                                                          double* __restrict__ alpha_raw) {
+  constexpr int n = N + 1;
+  constexpr int nn = n * n;
+  const int64_t e = (int64_t)blockIdx.x * kBlockAlpha + threadIdx.x;
+  if (e >= Ne) return;
+  // modes along x, row by row, then along y
+  double t[n][n];
+#pragma unroll
+  for (int q = 0; q < n; ++q) {
+    double x[n];
+#pragma unroll
+    for (int p = 0; p < n; ++p) x[p] = h[e * nn + q * n + p];
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      double s = T.Vinv[j][0] * x[0];
+#pragma unroll
+      for (int p = 1; p < n; ++p) s = fma(T.Vinv[j][p], x[p], s);
+      t[q][j] = s;
+    }
+  }
+  double tot = 0.0, clip1 = 0.0, clip2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      double m = T.Vinv[i][0] * t[0][j];
+#pragma unroll
+      for (int q = 1; q < n; ++q) m = fma(T.Vinv[i][q], t[q][j], m);
+      const double m2 = m * m;
+      tot += m2;
+      if (i < N && j < N) clip1 += m2;
+      if (i < N - 1 && j < N - 1) clip2 += m2;
+    }
+  double energy = tot > 0.0 ? (tot - clip1) / tot : 0.0;
+  if (N >= 2) {
+    const double e2 = clip1 > 0.0 ? (clip1 - clip2) / clip1 : 0.0;
+    energy = fmax(energy, e2);
+  }
+  double a = 1.0 / (1.0 + exp(-T.ind_sharp * (energy - T.ind_T)));
+  if (a < 1e-3) a = 0.0;
+  if (a > 1.0 - 1e-3) a = 1.0;
+  alpha_raw[e] = a;
+}
+
+// mode 1: smoothing of the indicator over the four face neighbours
+// (periodic mesh); mode 2: the fixed coefficient everywhere
+__global__ void __launch_bounds__(kBlockAlpha) k_alpha_smooth_2d(int64_t Ex, int64_t Ey, int mode,
+                                                                 double fixed,
+                                                                 const double* __restrict__ raw,
+                                                                 double* __restrict__ alpha) {
+  const int64_t e = (int64_t)blockIdx.x * kBlockAlpha + threadIdx.x;
+  if (e >= Ex * Ey) return;
+  if (mode == CRKFR_LIMITER_FIXED) {
+    alpha[e] = fixed;
+    return;
+  }
+  const int64_t ey = e / Ex, ex = e - ey * Ex;
+  const int64_t yl = (ey == 0 ? Ey - 1 : ey - 1) * Ex, yu = (ey == Ey - 1 ? 0 : ey + 1) * Ex;
+  const int64_t xl = ex == 0 ? Ex - 1 : ex - 1, xr = ex == Ex - 1 ? 0 : ex + 1;
+  const double nb = fmax(fmax(raw[yl + ex], raw[yu + ex]), fmax(raw[ey * Ex + xl], raw[ey * Ex + xr]));
+  alpha[e] = fmax(raw[e], 0.5 * nb);
+}
+
+}  // namespace
+
+int launch_local_2d_limit(const Launch2D& L, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (L.wb) return launch_local_2d_limit_wb(L, stream);
+  return L.imex ? launch_local_dispatch<true, false, true>(L, s)
+                : launch_local_dispatch<false, false, true>(L, s);
+}
+
+int launch_face_2d_limit(const Launch2D& L, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (L.wb) return launch_face_2d_limit_wb(L, stream);
+  return L.imex ? launch_face_dispatch<false, true, true>(L, s)
+                : launch_face_dispatch<false, true, false>(L, s);
+}
+
+int launch_alpha_2d(const Launch2D& L, double* alpha_raw, double* alpha, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t Ne = L.Ex * L.Ey;
+  const unsigned blocks = (unsigned)((Ne + kBlockAlpha - 1) / kBlockAlpha);
+  if (L.lim.mode == CRKFR_LIMITER_BLEND) {
+    switch (L.N) {
+      case 1: k_alpha_2d<1><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+      case 2: k_alpha_2d<2><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+      case 3: k_alpha_2d<3><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+      case 4: k_alpha_2d<4><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
+    const int e = (int)cudaGetLastError();
+    if (e) return e;
+  }
+  k_alpha_smooth_2d<<<blocks, kBlockAlpha, 0, s>>>(L.Ex, L.Ey, L.lim.mode, L.lim.alpha_fixed,
+                                                   alpha_raw, alpha);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace crkfr

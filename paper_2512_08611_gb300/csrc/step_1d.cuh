@@ -118,14 +118,6 @@ __device__ __forceinline__ void lo_flux(const double* uL, const double* uR, doub
   }
 }
 
-// Weight of the candidate b in theta b + (1 - theta) a for the linear
-// constraint P (Eq. theta.formula): 1 unless P(b) < eps.
-__device__ __forceinline__ double theta_lin(double eps, double Pa, double Pb) {
-  if (!(Pb < eps)) return 1.0;
-  const double den = Pb - Pa;
-  return den != 0.0 ? fmin(1.0, fabs((eps - Pa) / den)) : 1.0;
-}
-
 // Point-implicit backward-Euler source step of the low-order update
 // (Eq. low.order.update): u - dt s(u) = r, in closed form.
 template <int SYS>

@@ -161,11 +161,6 @@ def test_well_balanced_lake_at_rest_with_limiter(crk):
 
 
 def test_limiter_configuration_errors(crk):
-    s2 = crk.Solver("swe2d", 2, gravity=G)
-    s2.set_mesh([4, 4], [0.0, 0.0], [1.0, 1.0])
-    with pytest.raises(crk.CrkfrError) as e:
-        s2.set_limiter("blend")
-    assert e.value.status == -2
     s0 = crk.Solver("swe1d", 0, gravity=G)
     s0.set_mesh([8], [0.0], [1.0])
     with pytest.raises(crk.CrkfrError) as e:
