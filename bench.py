@@ -1,7 +1,8 @@
 """Benchmark of the cRK-FR hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload swe2d|swe1d|swe1d-limited|swe2d-friction|swe2d-wb|ensemble|adjoint]
+                    [--workload swe2d|swe1d|swe1d-limited|swe2d-limited|swe2d-friction|
+                                swe2d-wb|ensemble|adjoint]
 
 A step is one cRK-FR time step (element-local inner stages, time averages,
 face Riemann problems with non-conservative fluctuations, FR corrections,
@@ -61,12 +62,14 @@ class Workload:
         self.name = name
         self.source, self.source_coef, self.current = None, 0.0, (0.0, 0.0)
         self.limiter = None
-        if name in ("swe2d", "swe2d-friction", "swe2d-wb"):
+        if name in ("swe2d", "swe2d-friction", "swe2d-wb", "swe2d-limited"):
             side = mesh or 1024
             self.system, self.N, self.E, self.L = "swe2d", 3, (side, side), 100.0
             self.M, self.dim = 3, 2
             if name == "swe2d-wb":
                 self.system = "swe2d_wb"
+            if name == "swe2d-limited":
+                self.limiter = "blend"
             if name == "swe2d-friction":
                 self.source, self.source_coef, self.current = "chezy", 0.0025, (0.3, 0.2)
         elif name in ("swe1d", "swe1d-limited"):
@@ -113,9 +116,14 @@ class Workload:
 
     def local_flops_per_element(self):
         """FP64 flops (FMA = 2) of the element-local kernel per element, from
-        the operation count of its formulation (paper_2512_08611_gb300.flops)."""
-        from paper_2512_08611_gb300.flops import local_flops_per_element
-        return local_flops_per_element(self.system, self.N, imex=self.source is not None)
+        the operation count of its formulation (paper_2512_08611_gb300.flops);
+        the 2D limited kernel adds its first-order part."""
+        from paper_2512_08611_gb300.flops import (limiter_local_flops_per_element,
+                                                  local_flops_per_element)
+        f = local_flops_per_element(self.system, self.N, imex=self.source is not None)
+        if self.limiter and self.dim == 2:
+            f += limiter_local_flops_per_element(self.system, self.N)
+        return f
 
 
 # ---------------------------------------------------------------------------
@@ -201,8 +209,11 @@ def profiled_traffic(summary, files, scale):
 # CPU oracle timing on a bounded periodic patch of the workload
 # ---------------------------------------------------------------------------
 def oracle_patch(wl, side):
+    """(scheme, stepper, u, b, dof): the stepper is the scheme, or its
+    blending limiter for a limited workload."""
     from oracle.basis import Basis
     from oracle.crkfr import Scheme1D, Scheme2D
+    from oracle.limiter import Blending1D, Blending2D
     bs = Basis(wl.N)
     if wl.dim == 2:
         dx = wl.L / wl.E[0]
@@ -218,7 +229,10 @@ def oracle_patch(wl, side):
         u, b = wl.inputs((x,))
         sch = Scheme1D(wl.oracle_system(), wl.N, dx)
         dof = side * wl.nodes_per_elem * wl.M
-    return sch, u, b, dof
+    stepper = sch
+    if wl.limiter:
+        stepper = (Blending2D if wl.dim == 2 else Blending1D)(sch)
+    return sch, stepper, u, b, dof
 
 
 def time_oracle(wl, budget_s, max_steps):
@@ -226,16 +240,16 @@ def time_oracle(wl, budget_s, max_steps):
     work), sized so that max_steps steps take about budget_s seconds."""
     import oracle.fourier  # noqa: F401  (imports numpy-only modules)
     probe = 32 if wl.dim == 2 else 4096
-    sch, u, b, dof = oracle_patch(wl, probe)
+    sch, stepper, u, b, dof = oracle_patch(wl, probe)
     t0 = time.perf_counter()
-    sch.step(u, b, 1e-4)
+    stepper.step(u, b, 1e-4)
     per_dof = (time.perf_counter() - t0) / dof
     target = budget_s / max(max_steps, 1) / per_dof
     if wl.dim == 2:
         side = int(np.clip(np.sqrt(target / (wl.nodes_per_elem * wl.M)) // 8 * 8, 16, wl.E[0]))
     else:
         side = int(np.clip(target / (wl.nodes_per_elem * wl.M) // 128 * 128, 512, wl.E[0]))
-    sch, u, b, dof = oracle_patch(wl, side)
+    sch, stepper, u, b, dof = oracle_patch(wl, side)
     return sch, u, b, dof, side
 
 
@@ -250,13 +264,13 @@ def _oracle_worker(job):
     the patch (single-threaded numpy)."""
     name, mesh, side, steps, warmup, cfl = job
     wl = Workload(name, mesh)
-    sch, u, b, dof = oracle_patch(wl, side)
+    sch, stepper, u, b, dof = oracle_patch(wl, side)
     v = u
     for _ in range(warmup):
-        v = sch.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
+        v = stepper.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
     t0 = time.perf_counter()
     for _ in range(steps):
-        v = sch.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
+        v = stepper.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
     return dof, time.perf_counter() - t0
 
 
@@ -432,8 +446,11 @@ def run_ours(args, wl):
     hbm_peak = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
     if wl.dim == 2:
         kname, files = "local_2d", ["local_2d.cuh", "device_common.cuh", "tableau.h"]
+        if wl.limiter:
+            files = files + ["limit_2d.cuh"]
         summary = ("k_local_2d__swe2d_friction_N3.md" if wl.source else
                    "k_local_2d__swe2d_wb_N3.md" if wl.system == "swe2d_wb" else
+                   "k_local_2d__swe2d_N3_limited.md" if wl.limiter else
                    "k_local_2d__swe2d_N3.md")
     else:
         kname, files = "step_1d", ["step_1d.cuh", "device_common.cuh", "tableau.h"]
@@ -463,7 +480,10 @@ def run_ours(args, wl):
                      "flops_per_launch": flops,
                      "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
                      **({"flops_note": "the unlimited step's operation count: a lower bound "
-                                       "of the limited kernel's work"} if wl.limiter else {})},
+                                       "of the limited kernel's work"}
+                        if wl.limiter and wl.dim == 1 else
+                        {"flops_note": "the unlimited step's count plus the first-order part "
+                                       "of the limiter"} if wl.limiter else {})},
         "hbm": {"min_bytes_per_step": wl.min_bytes,
                 "achieved_gbs": wl.min_bytes / (ms_per_step / 1e3) / 1e9,
                 "peak_gbs": hbm_peak,
@@ -677,7 +697,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="swe2d",
-                    choices=["swe2d", "swe1d", "swe1d-limited", "swe2d-friction", "swe2d-wb",
+                    choices=["swe2d", "swe1d", "swe1d-limited", "swe2d-limited", "swe2d-friction",
+                             "swe2d-wb",
                              "ensemble", "adjoint"])
     ap.add_argument("--mesh", type=int, default=None,
                     help="elements per side (2D) or elements (1D); profiling of small cases")

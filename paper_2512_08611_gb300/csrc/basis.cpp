@@ -208,6 +208,7 @@ void fill_tables(const HostBasis& b, double dx, double dy, double gravity, bool 
     T->gRy[i] = dy > 0.0 ? 0.5 * b.gR[i] / dy : 0.0;
     T->gLy[i] = dy > 0.0 ? 0.5 * b.gL[i] / dy : 0.0;
     T->w[i] = b.w[i];
+    T->inv_w[i] = 1.0 / b.w[i];
   }
   T->inv_dx = 1.0 / dx;
   T->inv_dy = dy > 0.0 ? 1.0 / dy : 0.0;

@@ -34,6 +34,7 @@ struct Tables {
   double gRy[kMaxNodes];            // 0.5 g_R'(xi_p) / dy
   double gLy[kMaxNodes];            // 0.5 g_L'(xi_p) / dy
   double w[kMaxNodes];              // quadrature weights
+  double inv_w[kMaxNodes];          // 1 / w_p
   double inv_dx, inv_dy;
   double gravity, half_gravity;
   // The kernels accumulate time averages with the weights b_i / b_ref, b_ref

@@ -99,7 +99,7 @@ __device__ __forceinline__ void face_limited(const double* tm, const double* tp,
   FTp[nv] += g * tp[5] * Wp;
   // first-order face fluxes and Eq. Fblend
   double fLm[3], fLp[3];
-  lo_flux_2d<DIR, WB>(lm, lp, lm[3], lp[3], T, fLm, fLp);
+  lo_flux_2d<DIR, WB>(lm, lp, lm[3], lp[3], g, fLm, fLp);
   const double b0 = T.b0;
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
         }
         const double af = 0.5 * (L.lim.alpha[em] + L.lim.alpha[ep]);
         const double c2 = 2.0 * dtp * T.inv_dx;
-        face_limited<0, WB>(a, b, lm, lp, af, c2 / T.w[N], c2 / T.w[0], T, Tm, Tp, Fm, Fp);
+        face_limited<0, WB>(a, b, lm, lp, af, c2 * T.inv_w[N], c2 * T.inv_w[0], T, Tm, Tp, Fm, Fp);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           fxm[r][k][q][v] = Fm[v];
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
         const int64_t eym = (ey0 + k - 1 + Ey) % Ey, eyp = (ey0 + k) % Ey;
         const double af = 0.5 * (L.lim.alpha[eym * Ex + ex] + L.lim.alpha[eyp * Ex + ex]);
         const double c2 = 2.0 * dtp * T.inv_dy;
-        face_limited<1, WB>(a, b, lm, lp, af, c2 / T.w[N], c2 / T.w[0], T, Tm, Tp, Fm, Fp);
+        face_limited<1, WB>(a, b, lm, lp, af, c2 * T.inv_w[N], c2 * T.inv_w[0], T, Tm, Tp, Fm, Fp);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           fym[k][c][p][v] = Fm[v];
@@ -278,8 +278,8 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
     // first-order subcell update: the local kernel's part plus the
     // element-face fluxes of the face nodes (Eq. low.order.update), the
     // source point-implicitly; Eq. blended.scheme; Algorithm 2 (h > 0)
-    const double ax0 = dtp * T.inv_dx / T.w[0], axN = dtp * T.inv_dx / T.w[N];
-    const double ay0 = dtp * T.inv_dy / T.w[0], ayN = dtp * T.inv_dy / T.w[N];
+    const double ax0 = dtp * T.inv_dx * T.inv_w[0], axN = dtp * T.inv_dx * T.inv_w[N];
+    const double ay0 = dtp * T.inv_dy * T.inv_w[0], ayN = dtp * T.inv_dy * T.inv_w[N];
     const double alpha = L.lim.alpha[ge];
     double lo[3][n];
 #pragma unroll

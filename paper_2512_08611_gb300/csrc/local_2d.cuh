@@ -17,16 +17,13 @@
 // chain, D_y h reads the other rows of h through shared memory.
 //
 // With the subcell blending limiter (LIMIT; the tensor-product extension of
-// Sec. 4) the kernel also writes the first-order subcell update of every
-// node without its element-face terms, and for every face node the data the
-// face kernel needs for the first-order face flux and Algorithm 1: the nodal
-// state and coefficient next to the face, the first-order flux of the inner
-// subface next to it, and the trace of the coefficient.
+// Sec. 4) the kernel ends with the first-order part of limit_2d.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
+#include "limit_2d.cuh"
 
 namespace crkfr {
 namespace {
@@ -43,39 +40,9 @@ namespace {
 constexpr int kBlockLocal = CRKFR_LOCAL2D_BLOCK;
 constexpr int kWarpsLocal = kBlockLocal / 32;
 constexpr int kTrFields = 7;
-constexpr int kLimFields = 8;   // limiter face data: u (3), c, inner flux (3), trace of c
 // x-face trace fields: U_h, U_hu, U_hv, F_hu, F_hv (time-averaged x fluxes of
 // hu and hv), h^n, hu^n.  y-face trace fields: U_h, U_hu, U_hv, G_hu, G_hv,
 // h^n, hv^n.  (The time-averaged h fluxes are U_hu and U_hv.)
-
-// First-order non-conservative Rusanov fluxes (Eq. combined.num.flux) in
-// direction DIR (0: x, 1: y) between the nodal states L and R:
-// fm = f^num + B(w_L) w^num, fp = f^num + B(w_R) w^num; the jump of h, or of
-// eta = h + b in the well-balanced form, is dissipated.
-template <int DIR, bool WB>
-__device__ __forceinline__ void lo_flux_2d(const double* uL, const double* uR, double cL, double cR,
-                                           const Tables& T, double* fm, double* fp) {
-  constexpr int nv = 1 + DIR, nt = 2 - DIR;
-  const double g = T.gravity;
-  const double hL = uL[0], hR = uR[0];
-  const double lam = max_nonneg(swe_speed(hL, uL[nv], g), swe_speed(hR, uR[nv], g));
-  const double vL = uL[nv] * drcp(hL), vR = uR[nv] * drcp(hR);
-  const double fnL = WB ? uL[nv] * vL : fma(0.5 * g * hL, hL, uL[nv] * vL);
-  const double fnR = WB ? uR[nv] * vR : fma(0.5 * g * hR, hR, uR[nv] * vR);
-  const double jh = WB ? (hR + cR) - (hL + cL) : hR - hL;
-  double f[3];
-  f[0] = fma(-0.5 * lam, jh, 0.5 * (uL[nv] + uR[nv]));
-  f[nv] = fma(-0.5 * lam, uR[nv] - uL[nv], 0.5 * (fnL + fnR));
-  f[nt] = fma(-0.5 * lam, uR[nt] - uL[nt], 0.5 * (uL[nt] * vL + uR[nt] * vR));
-  const double wn = WB ? 0.5 * (hL + hR) + 0.5 * (cL + cR) : 0.5 * (cL + cR);
-#pragma unroll
-  for (int v = 0; v < 3; ++v) {
-    fm[v] = f[v];
-    fp[v] = f[v];
-  }
-  fm[nv] = f[nv] + g * hL * wn;
-  fp[nv] = f[nv] + g * hR * wn;
-}
 
 template <int N, bool GLL, bool RES, bool IMEX, bool WB, bool LIMIT = false>
 __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(const Launch2D L) {
@@ -87,7 +54,8 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
   constexpr int F0 = TB::first();
   constexpr int NB = 4;                // fields per shared-memory exchange round
   const Tables& T = L.tab;
-  __shared__ double sm[kWarpsLocal][EPW][NB][n][n];
+  // (the limiter's first-order part exchanges kLimRowFields fields at once)
+  __shared__ double sm[kWarpsLocal][EPW][LIMIT ? kLimRowFields : NB][n][n];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int le = lane / n, q = lane - le * n;
@@ -274,167 +242,6 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
 
   const int64_t tstride = Ne * n;  // one (field, side) plane of a trace array
 
-  // ---- limiter: first-order subcell update without the element-face terms,
-  //      and the face data of the first-order face fluxes -----------------------
-  if constexpr (LIMIT) {
-    static_assert(!RES, "the limiter needs a step");
-    double cn[n];
-#pragma unroll
-    for (int p = 0; p < n; ++p) cn[p] = L.lim.cnode[ge * nn + q * n + p];
-    // x: inner subfaces of row q
-    double fxm[3][N], fxp[3][N];
-#pragma unroll
-    for (int p = 0; p < N; ++p) {
-      double a[3], b[3], fm_[3], fp_[3];
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        a[v] = u0[v][p];
-        b[v] = u0[v][p + 1];
-      }
-      lo_flux_2d<0, WB>(a, b, cn[p], cn[p + 1], T, fm_, fp_);
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        fxm[v][p] = fm_[v];
-        fxp[v][p] = fp_[v];
-      }
-    }
-    // y: the element's rows through shared memory (round A: u and c rows)
-    __syncwarp();
-    if (lane_ok) {
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-        X[0][q][p] = u0[0][p];
-        X[1][q][p] = u0[1][p];
-        X[2][q][p] = u0[2][p];
-        X[3][q][p] = cn[p];
-      }
-    }
-    __syncwarp();
-    double fym[3][n], fyp[3][n];   // subface between rows q and q+1, column p
-    if (q < N) {
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-        double a[3], b[3], fm_[3], fp_[3];
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          a[v] = X[v][q][p];
-          b[v] = X[v][q + 1][p];
-        }
-        lo_flux_2d<1, WB>(a, b, X[3][q][p], X[3][q + 1][p], T, fm_, fp_);
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          fym[v][p] = fm_[v];
-          fyp[v][p] = fp_[v];
-        }
-      }
-    }
-    // column q of the element: nodal state and c at its bottom and top nodes,
-    // traces of c at the bottom and top faces
-    double uB[3], uT[3];
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      uB[v] = X[v][0][q];
-      uT[v] = X[v][N][q];
-    }
-    const double cB = X[3][0][q], cT = X[3][N][q];
-    double ctrB, ctrT;
-    if (GLL) {
-      ctrB = cB;
-      ctrT = cT;
-    } else {
-      ctrB = T.l0[0] * X[3][0][q];
-      ctrT = T.l1[0] * X[3][0][q];
-#pragma unroll
-      for (int j = 1; j < n; ++j) {
-        ctrB = fma(T.l0[j], X[3][j][q], ctrB);
-        ctrT = fma(T.l1[j], X[3][j][q], ctrT);
-      }
-    }
-    // round B: the plus-side flux of each inner y-subface to the row above
-    __syncwarp();
-    if (lane_ok && q < N) {
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-        X[0][q][p] = fyp[0][p];
-        X[1][q][p] = fyp[1][p];
-        X[2][q][p] = fyp[2][p];
-      }
-    }
-    __syncwarp();
-    double fyl[3][n];   // subface between rows q-1 and q, seen by row q
-    double fTin[3];     // column q: left flux of the top node (rows N-1 | N)
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-#pragma unroll
-      for (int p = 0; p < n; ++p) fyl[v][p] = q > 0 ? X[v][q > 0 ? q - 1 : 0][p] : 0.0;
-      fTin[v] = X[v][N - 1][q];
-    }
-    // round C: the minus-side flux of the bottom inner subface, by column
-    __syncwarp();
-    if (lane_ok && q == 0) {
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-        X[0][0][p] = fym[0][p];
-        X[1][0][p] = fym[1][p];
-        X[2][0][p] = fym[2][p];
-      }
-    }
-    __syncwarp();
-    double fBin[3];     // column q: right flux of the bottom node (rows 0 | 1)
-#pragma unroll
-    for (int v = 0; v < 3; ++v) fBin[v] = X[v][0][q];
-
-    if (active) {
-      // first-order update of row q without the element-face terms
-#pragma unroll
-      for (int v = 0; v < 3; ++v)
-#pragma unroll
-        for (int p = 0; p < n; ++p) {
-          const double xd = (p < N ? fxm[v][p < N ? p : 0] : 0.0) - (p > 0 ? fxp[v][p > 0 ? p - 1 : 0] : 0.0);
-          const double yd = (q < N ? fym[v][p] : 0.0) - (q > 0 ? fyl[v][p] : 0.0);
-          L.lim.ulo[(v * Ne + ge) * nn + q * n + p] =
-              u0[v][p] - (dt * T.inv_dx / T.w[p]) * xd - (dt * T.inv_dy / T.w[q]) * yd;
-        }
-      // x-face data of row q: left side (node 0), right side (node N)
-      double ctrL, ctrR;
-      if (GLL) {
-        ctrL = cn[0];
-        ctrR = cn[N];
-      } else {
-        ctrL = T.l0[0] * cn[0];
-        ctrR = T.l1[0] * cn[0];
-#pragma unroll
-        for (int p = 1; p < n; ++p) {
-          ctrL = fma(T.l0[p], cn[p], ctrL);
-          ctrR = fma(T.l1[p], cn[p], ctrR);
-        }
-      }
-      const double lx0[kLimFields] = {u0[0][0], u0[1][0], u0[2][0], cn[0],
-                                      fxm[0][0], fxm[1][0], fxm[2][0], ctrL};
-      const double lx1[kLimFields] = {u0[0][N], u0[1][N], u0[2][N], cn[N],
-                                      fxp[0][N - 1], fxp[1][N - 1], fxp[2][N - 1], ctrR};
-#pragma unroll
-      for (int f = 0; f < kLimFields; ++f) {
-        L.lim.lx[(2 * f + 0) * tstride + ge * n + q] = lx0[f];
-        L.lim.lx[(2 * f + 1) * tstride + ge * n + q] = lx1[f];
-      }
-      // y-face data of column q: bottom side (row 0), top side (row N)
-      const double ly0[kLimFields] = {uB[0], uB[1], uB[2], cB, fBin[0], fBin[1], fBin[2], ctrB};
-      const double ly1[kLimFields] = {uT[0], uT[1], uT[2], cT, fTin[0], fTin[1], fTin[2], ctrT};
-      const int64_t row = ge / L.Ex + 1, col = ge - (row - 1) * L.Ex;
-      const int64_t plane = L.Ex * n;
-#pragma unroll
-      for (int f = 0; f < kLimFields; ++f) {
-        L.lim.ly[((row * 2 + 0) * kLimFields + f) * plane + col * n + q] = ly0[f];
-        L.lim.ly[((row * 2 + 1) * kLimFields + f) * plane + col * n + q] = ly1[f];
-        if (L.periodic_y && row == 1)
-          L.lim.ly[(((L.Ey + 1) * 2 + 0) * kLimFields + f) * plane + col * n + q] = ly0[f];
-        if (L.periodic_y && row == L.Ey)
-          L.lim.ly[((0 * 2 + 1) * kLimFields + f) * plane + col * n + q] = ly1[f];
-      }
-    }
-  }
-
   // ---- x-face traces of row q -------------------------------------------------
   // field f of the x-face traces at node p of this row (f, p constant after unrolling)
   auto fx = [&](int f, int p) -> double {
@@ -522,6 +329,12 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
         }
       }
     }
+  }
+  // ---- limiter: first-order update without the element-face terms and the
+  //      face data of the first-order face fluxes (limit_2d.cuh) -------------
+  if constexpr (LIMIT) {
+    static_assert(!RES, "the limiter needs a step");
+    limit_local_2d<N, GLL, WB>(L, u0, X, q, lane_ok, active, ge, dt);
   }
 }
 

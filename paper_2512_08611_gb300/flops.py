@@ -32,6 +32,17 @@ whose operator is used (their 1/h shared with the solve: 2 FMA + 5 MUL);
 time averages 11 FMA (with the two source averages) on weighted stages
 after the first; W 5 FMA per node.
 
+First-order part of the 2D subcell blending limiter in the element-local
+kernel (limited=True; per element, GL nodes): per node the parts of both
+directions (1/h 3 FMA; sqrt(g h): 1 MUL + the 5-instruction root, 3 FMA +
+2 MUL; v_x, v_y 2 MUL; the two spectral radii 2 ADD; the normal fluxes
+with pressure 3 MUL + 2 FMA (well-balanced: 2 MUL); the tangential fluxes
+2 MUL); per inner subface (2 N n of them) the Rusanov flux from those parts
+(3 FMA + 4 MUL + 6 ADD; well-balanced: the jump and mean of eta, 3 ADD
+more) and the two fluctuations (4 MUL + 3 ADD); per node and variable the
+first-order update without the face terms (2 ADD + 2 FMA) plus 1 MUL per
+node; the traces of c at the four faces (4 n (1 MUL + (n - 1) FMA)).
+
 Well-balanced 2D form (system swe2d_wb): the fluxes lose the pressure
 (3 FMA + 5 MUL: 1/h, u, v, and the three products), the local operator gains
 D_x h and D_y h (2 MUL + 2 (n - 1) FMA) and g h_x + g b_x, g h_y + g b_y
@@ -81,6 +92,20 @@ def _swe2d_wb(N):
     per_node = 2 * fma + mul
     traces = 2 * n * 7 * 2 * (1 + 2 * (n - 1))
     return per_node * n * n + traces
+
+
+def limiter_local_flops_per_element(system, N, gll=False):
+    """Flops the first-order part of the 2D limiter adds to the element-local
+    kernel (counts in the module docstring)."""
+    if system not in ("swe2d", "swe2d_wb"):
+        raise ValueError("the limiter's local count is written out for 2D shallow water")
+    n = N + 1
+    wb = system == "swe2d_wb"
+    node = 2 * (3 + 3 + (0 if wb else 2)) + (1 + 2 + 2 + (2 if wb else 3) + 2) + 2
+    sub = 2 * 3 + 4 + 6 + (3 if wb else 0) + 4 + 3
+    update = 3 * (2 + 2 * 2) + 1
+    ctr = 0 if gll else 4 * n * (1 + 2 * (n - 1))
+    return n * n * (node + update) + 2 * N * n * sub + ctr
 
 
 def local_flops_per_element(system, N, imex=False):
