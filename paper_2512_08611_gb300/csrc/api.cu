@@ -16,6 +16,10 @@
 
 using namespace crkfr;
 
+// row chunks of the last face kernel of crkfr_step_host (2D), each read back
+// to the host as soon as it is final
+constexpr int kHostChunks = 8;
+
 struct crkfr_ctx {
   crkfr_config cfg{};
   HostBasis basis;
@@ -44,6 +48,11 @@ struct crkfr_ctx {
   double* d_ly = nullptr;
   int limit_mode = CRKFR_LIMITER_NONE;
   double alpha_fixed = 0.0;
+  // crkfr_step_host: a copy stream and events to read finished rows of the
+  // last step back while the face kernel updates the next rows
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_rows[kHostChunks] = {};
+  cudaEvent_t ev_copied = nullptr;
   DevState* d_state = nullptr;
   bool coef_set = false;
   bool subdomain = false;   // 2D slab of a larger mesh: halo rows come from outside
@@ -216,6 +225,8 @@ Launch2D make2d(crkfr_ctx* c) {
   L.st = c->d_state;
   L.tab = c->tab;
   L.periodic_y = c->subdomain ? 0 : 1;
+  L.row_begin = 0;
+  L.row_end = c->Ey;
   return L;
 }
 
@@ -244,9 +255,50 @@ crkfr_status launch_rate(crkfr_ctx* c, const double* u, int slot, cudaStream_t s
   return CRKFR_OK;
 }
 
+// The face kernel of a 2D step in up to kHostChunks chunks of element rows,
+// each chunk's rows of u (contiguous per variable) copied to host_out on the
+// copy stream once the chunk's face kernel has finished; the stream s then
+// waits for the last copy.
+crkfr_status faces_with_readback(crkfr_ctx* c, Launch2D L, const double* u, double* host_out,
+                                 cudaStream_t s) {
+  if (!c->copy_stream) {
+    CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (auto& ev : c->ev_rows) CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(c, cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+  }
+  const int64_t Ey = c->Ey, Ne = c->Ex * c->Ey;
+  const int64_t nn = (int64_t)c->basis.n * c->basis.n;
+  int64_t rows = (Ey + kHostChunks - 1) / kHostChunks;
+  rows = (rows + 7) / 8 * 8;
+  int k = 0;
+  for (int64_t r0 = 0; r0 < Ey; r0 += rows, ++k) {
+    const int64_t r1 = r0 + rows < Ey ? r0 + rows : Ey;
+    L.row_begin = r0;
+    L.row_end = r1;
+    int e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+    if (e) return cuda_fail(c, e, "2D face kernel");
+    c->launches += 1;
+    CK(c, cudaEventRecord(c->ev_rows[k], s));
+    CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_rows[k], 0));
+    const size_t off = (size_t)(r0 * c->Ex) * nn;
+    const size_t bytes = sizeof(double) * (size_t)((r1 - r0) * c->Ex) * nn;
+    for (int v = 0; v < 3; ++v)
+      CK(c, cudaMemcpyAsync(host_out + v * Ne * nn + off, u + v * Ne * nn + off, bytes,
+                            cudaMemcpyDeviceToHost, c->copy_stream));
+  }
+  CK(c, cudaEventRecord(c->ev_copied, c->copy_stream));
+  CK(c, cudaStreamWaitEvent(s, c->ev_copied, 0));
+  return CRKFR_OK;
+}
+
 // nsteps steps of u in place.  dt > 0 fixed, otherwise CFL (clipped to t_end).
+// host_out (2D, optional): the last step's face kernel runs in row chunks and
+// each chunk's rows are copied to host_out on the context's copy stream as
+// soon as they are final; the caller's stream waits for the copies.
+// *copied tells whether that happened.
 crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, double t_end,
-                       cudaStream_t s) {
+                       cudaStream_t s, double* host_out = nullptr, bool* copied = nullptr) {
+  if (copied) *copied = false;
   if (nsteps <= 0) return CRKFR_OK;
   const bool cfl_mode = !(dt > 0.0);
   if (cfl_mode) {
@@ -315,9 +367,17 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
         c->launches += c->limit_mode == CRKFR_LIMITER_BLEND ? 2 : 1;
       }
       int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
-      if (!e) e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
-      if (e) return cuda_fail(c, e, "2D step kernels");
-      c->launches += 2;
+      if (e) return cuda_fail(c, e, "2D local kernel");
+      c->launches += 1;
+      if (host_out && k == nsteps - 1) {
+        crkfr_status st = faces_with_readback(c, L, u, host_out, s);
+        if (st != CRKFR_OK) return st;
+        if (copied) *copied = true;
+      } else {
+        e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+        if (e) return cuda_fail(c, e, "2D face kernel");
+        c->launches += 1;
+      }
       c->nstep += 1;
     }
   }
@@ -404,6 +464,11 @@ void crkfr_destroy(crkfr_ctx* c) {
       cudaEventDestroy(r.b);
     }
     for (auto e : c->pool) cudaEventDestroy(e);
+    if (c->copy_stream) {
+      cudaStreamDestroy(c->copy_stream);
+      for (auto ev : c->ev_rows) cudaEventDestroy(ev);
+      cudaEventDestroy(c->ev_copied);
+    }
     if (prev != c->device && prev >= 0) cudaSetDevice(prev);
   }
   delete c;
@@ -690,9 +755,16 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
     }
   }
   CK(c, cudaMemcpyAsync(c->d_stage, u_in, bytes, cudaMemcpyHostToDevice, s));
-  st = run_steps(c, c->d_stage, dt, nsteps, std::numeric_limits<double>::infinity(), s);
-  if (st != CRKFR_OK) return st;
-  CK(c, cudaMemcpyAsync(u_out, c->d_stage, bytes, cudaMemcpyDeviceToHost, s));
+  // 2D: the last step's rows are read back while the face kernel finishes
+  // the rows after them
+  bool copied = false;
+  st = run_steps(c, c->d_stage, dt, nsteps, std::numeric_limits<double>::infinity(), s,
+                 c->dim == 2 ? u_out : nullptr, &copied);
+  if (st != CRKFR_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  if (!copied) CK(c, cudaMemcpyAsync(u_out, c->d_stage, bytes, cudaMemcpyDeviceToHost, s));
   CK(c, cudaStreamSynchronize(s));
   return CRKFR_OK;
 }

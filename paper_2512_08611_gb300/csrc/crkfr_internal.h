@@ -203,6 +203,9 @@ struct Launch2D {
   Tables tab;
   StepCtl ctl;
   LimitArgs2D lim;       // mode 0: no limiter
+  // element rows [row_begin, row_end) the face kernel updates (row_begin a
+  // multiple of 8, row_end a multiple of 8 or Ey): the whole mesh by default
+  int64_t row_begin, row_end;
 };
 // Adjoint of one 2D step (kernels_adj2d.cu); the forward local kernel must
 // have written the traces of u^n first.

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
   __shared__ double fym[LY + 1][LX][n][3], fyp[LY + 1][LX][n][3];
 
   const int64_t Ex = L.Ex, Ey = L.Ey, Ne = Ex * Ey, ts = Ne * n;
-  const int64_t ex0 = (int64_t)blockIdx.x * TX, ey0 = (int64_t)blockIdx.y * TY;
+  const int64_t ex0 = (int64_t)blockIdx.x * TX, ey0 = L.row_begin + (int64_t)blockIdx.y * TY;
   // the traces hold time averages divided by b_0: so do the face terms
   const double dtp = RES ? 1.0 : L.st->dt_cur;
   const double dt = dtp * T.b0;
@@ -384,7 +384,11 @@ template <int N, bool GLL, bool WB, bool LIMIT = false, bool IMEX = false>
 int launch_face_t(const Launch2D& L, cudaStream_t s) {
   constexpr int TX = 32 / (N + 1);
   constexpr int TY = FaceShape<N, LIMIT>::TY, BT = FaceShape<N, LIMIT>::block;
-  const dim3 grid((unsigned)((L.Ex + TX - 1) / TX), (unsigned)((L.Ey + TY - 1) / TY));
+  const dim3 grid((unsigned)((L.Ex + TX - 1) / TX),
+                  (unsigned)((L.row_end - L.row_begin + TY - 1) / TY));
+  if (L.row_begin % 8 != 0 || L.row_end <= L.row_begin || L.row_end > L.Ey ||
+      (L.row_end % 8 != 0 && L.row_end != L.Ey))
+    return (int)cudaErrorInvalidValue;
   if (grid.y > 65535u) return (int)cudaErrorInvalidConfiguration;
   if constexpr (LIMIT)
     k_face_2d<N, GLL, false, WB, true, IMEX><<<grid, BT, 0, s>>>(L);

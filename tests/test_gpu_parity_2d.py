@@ -159,3 +159,30 @@ def test_checkpoint_resume_repeats_the_run():
     s2.step(d2, 0.0, 5)
     assert np.array_equal(to_host(d1), to_host(d2))
     assert s1.time()[0] == s2.time()[0]
+
+
+@pytest.mark.parametrize("Ex,Ey", [(5, 3), (7, 8), (6, 37), (3, 70)])
+@pytest.mark.parametrize("limited", [False, True])
+def test_host_step_reads_rows_back_in_chunks(crk, Ex, Ey, limited):
+    """crkfr_step_host runs the last face kernel in chunks of element rows and
+    copies each chunk back while the next one computes: the result is the
+    device step's, bit for bit (CFL steps, one and three per call, with and
+    without the limiter), from pinned and from ordinary host memory."""
+    import torch
+    N = 3
+    u, b, dx, dy = swe2d_case(N, "gl", Ex, Ey)
+    for nsteps in (1, 3):
+        s1 = solver(crk, N, "gl", Ex, Ey, b)
+        s2 = solver(crk, N, "gl", Ex, Ey, b)
+        if limited:
+            s1.set_limiter("blend")
+            s2.set_limiter("blend")
+        du = to_dev(u)
+        s1.step(du, 0.0, nsteps)
+        pinned = torch.tensor(u).pin_memory().numpy()
+        out = s2.step_host(pinned, dt=0.0, nsteps=nsteps)
+        assert np.array_equal(out, to_host(du))
+        plain = s2.step_host(np.ascontiguousarray(u), dt=0.0, nsteps=nsteps)
+        assert np.array_equal(plain, to_host(du))
+        # two host calls from the same state: twice the simulated time
+        assert s2.time()[0] == pytest.approx(2 * s1.time()[0], rel=1e-15)
