@@ -46,9 +46,20 @@ __global__ void __launch_bounds__(kBlock1D) k_alpha_1d(int64_t E, const double* 
     const double e2 = tot2 > 0.0 ? m[N - 1] * m[N - 1] / tot2 : 0.0;
     energy = fmax(energy, e2);
   }
-  double a = 1.0 / (1.0 + exp(-T.ind_sharp * (energy - T.ind_T)));
-  if (a < 1e-3) a = 0.0;
-  if (a > 1.0 - 1e-3) a = 1.0;
+  // the logistic value lies below 1e-3 for z <= -7.5 and above 1 - 1e-3 for
+  // z >= 7.5, where the cut-offs decide it without the exponential (smooth
+  // elements, most of the mesh)
+  const double z = T.ind_sharp * (energy - T.ind_T);
+  double a;
+  if (z <= -7.5) {
+    a = 0.0;
+  } else if (z >= 7.5) {
+    a = 1.0;
+  } else {
+    a = 1.0 / (1.0 + exp(-z));
+    if (a < 1e-3) a = 0.0;
+    if (a > 1.0 - 1e-3) a = 1.0;
+  }
   alpha_raw[e] = a;
 }
 

@@ -61,9 +61,20 @@ __global__ void __launch_bounds__(kBlockAlpha) k_alpha_2d(int64_t Ne, const doub
     const double e2 = clip1 > 0.0 ? (clip1 - clip2) / clip1 : 0.0;
     energy = fmax(energy, e2);
   }
-  double a = 1.0 / (1.0 + exp(-T.ind_sharp * (energy - T.ind_T)));
-  if (a < 1e-3) a = 0.0;
-  if (a > 1.0 - 1e-3) a = 1.0;
+  // the logistic value lies below 1e-3 for z <= -7.5 and above 1 - 1e-3 for
+  // z >= 7.5, where the cut-offs decide it without the exponential (smooth
+  // elements, most of the mesh)
+  const double z = T.ind_sharp * (energy - T.ind_T);
+  double a;
+  if (z <= -7.5) {
+    a = 0.0;
+  } else if (z >= 7.5) {
+    a = 1.0;
+  } else {
+    a = 1.0 / (1.0 + exp(-z));
+    if (a < 1e-3) a = 0.0;
+    if (a > 1.0 - 1e-3) a = 1.0;
+  }
   alpha_raw[e] = a;
 }
 

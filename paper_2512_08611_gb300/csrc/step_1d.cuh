@@ -118,6 +118,35 @@ __device__ __forceinline__ void lo_flux(const double* uL, const double* uR, doub
   }
 }
 
+// Per-node parts of the shallow-water first-order flux: the spectral radius
+// |v| + sqrt(g h) and the momentum flux (with the pressure g h^2 / 2 in the
+// standard form).
+template <int SYS>
+__device__ __forceinline__ void lo_node_1d(double h, double m, double g, double& s, double& f) {
+  constexpr bool WB = (SYS == CRKFR_SYS_SWE_1D_WB);
+  const double v = m * drcp(h);
+  s = fabs(v) + dsqrt_pos(g * h);
+  f = WB ? m * v : fma(0.5 * g * h, h, m * v);
+}
+
+// lo_flux for shallow water from the per-node parts of its two states
+template <int SYS>
+__device__ __forceinline__ void lo_flux_nodes_1d(const double* uL, const double* uR, double cL,
+                                                 double cR, double sL, double sR, double fL,
+                                                 double fR, double g, double* fm, double* fp) {
+  constexpr bool WB = (SYS == CRKFR_SYS_SWE_1D_WB);
+  const double hL = uL[0], mL = uL[1], hR = uR[0], mR = uR[1];
+  const double lam = max_nonneg(sL, sR);
+  const double jh = WB ? (hR + cR) - (hL + cL) : hR - hL;
+  const double f0 = fma(-0.5 * lam, jh, 0.5 * (mL + mR));
+  const double f1 = fma(-0.5 * lam, mR - mL, 0.5 * (fL + fR));
+  const double wn = WB ? 0.5 * (hL + hR) + 0.5 * (cL + cR) : 0.5 * (cL + cR);
+  fm[0] = f0;
+  fp[0] = f0;
+  fm[1] = f1 + g * hL * wn;
+  fp[1] = f1 + g * hR * wn;
+}
+
 // Point-implicit backward-Euler source step of the low-order update
 // (Eq. low.order.update): u - dt s(u) = r, in closed form.
 template <int SYS>
@@ -200,6 +229,13 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
       const double rn = fmax(LA.alpha_raw[em], LA.alpha_raw[ep]);
       alpha = fmax(r0, 0.5 * rn);
     }
+    // inner subfaces p | p+1 from per-node parts (shallow water: one
+    // reciprocal and one root per node instead of per subface side)
+    double sp[n], fp2[n];
+    if constexpr (SWE) {
+#pragma unroll
+      for (int p = 0; p < n; ++p) lo_node_1d<SYS>(u0[0][p], u0[1][p], T.gravity, sp[p], fp2[p]);
+    }
 #pragma unroll
     for (int p = 0; p < LN; ++p) {
       double a[M], b[M], fm_[M], fp_[M];
@@ -208,7 +244,11 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
         a[v] = u0[v][p];
         b[v] = u0[v][p + 1];
       }
-      lo_flux<SYS>(a, b, cn[p], cn[p + 1], T, fm_, fp_);
+      if constexpr (SWE)
+        lo_flux_nodes_1d<SYS>(a, b, cn[p], cn[p + 1], sp[p], sp[p + 1], fp2[p], fp2[p + 1],
+                              T.gravity, fm_, fp_);
+      else
+        lo_flux<SYS>(a, b, cn[p], cn[p + 1], T, fm_, fp_);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         fim[v][p] = fm_[v];
@@ -420,7 +460,7 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
       Fp_[v] = (1.0 - af) * (b0 * FHp[v]) + af * fLp[v];
     }
     if constexpr (SWE) {
-      const double c0 = dtx / T.w[0], cN = dtx / T.w[N];
+      const double c0 = dtx * T.inv_w[0], cN = dtx * T.inv_w[N];
       const double fi0R = sm_fi0[0][t + 1], fiNL = fip[0][LN - 1];
       const double low0 = u0R[0] - c0 * (fi0R - fLp[0]);
       const double lowN = uN[0] - cN * (fLm[0] - fiNL);
@@ -507,7 +547,7 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
         for (int v = 0; v < M; ++v) {
           const double right = p < N ? fim[v][p < N ? p : 0] : Fm_lim[v];
           const double left = p > 0 ? fip[v][p > 0 ? p - 1 : 0] : sm_F[v][t];
-          x[v] = u0[v][p] - (dtx / T.w[p]) * (right - left);
+          x[v] = u0[v][p] - (dtx * T.inv_w[p]) * (right - left);
         }
         if constexpr (IMEX) lo_source<SYS>(T, dt, x);
 #pragma unroll
