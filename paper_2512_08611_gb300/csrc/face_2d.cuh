@@ -100,11 +100,21 @@ __device__ __forceinline__ void face_limited(const double* tm, const double* tp,
   // first-order face fluxes and Eq. Fblend
   double fLm[3], fLp[3];
   lo_flux_2d<DIR, WB>(lm, lp, lm[3], lp[3], g, fLm, fLp);
+  // (af = 0, both elements unlimited, and theta = 1 below are the common
+  // cases: there the blends reduce to their first terms and are skipped)
   const double b0 = T.b0;
+  if (af != 0.0) {
 #pragma unroll
-  for (int v = 0; v < 3; ++v) {
-    Fm[v] = (1.0 - af) * (b0 * FHm[v]) + af * fLm[v];
-    Fp[v] = (1.0 - af) * (b0 * FHp[v]) + af * fLp[v];
+    for (int v = 0; v < 3; ++v) {
+      Fm[v] = (1.0 - af) * (b0 * FHm[v]) + af * fLm[v];
+      Fp[v] = (1.0 - af) * (b0 * FHp[v]) + af * fLp[v];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      Fm[v] = b0 * FHm[v];
+      Fp[v] = b0 * FHp[v];
+    }
   }
   // Algorithm 1 (h > 0): the doubled-dt one-direction first-order updates
   // of the plus side's node 0 and the minus side's node N
@@ -113,10 +123,15 @@ __device__ __forceinline__ void face_limited(const double* tm, const double* tp,
   const double t0 = lp[0] - c2p * (lp[4] - Fp[0]);
   const double tN = lm[0] - c2m * (Fm[0] - lm[4]);
   const double th = fmin(theta_lin(0.1 * low0, low0, t0), theta_lin(0.1 * lowN, lowN, tN));
+  if (th < 1.0) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      Fm[v] = th * Fm[v] + (1.0 - th) * fLm[v];
+      Fp[v] = th * Fp[v] + (1.0 - th) * fLp[v];
+    }
+  }
 #pragma unroll
   for (int v = 0; v < 3; ++v) {
-    Fm[v] = th * Fm[v] + (1.0 - th) * fLm[v];
-    Fp[v] = th * Fp[v] + (1.0 - th) * fLp[v];
     Tm[v] = 2.0 * (Fm[v] * ib0 - FTm[v]);
     Tp[v] = 2.0 * (Fp[v] * ib0 - FTp[v]);
   }
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         lo[v][p] = x[v];
-        out[v][p] = (1.0 - alpha) * out[v][p] + alpha * x[v];
+        if (alpha != 0.0) out[v][p] = (1.0 - alpha) * out[v][p] + alpha * x[v];
       }
     }
     // Algorithm 2 over the element's n rows (lanes c*n .. c*n+n-1)
@@ -329,10 +344,12 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
       const int src = c * n + ((q + k) % n);
       thr = fmin(thr, __shfl_sync(0xffffffffu, th, src < 32 ? src : lane));
     }
+    if (thr < 1.0) {
 #pragma unroll
-    for (int v = 0; v < 3; ++v)
+      for (int v = 0; v < 3; ++v)
 #pragma unroll
-      for (int p = 0; p < n; ++p) out[v][p] = thr * out[v][p] + (1.0 - thr) * lo[v][p];
+        for (int p = 0; p < n; ++p) out[v][p] = thr * out[v][p] + (1.0 - thr) * lo[v][p];
+    }
   }
   if (active) {
 #pragma unroll

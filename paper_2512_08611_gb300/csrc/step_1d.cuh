@@ -453,11 +453,17 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
     }
     lo_flux<SYS>(uN, u0R, cn[N], sm_c0[t + 1], T, fLm, fLp);
     const double af = 0.5 * (alpha + sm_al[t + 1]);
+    // (af = 0 and theta = 1 are the common cases: there the blends reduce
+    // to their first terms and are skipped)
     double Fm_[M], Fp_[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) {
-      Fm_[v] = (1.0 - af) * (b0 * FHm[v]) + af * fLm[v];
-      Fp_[v] = (1.0 - af) * (b0 * FHp[v]) + af * fLp[v];
+      Fm_[v] = b0 * FHm[v];
+      Fp_[v] = b0 * FHp[v];
+      if (af != 0.0) {
+        Fm_[v] = (1.0 - af) * Fm_[v] + af * fLm[v];
+        Fp_[v] = (1.0 - af) * Fp_[v] + af * fLp[v];
+      }
     }
     if constexpr (SWE) {
       const double c0 = dtx * T.inv_w[0], cN = dtx * T.inv_w[N];
@@ -467,10 +473,12 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
       const double t0 = u0R[0] - c0 * (fi0R - Fp_[0]);
       const double tN = uN[0] - cN * (Fm_[0] - fiNL);
       const double th = fmin(theta_lin(0.1 * low0, low0, t0), theta_lin(0.1 * lowN, lowN, tN));
+      if (th < 1.0) {
 #pragma unroll
-      for (int v = 0; v < M; ++v) {
-        Fm_[v] = th * Fm_[v] + (1.0 - th) * fLm[v];
-        Fp_[v] = th * Fp_[v] + (1.0 - th) * fLp[v];
+        for (int v = 0; v < M; ++v) {
+          Fm_[v] = th * Fm_[v] + (1.0 - th) * fLm[v];
+          Fp_[v] = th * Fp_[v] + (1.0 - th) * fLp[v];
+        }
       }
     }
     // face terms in the doubled units of the corrections: 2 (F - F^tot) / b_ref
@@ -553,7 +561,7 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
 #pragma unroll
         for (int v = 0; v < M; ++v) {
           lo[v][p] = x[v];
-          out[v][p] = (1.0 - alpha) * out[v][p] + alpha * x[v];
+          if (alpha != 0.0) out[v][p] = (1.0 - alpha) * out[v][p] + alpha * x[v];
         }
       }
       if constexpr (SWE) {
@@ -564,10 +572,12 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
         double th = 1.0;
 #pragma unroll
         for (int p = 0; p < n; ++p) th = fmin(th, theta_lin(eps, lo[0][p], out[0][p]));
+        if (th < 1.0) {
 #pragma unroll
-        for (int v = 0; v < M; ++v)
+          for (int v = 0; v < M; ++v)
 #pragma unroll
-          for (int p = 0; p < n; ++p) out[v][p] = th * out[v][p] + (1.0 - th) * lo[v][p];
+            for (int p = 0; p < n; ++p) out[v][p] = th * out[v][p] + (1.0 - th) * lo[v][p];
+        }
       }
 #pragma unroll
       for (int v = 0; v < M; ++v)
