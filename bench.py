@@ -622,7 +622,11 @@ def run_ensemble(args):
         "speedup_vs_looped": (dof * args.steps / (ms / 1e3)) / looped,
         "roofline": {"bound": "alu", "kernel": "k_step_1d_batch (all kernels of the step)",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None},
+                     "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": profiled_traffic("k_step_1d_batch__ensemble256.md",
+                                                 ["step_1d.cuh", "device_common.cuh", "tableau.h"],
+                                                 1.0),
+                     "traffic_unit": "bytes per step (the degree classes' launches)"},
         "gpu_launches": launches, "clocks": clk}))
 
 
