@@ -272,3 +272,25 @@ def test_full_size_dam_break_sampled(crk):
         assert abs(alpha[y, x] - lim.last_alpha[2, 2]) < 1e-12
     assert np.max(alpha) > 0.5
     assert dt == pytest.approx(sch.compute_dt(u, b, cfl, 0.1), rel=1e-14)
+
+
+def test_thousand_limited_steps_2d(crk):
+    """1000 CFL steps of the limited 2D step with the indicator on a circular
+    dam break onto a thin layer (8 x 8, N = 3, GLL, C_s 0.1): positive, and
+    1e-10 relative L2 from the oracle after 1000 steps."""
+    N, E = 3, 8
+    u, b, dx, dy = dam(N, E, E)
+    sch = Scheme2D(ShallowWater2D(G), N, dx, dy, family="gll")
+    lim = Blending2D(sch)
+    cfl = golden_cfl(N, "gll")
+    v = u.copy()
+    for _ in range(1000):
+        v = lim.step(v, b, sch.compute_dt(v, b, cfl, 0.1))
+    s = solver(crk, "swe2d", N, "gll", E, E, b, cs=0.1)
+    s.set_limiter("blend")
+    du = to_dev(u)
+    s.step(du, 0.0, 1000)
+    s.status()
+    got = to_host(du)
+    assert np.min(got[0]) > 0.0
+    assert rel_l2(got, v) < 1e-10

@@ -186,3 +186,23 @@ def test_host_step_reads_rows_back_in_chunks(crk, Ex, Ey, limited):
         assert np.array_equal(plain, to_host(du))
         # two host calls from the same state: twice the simulated time
         assert s2.time()[0] == pytest.approx(2 * s1.time()[0], rel=1e-15)
+
+
+def test_thousand_steps_2d(crk):
+    """1000 CFL steps of the 2D workload's recipe (32 Gaussians of bathymetry,
+    a surface bump, a smooth current) on a 12 x 10, N = 3 mesh: 1e-10
+    relative L2 after 1000 steps."""
+    N, Ex, Ey = 3, 12, 10
+    u, b, dx, dy = swe2d_case(N, "gl", Ex, Ey, seed=7)
+    sch = Scheme2D(ShallowWater2D(G), N, dx, dy)
+    cfl = golden_cfl(N, "gl")
+    v = u
+    for _ in range(1000):
+        v = sch.step(v, b, sch.compute_dt(v, b, cfl, 0.5))
+    s = solver(crk, N, "gl", Ex, Ey, b)
+    du = to_dev(u)
+    s.step(du, 0.0, 1000)
+    s.status()
+    assert rel_l2(to_host(du), v) < 1e-10
+    # the flow has moved
+    assert rel_l2(v, u) > 1e-4
