@@ -213,3 +213,26 @@ def test_adjoint_with_source_is_refused(crk):
     with pytest.raises(crk.CrkfrError) as e:
         s.step_adjoint(to_dev(u), to_dev(np.ones_like(u)), 1e-3)
     assert e.value.status == -2
+
+
+def test_swe2d_chezy_thousand_steps(crk):
+    """1000 CFL steps of the friction workload's recipe (bathymetry, bump and
+    current; C_f = 0.0025 as in the bench) on a 12 x 10, N = 3 mesh: 1e-10
+    relative L2 after 1000 steps."""
+    N, Ex, Ey = 3, 12, 10
+    bs = Basis(N)
+    x, y, dx, dy = positions_2d(bs, Ex, Ey, 100.0)
+    inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=100.0, current=(0.3, 0.2)), (x, y), 3)
+    u, b = inp.state(x, y)
+    Cf = 0.0025
+    sch = Scheme2D(ShallowWater2D(G), N, dx, dy, source=ChezyFriction(Cf))
+    cfl = golden_cfl_imex(N, "gl")
+    want = u.copy()
+    for _ in range(1000):
+        want = sch.step(want, b, sch.compute_dt(want, b, cfl, 0.5))
+    s = solver(crk, "swe2d", N, "gl", [Ex, Ey], 100.0, b, "chezy", Cf)
+    du = to_dev(u)
+    s.step(du, 0.0, 1000)
+    s.status()
+    assert rel_l2(to_host(du), want) < 1e-10
+    assert rel_l2(want, u) > 1e-4

@@ -208,3 +208,20 @@ def test_thousand_steps_wb_with_friction(crk):
     s.step(du, 0.0, 1000)
     assert rel_l2(to_host(du), v) < 1e-10
     s.status()
+
+
+def test_wb2d_thousand_steps(crk):
+    """1000 CFL steps of the well-balanced 2D form on a moving flow over
+    bathymetry (12 x 10, N = 3): 1e-10 relative L2 after 1000 steps."""
+    N, Ex, Ey = 3, 12, 10
+    u, b, dx, dy = case_2d(N, "gl", Ex, Ey, seed=2)
+    sch = Scheme2D(ShallowWater2DWB(G), N, dx, dy)
+    want = u.copy()
+    for _ in range(1000):
+        want = sch.step(want, b, sch.compute_dt(want, b, golden_cfl(N, "gl"), 0.5))
+    s = solver(crk, "swe2d_wb", N, "gl", [Ex, Ey], 100.0, b)
+    du = to_dev(u)
+    s.step(du, 0.0, 1000)
+    s.status()
+    assert rel_l2(to_host(du), want) < 1e-10
+    assert rel_l2(want, u) > 1e-4
