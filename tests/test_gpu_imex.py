@@ -236,3 +236,29 @@ def test_swe2d_chezy_thousand_steps(crk):
     s.status()
     assert rel_l2(to_host(du), want) < 1e-10
     assert rel_l2(want, u) > 1e-4
+
+
+def test_full_size_friction_workload_sampled(crk):
+    """The friction bench workload as the benchmark launches it (1024^2,
+    N = 3, GL, C_f = 0.0025, current (0.3, 0.2), seed 0): one CFL step; the
+    oracle recomputes 128 sampled elements (incl. the corners)."""
+    N, E = 3, 1024
+    bs = Basis(N)
+    x, y, dx, dy = positions_2d(bs, E, E, 100.0)
+    inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=100.0, current=(0.3, 0.2)), (x, y), 0)
+    u, b = inp.state(x, y)
+    del x, y
+    Cf = 0.0025
+    sch = Scheme2D(ShallowWater2D(G), N, dx, dy, source=ChezyFriction(Cf))
+    dt = sch.compute_dt(u, b, golden_cfl_imex(N, "gl"), 0.5)
+    s = solver(crk, "swe2d", N, "gl", [E, E], 100.0, b, "chezy", Cf)
+    du = to_dev(u)
+    assert s.compute_dt(du) == pytest.approx(dt, rel=1e-14)
+    s.step(du, 0.0, 1)
+    got = to_host(du)
+    rng = np.random.default_rng(21)
+    ey = np.concatenate([[0, 0, E - 1, E - 1], rng.integers(0, E, 124)])
+    ex = np.concatenate([[0, E - 1, 0, E - 1], rng.integers(0, E, 124)])
+    want = sch.step_elements(u, b, dt, ey, ex)
+    assert rel_l2(got[:, ey, ex], want) < 1e-12
+    s.status()

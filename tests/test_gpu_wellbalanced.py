@@ -225,3 +225,29 @@ def test_wb2d_thousand_steps(crk):
     s.status()
     assert rel_l2(to_host(du), want) < 1e-10
     assert rel_l2(want, u) > 1e-4
+
+
+def test_full_size_wb_workload_sampled(crk):
+    """The well-balanced bench workload as the benchmark launches it (1024^2,
+    N = 3, GL, 32 Gaussians, bump, at rest otherwise, seed 0): one CFL step;
+    the oracle recomputes 128 sampled elements (incl. the corners)."""
+    N, E = 3, 1024
+    bs = Basis(N)
+    x, y, dx, dy = positions_2d(bs, E, E, 100.0)
+    inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=100.0), (x, y), 0)
+    u, b = inp.state(x, y)
+    del x, y
+    sch = Scheme2D(ShallowWater2DWB(G), N, dx, dy)
+    dt = sch.compute_dt(u, b, golden_cfl(N, "gl"), 0.5)
+    s = solver(crk, "swe2d_wb", N, "gl", [E, E], 100.0, b)
+    du = to_dev(u)
+    assert s.compute_dt(du) == pytest.approx(dt, rel=1e-14)
+    s.step(du, 0.0, 1)
+    got = to_host(du)
+    rng = np.random.default_rng(22)
+    ey = np.concatenate([[0, 0, E - 1, E - 1], rng.integers(0, E, 124)])
+    ex = np.concatenate([[0, E - 1, 0, E - 1], rng.integers(0, E, 124)])
+    want = sch.step_elements(u, b, dt, ey, ex)
+    assert rel_l2(got[:, ey, ex], want) < TOL_STEP
+    assert np.max(np.abs(want - u[:, ey, ex])) > 0
+    s.status()
