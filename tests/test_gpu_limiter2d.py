@@ -294,3 +294,35 @@ def test_thousand_limited_steps_2d(crk):
     got = to_host(du)
     assert np.min(got[0]) > 0.0
     assert rel_l2(got, v) < 1e-10
+
+
+def test_full_size_limited_workload_sampled(crk):
+    """The limited bench workload as the benchmark launches it (1024^2, N = 3,
+    GL, the default workload's inputs, indicator on): one CFL step; 64
+    sampled elements (incl. the corners) against the oracle's step of the
+    5 x 5 patch around each."""
+    from paper_2512_08611_gb300.workloads import SWE2DInput, accept_seed
+    N, E = 3, 1024
+    bs = Basis(N)
+    x, y, dx, dy = positions_2d(bs, E, E, 100.0)
+    inp, _ = accept_seed(lambda s: SWE2DInput(seed=s, L=100.0), (x, y), 0)
+    u, b = inp.state(x, y)
+    del x, y
+    s = crk.Solver("swe2d", N, gravity=G, cfl_safety=0.5, cfl_number=golden_cfl(N, "gl"))
+    s.set_mesh([E, E], [0.0, 0.0], [100.0, 100.0])
+    s.set_coefficients(to_dev(b))
+    s.set_limiter("blend")
+    du = to_dev(u)
+    dt = s.compute_dt(du)
+    s.step(du, 0.0, 1)
+    got = to_host(du)
+    alpha = to_host(s.limiter_alpha())
+    rng = np.random.default_rng(9)
+    ey = np.concatenate([[0, 0, E - 1, E - 1], rng.integers(0, E, 60)])
+    ex = np.concatenate([[0, E - 1, 0, E - 1], rng.integers(0, E, 60)])
+    sch5 = Scheme2D(ShallowWater2D(G), N, dx, dy)
+    for yy, xx in zip(ey, ex):
+        lim = Blending2D(sch5)
+        out = lim.step(_patch(u, yy, xx), _patch(b[None], yy, xx)[0], dt)
+        assert rel_l2(got[:, yy, xx], out[:, 2, 2]) < TOL_STEP, (yy, xx)
+        assert abs(alpha[yy, xx] - lim.last_alpha[2, 2]) < 1e-12
