@@ -314,6 +314,17 @@ def run_reference(args, wl):
     print(json.dumps(out))
 
 
+def build_once(world, dist):
+    """Build the library (if it is not up to date) in one process only; the
+    other ranks wait for it, so no two processes write the same files."""
+    from paper_2512_08611_gb300.build import build_library
+    if world > 1:
+        if dist.get_rank() == 0:
+            build_library()
+        dist.barrier()
+    build_library()
+
+
 def run_ours(args, wl):
     import torch
     import torch.distributed as dist
@@ -324,9 +335,7 @@ def run_ours(args, wl):
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-
-    from paper_2512_08611_gb300.build import build_library
-    build_library()
+    build_once(world, dist)
     from paper_2512_08611_gb300 import crkfr
 
     split = world > 1
@@ -522,12 +531,11 @@ def run_ensemble(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl")
-    from paper_2512_08611_gb300.build import build_library
-    build_library()
+    torch.cuda.set_device(local)
+    build_once(world, dist)
     from paper_2512_08611_gb300 import crkfr
     from paper_2512_08611_gb300.flops import local_flops_per_element
     from paper_2512_08611_gb300.workloads import SWE1DInput, accept_seed, ensemble_members
-    torch.cuda.set_device(local)
     L = 100.0
     mem = ensemble_members(256, seed=rank)
     nodes = {N: crkfr.Solver("swe1d", N).nodes()[0] for N in (2, 3, 4)}

@@ -187,3 +187,31 @@ def test_rank_drop_is_detected():
     assert procs[1].exitcode == 3
     assert out[1] == "left"
     assert str(out[0]).startswith("error after"), out[0]
+
+
+def _worker_build(rank, world, port, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2512_08611_gb300 import build
+    _init(rank, world, port)
+    bench.build_once(world, dist)
+    out[rank] = build.up_to_date()
+    dist.destroy_process_group()
+
+
+def test_benchmark_ranks_build_the_library_once():
+    """Under torchrun every rank of bench.py needs the library: rank 0 builds
+    it while the others wait at a barrier, then all find it up to date."""
+    from paper_2512_08611_gb300 import build
+    build.build_library()
+    world, port = 2, free_port()
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    procs = [ctx.Process(target=_worker_build, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert all(out[r] for r in range(world))
