@@ -178,10 +178,10 @@ crkfr_status crkfr_advance(crkfr_ctx* ctx, double* u_dev, double t_end, int64_t 
 
 /* Same as crkfr_step on host memory: copies u_in_host to a context-owned
  * device state, steps, and copies the result to u_out_host (the two may be
- * the same buffer).  In 2D the last step's face kernel runs in up to 8
- * chunks of element rows, and each chunk's rows are copied back on a
- * context-owned stream while the next chunk computes (u_out_host should be
- * pinned for the copies to overlap).  Synchronises the stream. */
+ * the same buffer).  In 2D the last step's kernels run in up to 8 parts of
+ * element rows, and each part's rows are copied back on a context-owned
+ * stream while the later parts compute (u_out_host should be pinned for the
+ * copies to overlap).  Synchronises the stream. */
 crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_out_host,
                              double dt, int64_t nsteps, void* stream);
 

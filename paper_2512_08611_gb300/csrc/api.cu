@@ -255,12 +255,17 @@ crkfr_status launch_rate(crkfr_ctx* c, const double* u, int slot, cudaStream_t s
   return CRKFR_OK;
 }
 
-// The face kernel of a 2D step in up to kHostChunks chunks of element rows,
-// each chunk's rows of u (contiguous per variable) copied to host_out on the
-// copy stream once the chunk's face kernel has finished; the stream s then
-// waits for the last copy.
-crkfr_status faces_with_readback(crkfr_ctx* c, Launch2D L, const double* u, double* host_out,
-                                 cudaStream_t s) {
+// The local and face kernels of a 2D step in up to kHostChunks parts of
+// element rows, each part's rows of u (contiguous per variable) copied to
+// host_out on the copy stream as soon as its face kernel has finished, while
+// the later parts compute; the stream s then waits for the last copy.  The
+// face kernel of part k needs the local kernel of the rows next to it, so the
+// order is: local of the last part (the periodic neighbour of row 0), local
+// of part 0, then local of part k+1 before the face kernel of part k.  The
+// local kernels read only their own rows of u, which no earlier face kernel
+// of this step writes.  The first local launch does the step's bookkeeping.
+crkfr_status step_with_readback(crkfr_ctx* c, Launch2D L, const double* u, double* host_out,
+                                cudaStream_t s) {
   if (!c->copy_stream) {
     CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     for (auto& ev : c->ev_rows) CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -270,21 +275,43 @@ crkfr_status faces_with_readback(crkfr_ctx* c, Launch2D L, const double* u, doub
   const int64_t nn = (int64_t)c->basis.n * c->basis.n;
   int64_t rows = (Ey + kHostChunks - 1) / kHostChunks;
   rows = (rows + 7) / 8 * 8;
-  int k = 0;
-  for (int64_t r0 = 0; r0 < Ey; r0 += rows, ++k) {
-    const int64_t r1 = r0 + rows < Ey ? r0 + rows : Ey;
-    L.row_begin = r0;
-    L.row_end = r1;
-    int e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+  const int parts = (int)((Ey + rows - 1) / rows);
+  auto r_begin = [&](int k) { return (int64_t)k * rows; };
+  auto r_end = [&](int k) { return (int64_t)(k + 1) * rows < Ey ? (int64_t)(k + 1) * rows : Ey; };
+  bool first = true;
+  auto local_part = [&](int k) -> crkfr_status {
+    Launch2D P = L;
+    P.row_begin = r_begin(k);
+    P.row_end = r_end(k);
+    P.ctl.skip_bookkeeping = first ? 0 : 1;
+    first = false;
+    int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(P, s); });
+    if (e) return cuda_fail(c, e, "2D local kernel");
+    c->launches += 1;
+    return CRKFR_OK;
+  };
+  auto face_part = [&](int k) -> crkfr_status {
+    Launch2D P = L;
+    P.row_begin = r_begin(k);
+    P.row_end = r_end(k);
+    int e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(P, s); });
     if (e) return cuda_fail(c, e, "2D face kernel");
     c->launches += 1;
     CK(c, cudaEventRecord(c->ev_rows[k], s));
     CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_rows[k], 0));
-    const size_t off = (size_t)(r0 * c->Ex) * nn;
-    const size_t bytes = sizeof(double) * (size_t)((r1 - r0) * c->Ex) * nn;
+    const size_t off = (size_t)(P.row_begin * c->Ex) * nn;
+    const size_t bytes = sizeof(double) * (size_t)((P.row_end - P.row_begin) * c->Ex) * nn;
     for (int v = 0; v < 3; ++v)
       CK(c, cudaMemcpyAsync(host_out + v * Ne * nn + off, u + v * Ne * nn + off, bytes,
                             cudaMemcpyDeviceToHost, c->copy_stream));
+    return CRKFR_OK;
+  };
+  crkfr_status st;
+  if (parts > 1 && (st = local_part(parts - 1)) != CRKFR_OK) return st;
+  if ((st = local_part(0)) != CRKFR_OK) return st;
+  for (int k = 0; k < parts; ++k) {
+    if (k + 1 <= parts - 2 && (st = local_part(k + 1)) != CRKFR_OK) return st;
+    if ((st = face_part(k)) != CRKFR_OK) return st;
   }
   CK(c, cudaEventRecord(c->ev_copied, c->copy_stream));
   CK(c, cudaStreamWaitEvent(s, c->ev_copied, 0));
@@ -292,9 +319,9 @@ crkfr_status faces_with_readback(crkfr_ctx* c, Launch2D L, const double* u, doub
 }
 
 // nsteps steps of u in place.  dt > 0 fixed, otherwise CFL (clipped to t_end).
-// host_out (2D, optional): the last step's face kernel runs in row chunks and
-// each chunk's rows are copied to host_out on the context's copy stream as
-// soon as they are final; the caller's stream waits for the copies.
+// host_out (2D, optional): the last step runs in row parts and each part's
+// rows are copied to host_out on the context's copy stream as soon as they
+// are final (step_with_readback); the caller's stream waits for the copies.
 // *copied tells whether that happened.
 crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, double t_end,
                        cudaStream_t s, double* host_out = nullptr, bool* copied = nullptr) {
@@ -366,17 +393,16 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
         if (ea) return cuda_fail(c, ea, "indicator kernels");
         c->launches += c->limit_mode == CRKFR_LIMITER_BLEND ? 2 : 1;
       }
-      int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
-      if (e) return cuda_fail(c, e, "2D local kernel");
-      c->launches += 1;
       if (host_out && k == nsteps - 1) {
-        crkfr_status st = faces_with_readback(c, L, u, host_out, s);
+        crkfr_status st = step_with_readback(c, L, u, host_out, s);
         if (st != CRKFR_OK) return st;
         if (copied) *copied = true;
       } else {
+        int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
+        if (e) return cuda_fail(c, e, "2D local kernel");
         e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
         if (e) return cuda_fail(c, e, "2D face kernel");
-        c->launches += 1;
+        c->launches += 2;
       }
       c->nstep += 1;
     }

@@ -84,6 +84,9 @@ struct StepCtl {
   int tslot;         // time slot read by this step
   int want_rate;     // compute the rate of the new state
   int residual;      // 1: write r = (u^{n+1}-u^n)/dt instead of u^{n+1}
+  int skip_bookkeeping;  // 2D local kernel launched in row parts: 1 on all
+                         // parts but the first (the step's time bookkeeping
+                         // runs once)
 };
 
 struct HostBasis {
@@ -203,8 +206,9 @@ struct Launch2D {
   Tables tab;
   StepCtl ctl;
   LimitArgs2D lim;       // mode 0: no limiter
-  // element rows [row_begin, row_end) the face kernel updates (row_begin a
-  // multiple of 8, row_end a multiple of 8 or Ey): the whole mesh by default
+  // element rows [row_begin, row_end) the local and face kernels process
+  // (for the face kernel row_begin a multiple of 8, row_end a multiple of 8
+  // or Ey): the whole mesh by default
   int64_t row_begin, row_end;
 };
 // Adjoint of one 2D step (kernels_adj2d.cu); the forward local kernel must

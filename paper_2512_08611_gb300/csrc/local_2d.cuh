@@ -60,17 +60,19 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int le = lane / n, q = lane - le * n;
   const int64_t Ne = L.Ex * L.Ey;
-  const int64_t g = ((int64_t)blockIdx.x * kWarpsLocal + warp) * EPW + le;
-  // lanes past EPW*n (n = 3, 5) and lanes past the last element compute on
-  // element 0 and store nothing, neither to memory nor to shared memory
+  const int64_t g = L.row_begin * L.Ex + ((int64_t)blockIdx.x * kWarpsLocal + warp) * EPW + le;
+  // lanes past EPW*n (n = 3, 5) and lanes past the last element of the rows
+  // [row_begin, row_end) compute on element 0 and store nothing, neither to
+  // memory nor to shared memory
   const bool lane_ok = le < EPW;
-  const bool active = lane_ok && (g < Ne);
+  const bool active = lane_ok && (g < L.row_end * L.Ex);
   const int64_t ge = active ? g : 0;
   const int lec = lane_ok ? le : 0;
   double (*X)[n][n] = sm[warp][lec];
 
   const double dt = RES ? L.ctl.dt_fixed : step_dt(L.ctl, L.st);
-  if (!RES && blockIdx.x == 0 && threadIdx.x == 0) step_bookkeeping(L.ctl, L.st, dt);
+  if (!RES && blockIdx.x == 0 && threadIdx.x == 0 && !L.ctl.skip_bookkeeping)
+    step_bookkeeping(L.ctl, L.st, dt);
 
   // ---- load row q of u^n and of the static terms g b_x, g b_y ---------------
   double u0[3][n], gbx[n], gby[n];
@@ -341,7 +343,9 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
 template <int N, bool GLL, bool IMEX, bool WB, bool LIMIT = false>
 int launch_local_t(const Launch2D& L, cudaStream_t s) {
   constexpr int per_block = kWarpsLocal * (32 / (N + 1));
-  const int64_t blocks = (L.Ex * L.Ey + per_block - 1) / per_block;
+  if (L.row_begin < 0 || L.row_end <= L.row_begin || L.row_end > L.Ey)
+    return (int)cudaErrorInvalidValue;
+  const int64_t blocks = ((L.row_end - L.row_begin) * L.Ex + per_block - 1) / per_block;
   if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
   if constexpr (LIMIT)
     k_local_2d<N, GLL, false, IMEX, WB, true><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
