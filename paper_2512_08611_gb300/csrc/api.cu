@@ -787,6 +787,8 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
   st = run_steps(c, c->d_stage, dt, nsteps, std::numeric_limits<double>::infinity(), s,
                  c->dim == 2 ? u_out : nullptr, &copied);
   if (st != CRKFR_OK) {
+    // copies already queued on the copy stream still target u_out
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
     cudaStreamSynchronize(s);
     return st;
   }
