@@ -158,3 +158,73 @@ def test_advection_has_no_constraint_and_blends():
     # unlimited one
     plain = sch.step(v, a, 0.2 * fourier.cfl_number(N, halvings=30) * dx / 1.5)
     assert np.max(np.abs(out - 0.5)) < np.max(np.abs(plain - 0.5))
+
+
+@pytest.mark.parametrize("N,family", [(N, f) for N in (1, 2, 3, 4) for f in ("gl", "gll")])
+def test_modal_coefficients_of_single_modes(N, family):
+    """The nodal values of the orthonormal Legendre mode j (on [0, 1] mapped to
+    [-1, 1]) have the coefficient vector e_j, and the coefficients of any
+    nodal data satisfy Parseval against a 12-point Gauss-Legendre integral of
+    its interpolant (independent of the inverse Vandermonde)."""
+    from oracle.limiter import legendre_orthonormal, modal_coefficients
+    bs = Basis(N, family)
+    for j in range(N + 1):
+        X = legendre_orthonormal(j, 2.0 * bs.xi - 1.0)
+        m = modal_coefficients(bs, X)
+        e = np.zeros(N + 1)
+        e[j] = 1.0
+        assert np.max(np.abs(m - e)) < 1e-13
+    rng = np.random.default_rng(N)
+    X = rng.standard_normal(N + 1)
+    m = modal_coefficients(bs, X)
+    g, w = np.polynomial.legendre.leggauss(12)
+    # Lagrange interpolant of X at the quadrature points of [-1, 1]
+    xi = 2.0 * bs.xi - 1.0
+    P = np.ones((12, N + 1))
+    for k in range(N + 1):
+        for l in range(N + 1):
+            if l != k:
+                P[:, k] *= (g - xi[l]) / (xi[k] - xi[l])
+    assert abs(np.sum(m * m) - np.sum(w * (P @ X) ** 2)) < 1e-12 * np.sum(m * m)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_indicator_energy_and_logistic_centre(N):
+    """Mode N alone has energy 1 (alpha 1); the mean plus mode N scaled so
+    that its energy share is exactly the threshold T(N) sits at the centre of
+    the logistic map (alpha 1/2); the mean plus mode N-1 with share T of the
+    modes below N also gives 1/2 (the second energy of the indicator)."""
+    from oracle.limiter import legendre_orthonormal
+    bs = Basis(N)
+    xi = 2.0 * bs.xi - 1.0
+    T = 0.5 * 10.0 ** (-1.8 * (N + 1) ** 0.25)
+    mode = lambda j: legendre_orthonormal(j, xi)
+    a = hennemann_alpha(bs, mode(N)[None, :], smooth=False)
+    assert a[0] == 1.0
+    r = np.sqrt(T / (1.0 - T))
+    a = hennemann_alpha(bs, (mode(0) + r * mode(N))[None, :], smooth=False)
+    assert a[0] == pytest.approx(0.5, abs=1e-9)
+    a = hennemann_alpha(bs, (mode(0) + r * mode(N - 1))[None, :], smooth=False)
+    assert a[0] == pytest.approx(0.5, abs=1e-9)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_indicator_2d_mode_classes(N):
+    """Tensor-product modes: P_i(y) P_j(x) with max(i, j) = N has energy 1 in
+    the first class (alpha 1); the mean plus a mode with max(i, j) = N - 1 of
+    share T among the modes below N sits at alpha 1/2; a mode with both
+    degrees below N - 1 leaves alpha 0."""
+    from oracle.limiter import hennemann_alpha_2d, legendre_orthonormal
+    bs = Basis(N)
+    xi = 2.0 * bs.xi - 1.0
+    T = 0.5 * 10.0 ** (-1.8 * (N + 1) ** 0.25)
+    m2 = lambda i, j: np.outer(legendre_orthonormal(i, xi), legendre_orthonormal(j, xi))
+    one = lambda X: X[None, None]
+    assert hennemann_alpha_2d(bs, one(m2(N, 0)), smooth=False)[0, 0] == 1.0
+    assert hennemann_alpha_2d(bs, one(m2(1, N)), smooth=False)[0, 0] == 1.0
+    r = np.sqrt(T / (1.0 - T))
+    X = m2(0, 0) + r * m2(N - 1, N - 2 if N >= 2 else 0)
+    assert hennemann_alpha_2d(bs, one(X), smooth=False)[0, 0] == pytest.approx(0.5, abs=1e-9)
+    if N >= 3:
+        X = m2(0, 0) + 0.5 * m2(N - 2, N - 2)
+        assert hennemann_alpha_2d(bs, one(X), smooth=False)[0, 0] == 0.0
