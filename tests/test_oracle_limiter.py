@@ -75,6 +75,27 @@ def test_alpha_one_is_subcell_finite_volumes(N, family):
     assert np.max(np.abs(got - want)) < 1e-14
 
 
+@pytest.mark.parametrize("N,family", [(1, "gl"), (3, "gll")])
+def test_alpha_one_with_friction_is_fv_then_backward_euler(N, family):
+    """With Chezy friction and alpha = 1 the limited step is the subcell FV
+    update followed by a backward-Euler friction step per node, in closed
+    form here (|m| + dt C_f |m|^2 / h^2 = |r|, positive root) instead of the
+    oracle's Newton iteration."""
+    from oracle.sources import ChezyFriction
+    bs, x, dx = grid(N, 7, family=family)
+    b = 0.1 * np.sin(2 * np.pi * x) ** 2
+    u = np.stack([1.0 + 0.1 * np.cos(2 * np.pi * x) - b, 0.3 * np.sin(2 * np.pi * x)])
+    sy = ShallowWater1D(G)
+    Cf = 3.0
+    sch = Scheme1D(sy, N, dx, family=family, source=ChezyFriction(Cf))
+    dt = 0.2 * dx * np.min(bs.w) / 4.0
+    got = Blending1D(sch, alpha=1.0).step(u, b, dt)
+    h, r = subcell_fv(sy, u, b, bs.w, dx, dt)
+    k = dt * Cf / (h * h)
+    m = np.sign(r) * (-1.0 + np.sqrt(1.0 + 4.0 * k * np.abs(r))) / (2.0 * k)
+    assert np.max(np.abs(got - np.stack([h, m]))) < 1e-14
+
+
 def dam_break(N, E, hR=1e-3, family="gll"):
     bs, x, dx = grid(N, E, family=family)
     h = np.where((x > 0.25) & (x < 0.75), 1.0, hR)

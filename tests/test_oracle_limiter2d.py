@@ -154,3 +154,27 @@ def test_well_balanced_lake_at_rest_with_2d_limiter(alpha):
     for _ in range(8):
         u = lim.step(u, b, 1e-3)
     assert np.max(np.abs(u - u0)) < 1e-13
+
+
+@pytest.mark.parametrize("N,family", [(1, "gl"), (2, "gll")])
+def test_alpha_one_with_friction_is_fv_then_backward_euler(N, family):
+    """With Chezy friction and alpha = 1 the limited step is the first-order
+    subcell FV update followed by a backward-Euler friction step per node,
+    here in closed form (m parallel to the FV momentum r, |m| the positive
+    root of |m| + dt C_f |m|^2 / h^2 = |r|) instead of the oracle's Newton
+    iteration."""
+    from oracle.sources import ChezyFriction
+    bs, x, y, dx, dy = grid(N, 3, 2, family)
+    u, b = flow(x, y)
+    sy = ShallowWater2D(G)
+    Cf = 2.0
+    sch = Scheme2D(sy, N, dx, dy, family=family, source=ChezyFriction(Cf))
+    dt = 0.05 * min(dx, dy) * np.min(bs.w) / 4.0
+    got = Blending2D(sch, alpha=1.0).step(u, b, dt)
+    fv = subcell_fv_2d(sy, u, b, bs.w, dx, dy, dt)
+    h, rx, ry = fv
+    nr = np.sqrt(rx * rx + ry * ry)
+    k = dt * Cf / (h * h)
+    nm = (-1.0 + np.sqrt(1.0 + 4.0 * k * nr)) / (2.0 * k)
+    want = np.stack([h, rx * nm / nr, ry * nm / nr])
+    assert np.max(np.abs(got - want)) < 1e-13
