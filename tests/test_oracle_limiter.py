@@ -92,7 +92,8 @@ def test_alpha_one_with_friction_is_fv_then_backward_euler(N, family):
     got = Blending1D(sch, alpha=1.0).step(u, b, dt)
     h, r = subcell_fv(sy, u, b, bs.w, dx, dt)
     k = dt * Cf / (h * h)
-    m = np.sign(r) * (-1.0 + np.sqrt(1.0 + 4.0 * k * np.abs(r))) / (2.0 * k)
+    # the positive root without cancellation: 2 |r| / (1 + sqrt(1 + 4 k |r|))
+    m = 2.0 * r / (1.0 + np.sqrt(1.0 + 4.0 * k * np.abs(r)))
     assert np.max(np.abs(got - np.stack([h, m]))) < 1e-14
 
 

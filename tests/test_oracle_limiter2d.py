@@ -175,6 +175,6 @@ def test_alpha_one_with_friction_is_fv_then_backward_euler(N, family):
     h, rx, ry = fv
     nr = np.sqrt(rx * rx + ry * ry)
     k = dt * Cf / (h * h)
-    nm = (-1.0 + np.sqrt(1.0 + 4.0 * k * nr)) / (2.0 * k)
-    want = np.stack([h, rx * nm / nr, ry * nm / nr])
+    f = 2.0 / (1.0 + np.sqrt(1.0 + 4.0 * k * nr))   # |m| / |r|, without cancellation
+    want = np.stack([h, rx * f, ry * f])
     assert np.max(np.abs(got - want)) < 1e-13
