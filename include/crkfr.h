@@ -120,7 +120,8 @@ typedef struct {
  * on failure. */
 crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg);
 
-/* Free the context and every device buffer it owns (synchronises the device). */
+/* Free the context and every device buffer it owns (synchronises the device).
+ * Resource management only: the paper has no counterpart. */
 void crkfr_destroy(crkfr_ctx* ctx);
 
 /* Uniform periodic mesh (Sec. 2, Eqs. reference.element, ref.map).
@@ -130,21 +131,26 @@ void crkfr_destroy(crkfr_ctx* ctx);
 crkfr_status crkfr_set_mesh(crkfr_ctx* ctx, int32_t dim, const int64_t* n_elem,
                             const double* lo, const double* hi);
 
-/* Number of FP64 values of the state u (vars x nodes) and of the coefficient
- * field c, for the mesh that is set. */
+/* Number of FP64 values of the state u (vars x nodes: (N+1)^dim nodal
+ * values of the solution polynomial per element, Sec. 2, Eq. soln.poly) and
+ * of the coefficient field c, for the mesh that is set. */
 crkfr_status crkfr_sizes(const crkfr_ctx* ctx, int64_t* n_state, int64_t* n_coef);
 
 /* Solution points xi_p in [0, 1] and quadrature weights w_p (N+1 values each,
  * host arrays) of the context's node family (Sec. 2, Eq. soln.points). */
 crkfr_status crkfr_get_nodes(const crkfr_ctx* ctx, double* xi_host, double* w_host);
 
-/* CFL(N) the context uses (given or computed). */
+/* CFL(N) of Sec. 5, Eq. time.step.2d, that the context uses (given or
+ * computed). */
 crkfr_status crkfr_get_cfl(const crkfr_ctx* ctx, double* cfl_host);
 
 /* Static coefficient field c at the solution points (device, layout above):
- * a(x) for advection, the bathymetry b for shallow water.  The library
- * derives and stores what the scheme needs from it (the local
- * non-conservative factor B(c) dloc c per node and the face traces of c). */
+ * a(x) for advection, the bathymetry b for shallow water, the static part of
+ * w = (u, c) in the non-conservative product B(w) dw/dx (Sec. 3, Eq.
+ * crkfr.non.cons.final; c as a field of x rather than an evolved variable,
+ * Sec. 5.1.3).  The library derives and stores what the scheme needs from it
+ * (the local non-conservative factor B(c) dloc c per node and the face
+ * traces of c). */
 crkfr_status crkfr_set_coefficients(crkfr_ctx* ctx, const double* c_dev, void* stream);
 
 /* Time step of Sec. 5, Eq. time.step.2d for the state u_dev:
@@ -176,7 +182,8 @@ crkfr_status crkfr_step(crkfr_ctx* ctx, double* u_dev, double dt, int64_t nsteps
 crkfr_status crkfr_advance(crkfr_ctx* ctx, double* u_dev, double t_end, int64_t max_steps,
                            int64_t* steps_taken, void* stream);
 
-/* Same as crkfr_step on host memory: copies u_in_host to a context-owned
+/* The step of crkfr_step (Sec. 3, Eq. crkfr.non.cons.final) on host memory;
+ * the host transfers have no counterpart in the paper.  Copies u_in_host to a context-owned
  * device state, steps, and copies the result to u_out_host (the two may be
  * the same buffer).  In 2D the last step's kernels run in up to 8 parts of
  * element rows, and each part's rows are copied back on a context-owned
@@ -218,7 +225,9 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** s
 crkfr_status crkfr_step_local(crkfr_ctx* ctx, const double* u_dev, double dt, void* stream);
 crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
 
-/* Adjoint of one 2D shallow-water step with fixed dt > 0 (standard form,
+/* Adjoint of the step of Sec. 3, Eq. crkfr.non.cons.final (the paper has
+ * no adjoint; it is this library's differentiation path).
+ * Adjoint of one 2D shallow-water step with fixed dt > 0 (standard form,
  * GL nodes, no source term, context not in subdomain mode; otherwise
  * CRKFR_ERR_UNSUPPORTED or CRKFR_ERR_STATE).  With u^{n+1} = S(u^n; b) the step of crkfr_step
  * and a scalar J: given ubar1 = dJ/du^{n+1} (device, state layout), writes
@@ -275,22 +284,26 @@ crkfr_status crkfr_limiter_alpha(crkfr_ctx* ctx, double* alpha_dev, void* stream
 /* Simulated time and the size of the last step taken (synchronises). */
 crkfr_status crkfr_get_time(crkfr_ctx* ctx, double* t_host, double* last_dt_host, void* stream);
 
-/* Reset the simulated time to t (asynchronous). */
+/* Reset the simulated time to t (asynchronous).  Bookkeeping only: the
+ * paper has no counterpart. */
 crkfr_status crkfr_set_time(crkfr_ctx* ctx, double t, void* stream);
 
 /* Read and clear the device status word: CRKFR_OK, or CRKFR_ERR_NONPHYSICAL
  * if any step since the last call produced h <= 0 or a non-finite value
- * (shallow water) or a non-finite value (advection).  Synchronises. */
+ * (shallow water: the admissible set of Sec. 2, h > 0) or a non-finite value
+ * (advection).  Synchronises. */
 crkfr_status crkfr_get_status(crkfr_ctx* ctx, void* stream);
 
-/* Number of kernel launches the context has issued (for accounting). */
+/* Number of kernel launches the context has issued (for accounting; the
+ * paper has no counterpart). */
 int64_t crkfr_launch_count(const crkfr_ctx* ctx);
 
 /* Kernel timing.  While enabled, the context records a CUDA event pair on
  * the launch stream around every kernel it launches; crkfr_profile_read
  * synchronises on the recorded events and returns, for one kernel kind, the
  * launches and summed device time (ms) since profiling was enabled.
- * Enabling (again) clears the accumulated values. */
+ * Enabling (again) clears the accumulated values.  Measurement aid: the
+ * paper has no counterpart. */
 typedef enum {
   CRKFR_KERNEL_STEP_1D = 0,    /* fused 1D step                              */
   CRKFR_KERNEL_LOCAL_2D = 1,   /* 2D element-local stages and face traces    */
@@ -298,13 +311,14 @@ typedef enum {
   CRKFR_KERNEL_RATE = 3,       /* wave-speed rate of a state (time step)     */
   CRKFR_KERNEL_COEF = 4,       /* static coefficient terms                   */
   CRKFR_KERNEL_ADJOINT_2D = 5, /* 2D adjoint step (face and local kernels)   */
-  CRKFR_KERNEL_INDICATOR = 6,  /* smoothness indicator of the 1D limiter      */
+  CRKFR_KERNEL_INDICATOR = 6,  /* smoothness indicator of the limiter (1D, 2D) */
   CRKFR_KERNEL_KINDS = 7
 } crkfr_kernel_kind;
 crkfr_status crkfr_profile_enable(crkfr_ctx* ctx, int32_t enable);
 crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms);
 
-/* Self-check of the two FP64 elementary operations the kernels implement
+/* (Testing aid; the paper has no counterpart.)
+ * Self-check of the two FP64 elementary operations the kernels implement
  * themselves instead of the IEEE division and square root: out[i] = 1/x[i]
  * (op 0) or sqrt(x[i]) (op 1) for n values, device arrays, computed by the
  * same device functions the step uses (FP32 seed built from the bit pattern,
@@ -352,7 +366,9 @@ crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n_elem, doub
  * coefficient field and, with the CFL step, its own time step).  A step of
  * the whole ensemble is one kernel launch per degree class over a work list
  * of (instance, 126-element tile) pairs running the same fused step as
- * crkfr_step, so instances of any size share the GPU.
+ * crkfr_step (Sec. 3, Eq. crkfr.non.cons.final; Sec. 5, Eq. time.step.2d per
+ * instance), so instances of any size share the GPU.  The batching itself
+ * has no counterpart in the paper.
  *
  * crkfr_batch_create: cfg->system a 1D system (cfg->degree ignored); n instances with degrees[i], n_elem[i] elements on
  * [lo[i], hi[i]] (host arrays).  Allocates the batch's device buffers.
@@ -401,7 +417,7 @@ crkfr_status crkfr_batch_get_status(crkfr_batch* batch, void* stream);
 int64_t crkfr_batch_launch_count(const crkfr_batch* batch);
 const char* crkfr_batch_last_error(const crkfr_batch* batch);
 
-/* Static strings. */
+/* Static strings (the paper has no counterpart). */
 const char* crkfr_error_string(crkfr_status status);
 const char* crkfr_last_error(const crkfr_ctx* ctx);
 
