@@ -181,6 +181,7 @@ class Solver:
                  source=None, source_coef=0.0):
         self.system, self.degree, self.family = system, degree, nodes
         self.source, self.source_coef = source, source_coef
+        self.limiter = (None, 0.0)
         self.M = NVARS[system]
         self.dim = DIM[system]
         self.n = degree + 1
@@ -219,6 +220,7 @@ class Solver:
         self._check(lib().crkfr_set_mesh(self.h, d, arr, (ctypes.c_double * d)(*lo),
                                          (ctypes.c_double * d)(*hi)))
         self.n_elem, self.lo, self.hi = n_elem, lo, hi
+        self.limiter = (None, 0.0)   # a new mesh switches the limiter off
         n = self.n
         if self.dim == 1:
             self.shape = (self.M, n_elem[0], n)
@@ -354,13 +356,14 @@ class Solver:
 
     def state_dict(self, u):
         """Checkpoint of a run: the state (a copy), the simulated time and
-        the configuration it belongs to.  The CFL step is recomputed from the
-        state at every call, so resuming from a checkpoint repeats the run."""
+        the configuration it belongs to (including the limiter setting).  The
+        CFL step and the limiter's coefficients are recomputed from the state
+        at every call, so resuming from a checkpoint repeats the run."""
         t, dt_last = self.time()
         return {"u": u.detach().clone(), "t": t, "dt_last": dt_last, "system": self.system,
                 "degree": self.degree, "nodes": self.family, "n_elem": list(self.n_elem),
                 "lo": list(self.lo), "hi": list(self.hi), "source": self.source,
-                "source_coef": self.source_coef}
+                "source_coef": self.source_coef, "limiter": list(self.limiter)}
 
     def load_state_dict(self, sd, u):
         """Restore a checkpoint into the device tensor u and the context's
@@ -372,6 +375,9 @@ class Solver:
                 raise ValueError(f"checkpoint {k} {sd[k]!r} differs from {want!r}")
         if list(sd["n_elem"]) != list(self.n_elem):
             raise ValueError("checkpoint mesh differs")
+        mode, alpha = sd.get("limiter", (None, 0.0))
+        if (mode, float(alpha)) != self.limiter:
+            self.set_limiter(mode, alpha)
         u.copy_(sd["u"])
         self.set_time(sd["t"])
         return u
@@ -393,6 +399,7 @@ class Solver:
         mesh): 'blend' (smoothness indicator), 'fixed' (alpha for every
         element) or None (off)."""
         self._check(lib().crkfr_set_limiter(self.h, self.LIMITERS[mode], float(alpha)))
+        self.limiter = (mode, float(alpha))
 
     def limiter_alpha(self):
         """alpha_e of the last limited step (cuda float64 tensor: (E,) in 1D,

@@ -326,3 +326,22 @@ def test_full_size_limited_workload_sampled(crk):
         out = lim.step(_patch(u, yy, xx), _patch(b[None], yy, xx)[0], dt)
         assert rel_l2(got[:, yy, xx], out[:, 2, 2]) < TOL_STEP, (yy, xx)
         assert abs(alpha[yy, xx] - lim.last_alpha[2, 2]) < 1e-12
+
+
+def test_checkpoint_resume_with_the_limiter(crk):
+    """state_dict of a limited run carries the limiter setting: a fresh
+    context loaded from it (limiter not set by hand) repeats the run bitwise."""
+    N, E = 3, 10
+    u, b, dx, dy = dam(N, E, E)
+    s1 = solver(crk, "swe2d", N, "gll", E, E, b, cs=0.1)
+    s1.set_limiter("blend")
+    d1 = to_dev(u)
+    s1.step(d1, 0.0, 5)
+    sd = s1.state_dict(d1)
+    s1.step(d1, 0.0, 5)
+    s2 = solver(crk, "swe2d", N, "gll", E, E, b, cs=0.1)
+    d2 = to_dev(np.zeros_like(u))
+    s2.load_state_dict(sd, d2)
+    assert s2.limiter == ("blend", 0.0)
+    s2.step(d2, 0.0, 5)
+    assert np.array_equal(to_host(d1), to_host(d2))
