@@ -131,6 +131,24 @@ def test_config1_to_final_time(crk):
     assert err < 1e-6
 
 
+@pytest.mark.parametrize("N", [2, 3])
+def test_config1_design_order_on_gpu(crk, N):
+    """The first configuration's convergence study on the GPU: E = 25, 50,
+    100, 200, CFL 0.5, T = 1, L2 error against the characteristics solution;
+    the observed order on the finest pair is at least N + 1 - 0.3."""
+    sc = SineCoefficient(0.5)
+    errs = []
+    for E in (25, 50, 100, 200):
+        v, a, dx = varadv_case(N, "gl", E)
+        s = solver(crk, "varadv1d", N, "gl", E, 0.0, 1.0, a)
+        dv = to_dev(v)
+        s.advance(dv, 1.0)
+        errs.append(l2_error_1d(to_host(dv)[0], lambda x: np.sin(2 * np.pi * sc.foot(x, 1.0)),
+                                0.0, dx, Basis(N).xi))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > N + 1 - 0.3, (errs, rates)
+
+
 @pytest.fixture(scope="module")
 def config2(crk):
     N, E = 4, 100000
