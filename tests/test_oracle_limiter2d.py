@@ -142,13 +142,15 @@ def test_indicator_2d(N):
     assert np.all(a[:, 5] > 0.9) and np.all(a[:, :4] == 0.0) and np.all(a[:, 7:] == 0.0)
 
 
-@pytest.mark.parametrize("alpha", [None, 0.4])
-def test_well_balanced_lake_at_rest_with_2d_limiter(alpha):
+@pytest.mark.parametrize("alpha,Cf", [(None, 0.0), (0.4, 0.0), (None, 2.0)])
+def test_well_balanced_lake_at_rest_with_2d_limiter(alpha, Cf):
+    from oracle.sources import ChezyFriction
     N = 3
     bs, x, y, dx, dy = grid(N, 6, 5, "gll")
     b = 0.3 * np.exp(-((x - 0.4) ** 2 + (y - 0.5) ** 2) / (2 * 0.08 ** 2)) + np.where(x > 0.7, 0.2, 0.0)
     u0 = np.stack([1.0 - b, np.zeros_like(b), np.zeros_like(b)])
-    sch = Scheme2D(ShallowWater2DWB(G), N, dx, dy, family="gll")
+    sch = Scheme2D(ShallowWater2DWB(G), N, dx, dy, family="gll",
+                   source=ChezyFriction(Cf) if Cf else None)
     lim = Blending2D(sch, alpha=alpha)
     u = u0.copy()
     for _ in range(8):
