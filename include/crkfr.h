@@ -326,6 +326,27 @@ crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches,
 crkfr_status crkfr_math_check(const double* x_dev, double* out_dev, int64_t n, int32_t op,
                               void* stream);
 
+/* (Measurement aid; the paper has no counterpart.)
+ * FP64 throughput probe: the peak rates the step kernels' rooflines are
+ * measured against.  One launch of `blocks` blocks of CRKFR_PROBE_BLOCK
+ * threads; every thread runs `iters` loop iterations of independent FP64
+ * dependency chains (issue-bound, not latency-bound):
+ *   mode 0: 8 FMA chains per thread on the FP64 pipe of the CUDA cores;
+ *   mode 1: 4 chains of the FP64 tensor-core instruction mma.sync m8n8k4
+ *           (8 x 8 x 4 FMAs per warp instruction) per warp;
+ *   mode 2: both in every loop iteration (shows whether they share a unit).
+ * sink_dev: device array of blocks * CRKFR_PROBE_BLOCK doubles, written
+ * (keeps the work live).  *flops: the FP64 flops the launch performs (an
+ * FMA counts 2).  Asynchronous on `stream`; the caller times it with events.
+ * Limits: 1 <= blocks <= CRKFR_PROBE_MAX_BLOCKS, 1 <= iters <=
+ * CRKFR_PROBE_MAX_ITERS (at most about 2 s of work); otherwise
+ * CRKFR_ERR_ARG without a launch. */
+#define CRKFR_PROBE_BLOCK 256
+#define CRKFR_PROBE_MAX_BLOCKS 9728
+#define CRKFR_PROBE_MAX_ITERS 65536
+crkfr_status crkfr_fp64_probe(int32_t mode, int32_t blocks, int32_t iters, double* sink_dev,
+                              double* flops, void* stream);
+
 /* crkfr_step_1d_noalloc: crkfr_step for a 1D system without any device
  * memory allocation.  The paper has no counterpart to this entry point; it
  * concerns memory handling only.

@@ -22,7 +22,7 @@ LIBNAME = "libcrkfr.so"
 
 SOURCES = ["api.cu", "kernels_1d.cu", "kernels_2d.cu", "kernels_imex.cu", "kernels_wb.cu",
            "kernels_limit.cu", "kernels_limit2d.cu", "kernels_limit2d_wb.cu", "noalloc.cu", "batch.cu",
-           "kernels_adj2d.cu", "basis.cpp"]
+           "kernels_adj2d.cu", "probe.cu", "basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 

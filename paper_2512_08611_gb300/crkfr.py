@@ -87,6 +87,7 @@ SIGNATURES = {
     "crkfr_limiter_alpha": (_I32, [_P, _P, _P]),
     "crkfr_profile_read": (_I32, [_P, _I32, _PI64, _PD]),
     "crkfr_math_check": (_I32, [_P, _P, _I64, _I32, _P]),
+    "crkfr_fp64_probe": (_I32, [_I32, _I32, _I32, _P, _PD, _P]),
     "crkfr_step_1d_noalloc": (_I32, [ctypes.POINTER(Config), _I64, _D, _D, _P, _P, _P, _D, _I64,
                                      _P]),
     "crkfr_batch_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(Config), _I32,
@@ -150,6 +151,36 @@ def math_check(x, op):
     if st != CRKFR_OK:
         raise CrkfrError(st, lib().crkfr_error_string(st).decode())
     return out
+
+
+def fp64_probe(mode, blocks=None, iters=4096, repeats=5):
+    """FP64 throughput of this GPU in TFLOP/s (crkfr_fp64_probe): 'fma' (the
+    FP64 pipe of the CUDA cores), 'mma' (mma.sync m8n8k4 on the tensor
+    cores) or 'both' interleaved.  Best of `repeats` launches timed with CUDA
+    events on the current stream, after one warm-up launch."""
+    import torch
+    m = {"fma": 0, "mma": 1, "both": 2}[mode]
+    if blocks is None:
+        blocks = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    flops = ctypes.c_double(0.0)
+    stream = torch.cuda.current_stream()
+    best = None
+    for r in range(repeats + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = lib().crkfr_fp64_probe(m, int(blocks), int(iters), ctypes.c_void_p(sink.data_ptr()),
+                                    ctypes.byref(flops), _stream())
+        e1.record(stream)
+        if st != CRKFR_OK:
+            raise CrkfrError(st, lib().crkfr_error_string(st).decode())
+        e1.synchronize()
+        if r > 0:
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    if not torch.isfinite(sink).all():
+        raise RuntimeError("probe produced non-finite values")
+    return flops.value / (best * 1e-3) / 1e12
 
 
 def step_1d_noalloc(system, degree, n_elem, lo, hi, c, u_in, u_out, dt=0.0, nsteps=1,

@@ -146,3 +146,16 @@ def test_well_balanced_systems_configure_like_standard(crk, system):
 def test_explicit_cfl_number_is_used(crk):
     from paper_2512_08611_gb300.crkfr import Solver
     assert Solver("swe1d", 3, cfl_number=0.05).cfl() == 0.05
+
+
+def test_fp64_probe_refuses_bad_arguments_without_a_launch(crk):
+    """Out-of-range modes, grid or loop sizes and null pointers return
+    CRKFR_ERR_ARG before any CUDA call (runs without a GPU)."""
+    L = crk.lib()
+    f = ctypes.c_double(-1.0)
+    sink = ctypes.c_void_p(16)   # never dereferenced: the checks come first
+    for mode, blocks, iters in ((3, 1, 1), (-1, 1, 1), (0, 0, 1), (0, 9729, 1), (0, 1, 0),
+                                (0, 1, 65537)):
+        assert L.crkfr_fp64_probe(mode, blocks, iters, sink, ctypes.byref(f), None) == -1
+    assert L.crkfr_fp64_probe(0, 1, 1, None, ctypes.byref(f), None) == -1
+    assert L.crkfr_fp64_probe(0, 1, 1, sink, None, None) == -1
