@@ -513,6 +513,10 @@ def run_ours(args, wl):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and wl.name == "swe2d" and not args.no_adjoint:
+        # the metric's third part: the adjoint's cost against the forward run
+        a = measure_adjoint(crkfr)
+        out["adjoint"] = {k: v for k, v in a.items() if k != "dof"}
     if rank == 0 and world == 1 and not args.no_cpu:
         value_cpu, el_cpu, procs, patch, dof = oracle_on_all_cores(wl, 15.0, 2, 0)
         out["cpu_baseline"] = {
@@ -648,20 +652,15 @@ def run_ensemble(args):
         "gpu_launches": launches, "clocks": clk}))
 
 
-def run_adjoint(args):
+def measure_adjoint(crkfr, E=256, N=3, L=100.0, nsteps=200, every=20):
     """Gradient of the final surface misfit w.r.t. the bathymetry on the 2D
-    256 x 256, N = 3 mesh: 200 fixed steps, checkpoints every 20; reports the
-    cost of the adjoint relative to the forward run."""
+    E x E, N = 3 mesh: nsteps fixed steps, checkpoints every `every` steps,
+    the backward pass recomputing each segment with recorded steps.  Returns
+    the forward and backward times (CUDA events) and the per-step costs."""
     import torch
-    from paper_2512_08611_gb300.build import build_library
-    build_library()
-    from oracle.basis import Basis  # noqa: F401  (not used on the timed path)
-    from paper_2512_08611_gb300 import crkfr
     from paper_2512_08611_gb300.adjoint import (BathymetryToState, quadrature_weights,
                                                 surface_misfit)
     from paper_2512_08611_gb300.workloads import SWE2DInput, accept_seed
-    torch.cuda.set_device(0)
-    E, N, L, nsteps, every = 256, 3, 100.0, 200, 20
     s = crkfr.Solver("swe2d", N, gravity=G, cfl_safety=0.5)
     s.set_mesh([E, E], [0.0, 0.0], [L, L])
     x, y = s.positions()
@@ -692,24 +691,38 @@ def run_adjoint(args):
     prof = s.profile_read()
     s.profile(False)
     fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    n_adj = prof.get("adjoint_2d", (0, 0.0))
-    n_loc = prof.get("local_2d", (0, 0.0))
-    n_face = prof.get("face_2d", (0, 0.0))
-    # per step: forward = local + face; adjoint step = local (traces) + adjoint kernels
-    fwd_step = (n_loc[1] / max(n_loc[0], 1)) + (n_face[1] / max(n_face[0], 1))
-    adj_step = (n_loc[1] / max(n_loc[0], 1)) + n_adj[1] / max(n_adj[0], 1)
-    dof = 3 * E * E * (N + 1) ** 2
+    n_adj, ms_adj = prof.get("adjoint_2d", (0, 0.0))
+    return {"workload": f"adjoint-swe2d-{E}x{E}-N{N}-{nsteps}steps-ckpt{every}",
+            "loss": "1/2 sum w (h + b - target)^2 at T", "dt": dt,
+            "forward_ms": fwd, "backward_ms": bwd,
+            "backward_over_forward": bwd / fwd,
+            "forward_step_ms": fwd / nsteps,
+            "adjoint_step_ms": ms_adj / max(n_adj, 1),
+            "adjoint_step_over_forward_step": (ms_adj / max(n_adj, 1)) / (fwd / nsteps),
+            "backward": "segments recomputed from checkpoints with recorded steps "
+                        "(face traces and stage values kept), adjoint steps read the records",
+            "gradient_norm": float(bb.grad.norm()),
+            "dof": 3 * E * E * (N + 1) ** 2}
+
+
+def run_adjoint(args):
+    """The adjoint workload alone: cost of the adjoint relative to the forward
+    run (Sec. 3, Eq. crkfr.non.cons.final reversed)."""
+    import torch
+    from paper_2512_08611_gb300.build import build_library
+    build_library()
+    from paper_2512_08611_gb300 import crkfr
+    torch.cuda.set_device(0)
+    nsteps = 200
+    a = measure_adjoint(crkfr, nsteps=nsteps)
     print(json.dumps({
-        "metric": METRIC, "value": dof * nsteps / (bwd / 1e3), "unit": "DoF-updates/s (adjoint)",
-        "n_gpus": 1, "steps": nsteps, "warmup": 1, "ms_per_step": bwd / nsteps,
+        "metric": METRIC, "value": a["dof"] * nsteps / (a["backward_ms"] / 1e3),
+        "unit": "DoF-updates/s (adjoint)",
+        "n_gpus": 1, "steps": nsteps, "warmup": 1, "ms_per_step": a["backward_ms"] / nsteps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "adjoint-swe2d-256x256-N3-200steps-ckpt20",
-                   "loss": "1/2 sum w (h + b - target)^2 at T", "dt": dt},
-        "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
-        "adjoint_step_over_forward_step": adj_step / fwd_step,
-        "adjoint_step_ms": adj_step, "forward_step_ms": fwd_step,
-        "gradient_norm": float(bb.grad.norm())}))
+        "config": {"workload": a["workload"], "loss": a["loss"], "dt": a["dt"]},
+        **{k: v for k, v in a.items() if k not in ("workload", "loss", "dt", "dof")}}))
 
 
 def main():
@@ -726,6 +739,8 @@ def main():
                     help="elements per side (2D) or elements (1D); profiling of small cases")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint measurement of the default workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

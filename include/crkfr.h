@@ -242,6 +242,41 @@ crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
 crkfr_status crkfr_step_adjoint(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
                                 double* ubar0_dev, double* bbar_dev, double dt, void* stream);
 
+/* Recorded steps for the adjoint of Sec. 3, Eq. crkfr.non.cons.final (the
+ * paper has no adjoint; this is this library's differentiation path).  A
+ * reverse pass that recomputes a segment of forward steps from a checkpoint
+ * can keep, for each step, what the adjoint step would otherwise recompute:
+ * the face traces of u^n (the Riemann problems' inputs, Eqs. numflux.cons,
+ * good.numflux.non.cons) and the inner stage values 1..S-1 of Eq.
+ * crkfr.non.cons.final.  Same contexts as crkfr_step_adjoint.
+ *
+ * crkfr_record_size: *count = doubles of one step record (x- and y-face
+ * traces and stage values: 14 n (2 Ex Ey + 2 Ex) + 3 (S-1) Ex Ey n^2 with
+ * n = N+1 and S the stages of the degree's tableau); CRKFR_ERR_STATE before
+ * crkfr_set_mesh of a 2D mesh.
+ *
+ * crkfr_step_record: with advance = 1, one step of u_dev in place with the
+ * fixed dt > 0 (as crkfr_step with nsteps = 1, advancing the simulated
+ * time), whose element-local kernel writes the record of the step from the
+ * input state into record_dev; with advance = 0, only the record of the
+ * step from u_dev is written (u_dev and the time are unchanged).  record_dev:
+ * device, caller-owned, crkfr_record_size doubles, not overlapping u_dev; its
+ * layout is the library's and may change between versions.
+ *
+ * crkfr_step_adjoint_recorded: crkfr_step_adjoint of the step from u_dev with
+ * step dt, reading the face traces and stage values from record_dev (written
+ * by crkfr_step_record for the same u_dev, dt and coefficients) instead of
+ * recomputing them: the forward element-local kernel is not launched and the
+ * reverse local kernel does not recompute the stages.  Arguments and errors
+ * otherwise as crkfr_step_adjoint. */
+crkfr_status crkfr_record_size(const crkfr_ctx* ctx, int64_t* count);
+crkfr_status crkfr_step_record(crkfr_ctx* ctx, double* u_dev, double dt, double* record_dev,
+                               int32_t advance, void* stream);
+crkfr_status crkfr_step_adjoint_recorded(crkfr_ctx* ctx, const double* u_dev,
+                                         const double* record_dev, const double* ubar1_dev,
+                                         double* ubar0_dev, double* bbar_dev, double dt,
+                                         void* stream);
+
 /* Subcell blending limiter of the step (Sec. 4; in 2D its tensor-product
  * extension).  Each element blends the cRK-FR update with a first-order
  * finite-volume update on its subcells of widths w_p dx (x w_q dy in 2D)

@@ -8,7 +8,11 @@ fixed dt is applied nsteps times, and the state u_T is returned.  Backward:
 the states are recomputed segment by segment from checkpoints stored every
 ``every`` steps, and the adjoint steps run in reverse, accumulating
 dJ/db through the static terms of the step (g b_x, g b_y, the face jumps of
-b) and, at the end, through the initial condition (h0 = eta0 - b).
+b) and, at the end, through the initial condition (h0 = eta0 - b).  With
+``recorded`` (the default) the recomputation records each step's face traces
+and inner stage values (crkfr_step_record, one record per step of a segment
+held at a time) and the adjoint steps read them back
+(crkfr_step_adjoint_recorded) instead of recomputing them.
 
 ``BathymetryToState`` is a torch.autograd.Function, so any differentiable
 torch expression of u_T and b can serve as J; ``surface_misfit`` is the
@@ -36,7 +40,7 @@ class BathymetryToState(torch.autograd.Function):
     """u_T(b) for a 2D swe Solver (GL nodes) with fixed dt."""
 
     @staticmethod
-    def forward(ctx, b, solver, eta0, dt, nsteps, every):
+    def forward(ctx, b, solver, eta0, dt, nsteps, every, recorded=True):
         solver.set_coefficients(b.detach().contiguous())
         u = initial_state(eta0, b.detach()).contiguous()
         checkpoints = [u.clone()]
@@ -48,6 +52,7 @@ class BathymetryToState(torch.autograd.Function):
             if done < nsteps:
                 checkpoints.append(u.clone())
         ctx.solver, ctx.dt, ctx.nsteps, ctx.every = solver, dt, nsteps, every
+        ctx.recorded = recorded
         ctx.checkpoints = checkpoints
         ctx.b = b.detach().contiguous()
         return u
@@ -60,19 +65,32 @@ class BathymetryToState(torch.autograd.Function):
         bbar = torch.zeros_like(ctx.b)
         other = torch.empty_like(ubar)
         starts = list(range(0, nsteps, every))
+        records = s.new_records(min(every, nsteps)) if ctx.recorded else None
         for seg, start in reversed(list(enumerate(starts))):
             k = min(every, nsteps - start)
             states = [ctx.checkpoints[seg].clone()]
-            for _ in range(k - 1):
+            for j in range(k - 1):
                 x = states[-1].clone()
-                s.step(x, dt, 1)
+                if records is None:
+                    s.step(x, dt, 1)
+                else:
+                    s.step_record(x, dt, records[j])
                 states.append(x)
-            for x in reversed(states):
-                s.step_adjoint(x, ubar, dt, ubar0=other, bbar=bbar)
-                ubar, other = other, ubar
+            if records is None:
+                for x in reversed(states):
+                    s.step_adjoint(x, ubar, dt, ubar0=other, bbar=bbar)
+                    ubar, other = other, ubar
+            else:
+                # the recomputation recorded the steps from states 0..k-2;
+                # record the last one without stepping
+                s.step_record(states[-1], dt, records[k - 1], advance=False)
+                for j in reversed(range(k)):
+                    s.step_adjoint_recorded(states[j], records[j], ubar, dt, ubar0=other,
+                                            bbar=bbar)
+                    ubar, other = other, ubar
         # initial condition h0 = eta0 - b
         bbar -= ubar[0]
-        return bbar, None, None, None, None, None
+        return bbar, None, None, None, None, None, None
 
 
 def surface_misfit(u, b, target, weights):

@@ -74,6 +74,9 @@ SIGNATURES = {
     "crkfr_step_local": (_I32, [_P, _P, _D, _P]),
     "crkfr_step_faces": (_I32, [_P, _P, _P]),
     "crkfr_step_adjoint": (_I32, [_P, _P, _P, _P, _P, _D, _P]),
+    "crkfr_record_size": (_I32, [_P, _PI64]),
+    "crkfr_step_record": (_I32, [_P, _P, _D, _P, _I32, _P]),
+    "crkfr_step_adjoint_recorded": (_I32, [_P, _P, _P, _P, _P, _P, _D, _P]),
     "crkfr_get_time": (_I32, [_P, _PD, _PD, _P]),
     "crkfr_set_time": (_I32, [_P, _D, _P]),
     "crkfr_get_status": (_I32, [_P, _P]),
@@ -375,6 +378,40 @@ class Solver:
                                              self._dev(ubar0, self.shape),
                                              self._dev(bbar, self.coef_shape), float(dt),
                                              _stream()))
+        return ubar0, bbar
+
+    def record_size(self):
+        """Doubles of one step record (crkfr_record_size)."""
+        n = ctypes.c_int64()
+        self._check(lib().crkfr_record_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def new_records(self, count):
+        """``count`` step records, one per row of a zeroed device array (a
+        record leaves the two unused sides of the y-trace halo rows
+        unwritten)."""
+        import torch
+        return torch.zeros((count, self.record_size()), dtype=torch.float64, device="cuda")
+
+    def step_record(self, u, dt, record, advance=True):
+        """One fixed step of u in place (advance) or none, writing the record
+        of the step from the input state (crkfr_step_record)."""
+        self._check(lib().crkfr_step_record(self.h, self._dev(u, self.shape), float(dt),
+                                            self._dev(record, (self.record_size(),)),
+                                            1 if advance else 0, _stream()))
+
+    def step_adjoint_recorded(self, u, record, ubar1, dt, ubar0=None, bbar=None):
+        """step_adjoint of the step from u whose record crkfr_step_record
+        wrote (crkfr_step_adjoint_recorded).  Returns (ubar0, bbar)."""
+        import torch
+        if ubar0 is None:
+            ubar0 = torch.empty_like(ubar1)
+        if bbar is None:
+            bbar = torch.zeros(self.coef_shape, dtype=torch.float64, device=u.device)
+        self._check(lib().crkfr_step_adjoint_recorded(
+            self.h, self._dev(u, self.shape), self._dev(record, (self.record_size(),)),
+            self._dev(ubar1, self.shape), self._dev(ubar0, self.shape),
+            self._dev(bbar, self.coef_shape), float(dt), _stream()))
         return ubar0, bbar
 
     def time(self):

@@ -873,8 +873,12 @@ crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
   return CRKFR_OK;
 }
 
-crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* ubar1, double* ubar0,
-                                double* bbar, double dt, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The contexts the adjoint (and the recorded step) support.
+crkfr_status adjoint_context(crkfr_ctx* c) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
   if (c->dim != 2 || c->cfg.system != CRKFR_SYS_SWE_2D)
@@ -886,6 +890,49 @@ crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* uba
   if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "no adjoint in subdomain mode");
   if (c->limit_mode != CRKFR_LIMITER_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step has no limiter");
+  return CRKFR_OK;
+}
+
+// Parts of a step record: x-face traces, y-face traces (with the two halo
+// rows), inner stage values 1..S-1 (doubles each).
+void record_parts(const crkfr_ctx* c, int64_t* ntx, int64_t* nty, int64_t* nst) {
+  const int64_t n = c->basis.n, Ne = c->Ex * c->Ey;
+  *ntx = 7 * 2 * Ne * n;
+  *nty = 7 * 2 * (c->Ey + 2) * c->Ex * n;
+  *nst = (int64_t)(tab_stages(c->cfg.degree) - 1) * 3 * Ne * n * n;
+}
+
+// The adjoint kernels of one step whose forward traces of u^n are in
+// (trx, try_) and whose stage values are in `stages` (null: recomputed).
+crkfr_status launch_adjoint(crkfr_ctx* c, const double* u, const double* ubar1, double* ubar0,
+                            double* bbar, double dt, const double* trx, const double* try_,
+                            const double* stages, cudaStream_t s) {
+  Launch2DAdj A{};
+  A.N = c->cfg.degree;
+  A.Ex = c->Ex;
+  A.Ey = c->Ey;
+  A.dt = dt;
+  A.u = u;
+  A.ubar1 = ubar1;
+  A.ubar0 = ubar0;
+  A.bbar = bbar;
+  A.snode = c->d_snode;
+  A.sface = c->d_sface;
+  A.trx = trx;
+  A.try_ = try_;
+  A.atrx = c->d_atrx;
+  A.atry = c->d_atry;
+  A.gbar = c->d_gbar;
+  A.stages = stages;
+  A.tab = c->tab;
+  int e = timed(c, CRKFR_KERNEL_ADJOINT_2D, s, [&] { return launch_adjoint_2d(A, s); });
+  if (e) return cuda_fail(c, e, "2D adjoint kernels");
+  c->launches += 2;
+  return CRKFR_OK;
+}
+
+crkfr_status adjoint_args(crkfr_ctx* c, const double* u, const double* ubar1, double* ubar0,
+                          double* bbar, double dt) {
   if (!u || !ubar1 || !ubar0 || !bbar) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
   const size_t bytes = sizeof(double) * c->n_state;
@@ -901,6 +948,18 @@ crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* uba
       return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
     }
   }
+  return CRKFR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* ubar1, double* ubar0,
+                                double* bbar, double dt, void* stream) {
+  crkfr_status st = adjoint_context(c);
+  if (st == CRKFR_OK) st = adjoint_args(c, u, ubar1, ubar0, bbar, dt);
+  if (st != CRKFR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   // forward traces of u^n: the local kernel in its residual form (same traces,
   // no time bookkeeping)
@@ -912,27 +971,77 @@ crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* uba
   L.u_in = u;
   int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
   if (e) return cuda_fail(c, e, "2D local kernel");
-  Launch2DAdj A{};
-  A.N = c->cfg.degree;
-  A.Ex = c->Ex;
-  A.Ey = c->Ey;
-  A.dt = dt;
-  A.u = u;
-  A.ubar1 = ubar1;
-  A.ubar0 = ubar0;
-  A.bbar = bbar;
-  A.snode = c->d_snode;
-  A.sface = c->d_sface;
-  A.trx = c->d_trx;
-  A.try_ = c->d_try;
-  A.atrx = c->d_atrx;
-  A.atry = c->d_atry;
-  A.gbar = c->d_gbar;
-  A.tab = c->tab;
-  e = timed(c, CRKFR_KERNEL_ADJOINT_2D, s, [&] { return launch_adjoint_2d(A, s); });
-  if (e) return cuda_fail(c, e, "2D adjoint kernels");
-  c->launches += 3;
+  c->launches += 1;
+  return launch_adjoint(c, u, ubar1, ubar0, bbar, dt, c->d_trx, c->d_try, nullptr, s);
+}
+
+crkfr_status crkfr_record_size(const crkfr_ctx* c, int64_t* count) {
+  if (!c || !count) return CRKFR_ERR_ARG;
+  if (c->dim != 2) return CRKFR_ERR_STATE;
+  int64_t tx, ty, ns;
+  record_parts(c, &tx, &ty, &ns);
+  *count = tx + ty + ns;
   return CRKFR_OK;
+}
+
+crkfr_status crkfr_step_record(crkfr_ctx* c, double* u, double dt, double* record,
+                               int32_t advance, void* stream) {
+  crkfr_status st = adjoint_context(c);
+  if (st != CRKFR_OK) return st;
+  if (!u || !record) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
+  if (advance != 0 && advance != 1) return fail(c, CRKFR_ERR_ARG, "advance must be 0 or 1");
+  int64_t tx, ty, ns;
+  record_parts(c, &tx, &ty, &ns);
+  const size_t rbytes = sizeof(double) * (size_t)(tx + ty + ns);
+  const size_t ubytes = sizeof(double) * c->n_state;
+  const char *a = (const char*)u, *r = (const char*)record;
+  if (a < r + rbytes && r < a + ubytes) return fail(c, CRKFR_ERR_ARG, "u and record overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  Launch2D L = make2d(c);
+  L.trx = record;
+  L.try_ = record + tx;
+  L.stages = record + tx + ty;
+  L.u_in = u;
+  L.u_out = u;
+  StepCtl ctl{};
+  ctl.dt_fixed = dt;
+  ctl.cs_cfl = c->cfg.cfl_safety * c->cfl;
+  ctl.t_end = std::numeric_limits<double>::infinity();
+  if (!advance) {
+    // traces and stages only (residual form: no time bookkeeping, u unchanged)
+    ctl.residual = 1;
+    L.ctl = ctl;
+    int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d_stages(L, s); });
+    if (e) return cuda_fail(c, e, "2D local kernel");
+    c->launches += 1;
+    return CRKFR_OK;
+  }
+  ctl.slot_read = (int)(c->nstep % 3);
+  ctl.slot_write = (int)((c->nstep + 1) % 3);
+  ctl.slot_reset = (int)((c->nstep + 2) % 3);
+  ctl.tslot = (int)(c->nstep % 2);
+  L.ctl = ctl;
+  int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d_stages(L, s); });
+  if (e) return cuda_fail(c, e, "2D local kernel");
+  e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+  if (e) return cuda_fail(c, e, "2D face kernel");
+  c->launches += 2;
+  c->nstep += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_step_adjoint_recorded(crkfr_ctx* c, const double* u, const double* record,
+                                         const double* ubar1, double* ubar0, double* bbar,
+                                         double dt, void* stream) {
+  crkfr_status st = adjoint_context(c);
+  if (st == CRKFR_OK) st = adjoint_args(c, u, ubar1, ubar0, bbar, dt);
+  if (st != CRKFR_OK) return st;
+  if (!record) return fail(c, CRKFR_ERR_ARG, "null argument");
+  int64_t tx, ty, ns;
+  record_parts(c, &tx, &ty, &ns);
+  return launch_adjoint(c, u, ubar1, ubar0, bbar, dt, record, record + tx, record + tx + ty,
+                        (cudaStream_t)stream);
 }
 
 crkfr_status crkfr_get_time(crkfr_ctx* c, double* t_host, double* last_dt_host, void* stream) {

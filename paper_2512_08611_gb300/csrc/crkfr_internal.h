@@ -210,6 +210,9 @@ struct Launch2D {
   // (for the face kernel row_begin a multiple of 8, row_end a multiple of 8
   // or Ey): the whole mesh by default
   int64_t row_begin, row_end;
+  // recorded steps (crkfr_step_record): the local kernel also stores the
+  // inner stage values 1..S-1, [S-1][3][Ey][Ex][n][n]
+  double* stages;
 };
 // Adjoint of one 2D step (kernels_adj2d.cu); the forward local kernel must
 // have written the traces of u^n first.
@@ -228,9 +231,15 @@ struct Launch2DAdj {
   double* atrx;          // adjoint traces [7][2][Ey][Ex][n]
   double* atry;          // adjoint traces [Ey][2][7][Ex][n]
   double* gbar;          // adjoint of the face jumps: [Ey][Ex][n] x faces, [Ey][Ex][n] y faces
+  // stage values 1..S-1 of the step from u^n, [S-1][3][Ey][Ex][n][n], as the
+  // forward local kernel stored them (crkfr_step_record); null: recompute
+  const double* stages;
   Tables tab;
 };
-int launch_adjoint_2d(const Launch2DAdj& A, void* stream);
+// the forward local kernel (standard form, GL or GLL, no source) that also
+// stores the inner stage values into L.stages (kernels_adj2d.cu)
+int launch_local_2d_stages(const Launch2D& L, void* stream);
+int launch_adjoint_2d(const Launch2DAdj& A, void* stream);   // A.stages null or not
 
 int launch_local_2d(const Launch2D& L, void* stream);
 int launch_local_2d_imex(const Launch2D& L, void* stream);   // kernels_imex.cu

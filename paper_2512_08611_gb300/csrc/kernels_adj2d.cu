@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "local_2d.cuh"
 
 namespace crkfr {
 namespace {
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(256) k_face_adj_2d(const Launch2DAdj A) {
   }
 }
 
-template <int N>
+template <int N, bool LOADED>
 __global__ void __launch_bounds__(kBlockAdj) k_local_adj_2d(const Launch2DAdj A) {
   constexpr int n = N + 1;
   constexpr int nn = n * n;
@@ -201,9 +202,21 @@ __global__ void __launch_bounds__(kBlockAdj) k_local_adj_2d(const Launch2DAdj A)
     gby[p] = A.snode[(Ne + ge) * nn + q * n + p];
   }
 
-  // ---- forward recompute of the stage values (row q) ----------------------
+  // ---- stage values (row q): loaded from the recorded step, or recomputed --
   double cur[S][3][n];
-  {
+  if constexpr (LOADED) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) cur[0][v][p] = u0[v][p];
+#pragma unroll
+    for (int i = 1; i < S; ++i)
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int p = 0; p < n; ++p)
+          cur[i][v][p] = A.stages[(((int64_t)(i - 1) * 3 + v) * Ne + ge) * nn + q * n + p];
+  } else {
     double Lp[S][3][n];
 #pragma unroll
     for (int i = 0; i < S; ++i) {
@@ -467,6 +480,28 @@ __global__ void __launch_bounds__(kBlockAdj) k_local_adj_2d(const Launch2DAdj A)
   }
 }
 
+template <int N>
+void launch_adjoint_t(const Launch2DAdj& A, unsigned fblocks, unsigned lblocks, cudaStream_t s) {
+  static_assert(Tab<N, false>::S == tab_stages(N), "one stage count for both kernels");
+  k_face_adj_2d<N><<<fblocks, 256, 0, s>>>(A);
+  if (A.stages)
+    k_local_adj_2d<N, true><<<lblocks, kBlockAdj, 0, s>>>(A);
+  else
+    k_local_adj_2d<N, false><<<lblocks, kBlockAdj, 0, s>>>(A);
+}
+
+template <int N, bool GLL>
+int launch_local_stages_t(const Launch2D& L, cudaStream_t s) {
+  constexpr int per_block = kWarpsLocal * (32 / (N + 1));
+  const int64_t blocks = (L.Ex * L.Ey + per_block - 1) / per_block;
+  if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
+  if (L.ctl.residual)
+    k_local_2d<N, GLL, true, false, false, false, true><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
+  else
+    k_local_2d<N, GLL, false, false, false, false, true><<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace
 
 int launch_adjoint_2d(const Launch2DAdj& A, void* stream) {
@@ -478,26 +513,30 @@ int launch_adjoint_2d(const Launch2DAdj& A, void* stream) {
   const int per_block = kWarpsAdj * (32 / n);
   const unsigned lblocks = (unsigned)((Ne + per_block - 1) / per_block);
   switch (A.N) {
-    case 1:
-      k_face_adj_2d<1><<<fblocks, 256, 0, s>>>(A);
-      k_local_adj_2d<1><<<lblocks, kBlockAdj, 0, s>>>(A);
-      break;
-    case 2:
-      k_face_adj_2d<2><<<fblocks, 256, 0, s>>>(A);
-      k_local_adj_2d<2><<<lblocks, kBlockAdj, 0, s>>>(A);
-      break;
-    case 3:
-      k_face_adj_2d<3><<<fblocks, 256, 0, s>>>(A);
-      k_local_adj_2d<3><<<lblocks, kBlockAdj, 0, s>>>(A);
-      break;
-    case 4:
-      k_face_adj_2d<4><<<fblocks, 256, 0, s>>>(A);
-      k_local_adj_2d<4><<<lblocks, kBlockAdj, 0, s>>>(A);
-      break;
+    case 1: launch_adjoint_t<1>(A, fblocks, lblocks, s); break;
+    case 2: launch_adjoint_t<2>(A, fblocks, lblocks, s); break;
+    case 3: launch_adjoint_t<3>(A, fblocks, lblocks, s); break;
+    case 4: launch_adjoint_t<4>(A, fblocks, lblocks, s); break;
     default:
       return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();
+}
+
+int launch_local_2d_stages(const Launch2D& L, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (L.row_begin != 0 || L.row_end != L.Ey || !L.stages) return (int)cudaErrorInvalidValue;
+  switch (L.N * 2 + (L.gll ? 1 : 0)) {
+    case 2: return launch_local_stages_t<1, false>(L, s);
+    case 3: return launch_local_stages_t<1, true>(L, s);
+    case 4: return launch_local_stages_t<2, false>(L, s);
+    case 5: return launch_local_stages_t<2, true>(L, s);
+    case 6: return launch_local_stages_t<3, false>(L, s);
+    case 7: return launch_local_stages_t<3, true>(L, s);
+    case 8: return launch_local_stages_t<4, false>(L, s);
+    case 9: return launch_local_stages_t<4, true>(L, s);
+  }
+  return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace crkfr

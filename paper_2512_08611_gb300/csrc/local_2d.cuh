@@ -44,8 +44,9 @@ constexpr int kTrFields = 7;
 // hu and hv), h^n, hu^n.  y-face trace fields: U_h, U_hu, U_hv, G_hu, G_hv,
 // h^n, hv^n.  (The time-averaged h fluxes are U_hu and U_hv.)
 
-template <int N, bool GLL, bool RES, bool IMEX, bool WB, bool LIMIT = false>
+template <int N, bool GLL, bool RES, bool IMEX, bool WB, bool LIMIT = false, bool STAGES = false>
 __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(const Launch2D L) {
+  static_assert(!(STAGES && (IMEX || WB || LIMIT)), "stages are recorded for the standard form");
   using TB = Tab<N, IMEX>;
   constexpr int n = N + 1;
   constexpr int nn = n * n;
@@ -132,6 +133,17 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
           Ss[i][0][p] = c * cur[1][p];
           Ss[i][1][p] = c * cur[2][p];
         }
+      }
+    }
+    if constexpr (STAGES) {
+      // recorded step: the adjoint reads the stage values instead of
+      // recomputing them (stage 0 is u^n itself)
+      if (i > 0 && active) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+          for (int p = 0; p < n; ++p)
+            L.stages[(((int64_t)(i - 1) * 3 + v) * Ne + ge) * nn + q * n + p] = cur[v][p];
       }
     }
     const double wi = TB::b(i) / TB::bref();
