@@ -603,6 +603,26 @@ def run_ensemble(args):
         dist.all_reduce(sm, op=dist.ReduceOp.SUM)
         ms, tot_dof = float(mx.item()), float(sm.item())
     launches = batch.launch_count() - n0
+    # time between kernels: the same steps without a graph with every kernel
+    # timed (their sum) against the graph's wall time, for the tuned shape
+    # and for one serial chain of launches
+    batch.set_tuning(tpb, order, 0)
+    u.copy_(u0)
+    batch.step(u, 0.0, args.warmup, graph=False)
+    batch.profile(True)
+    batch.step(u, 0.0, args.steps, graph=False)
+    n_k, kernel_ms = batch.profile_read()
+    batch.profile(False)
+    u.copy_(u0)
+    batch.step(u, 0.0, args.steps, graph=True)     # capture + warm-up
+    u.copy_(u0)
+    torch.cuda.synchronize()
+    ev0.record()
+    batch.step(u, 0.0, args.steps, graph=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_serial = ev0.elapsed_time(ev1)
+    batch.set_tuning(tpb, order, parallel)
     # looping the single-mesh step over the instances
     solvers, states = [], []
     for (N, E, lo, hi), x, b in zip(members, us, cs):
@@ -642,6 +662,19 @@ def run_ensemble(args):
         "looped": {"value": looped, "ms_per_step": ms_loop / args.steps,
                    "mode": "crkfr_step of K steps per instance, instances in sequence (rank 0)"},
         "speedup_vs_looped": (dof * args.steps / (ms / 1e3)) / looped,
+        "launch_gaps": {
+            "graph_ms_per_step": ms / args.steps,
+            "serial_graph_ms_per_step": ms_serial / args.steps,
+            "kernel_ms_per_step": kernel_ms / args.steps, "kernels_timed": n_k,
+            "gap_fraction_serial": 1.0 - kernel_ms / ms_serial,
+            "note": "kernel_ms: sum of every step kernel's duration (CUDA events, no graph, "
+                    "degree classes one after another); the serial graph runs the same "
+                    "kernels back to back, so its excess over the sum is the time between "
+                    "kernels that one persistent launch could remove"},
+        "fp64_ceiling": {
+            "flop_per_dof_update": flops_step / dof,
+            "dof_updates_per_s": FP64_PEAK_TFLOPS * 1e12 * dof / flops_step,
+            "max_ratio_over_looped": FP64_PEAK_TFLOPS * 1e12 * dof / flops_step / looped},
         "roofline": {"bound": "alu", "kernel": "k_step_1d_batch (all kernels of the step)",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,

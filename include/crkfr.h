@@ -42,7 +42,10 @@
  *   case they synchronise that stream only.
  * - Errors: every entry point returns a crkfr_status; nothing traps or
  *   throws across the ABI.  crkfr_last_error gives the context's last error
- *   text.  A context is not thread-safe; use one context per host thread.
+ *   text; crkfr_last_error(NULL) gives the calling host thread's last error
+ *   of a call that has no context to hold it (crkfr_create,
+ *   crkfr_batch_create, crkfr_step_1d_noalloc).  A context is not
+ *   thread-safe; use one context per host thread.
  */
 #ifndef CRKFR_H
 #define CRKFR_H
@@ -112,24 +115,53 @@ typedef struct {
                           von Neumann value (crkfr_get_cfl), which with a source is
                           that of the explicit part of SSP3-IMEX(4,3,3)              */
   double source_coef;  /* K or C_f, finite and >= 0; ignored without a source       */
+  /* Readings of the paper that are switches of the method (a zero-filled
+   * config selects the built default of each; any other value returns
+   * CRKFR_ERR_UNSUPPORTED, with the reason in crkfr_last_error(NULL)): */
+  int32_t rk;          /* order of the Runge-Kutta tableau of Eq. crkfr.non.cons.final:
+                          0 or the default order, N+1 without a source (forward Euler,
+                          HT(1,1,2) and SSP3-IMEX(4,3,3) explicit parts, classical RK4,
+                          Butcher's six-stage fifth-order method for N = 0..4) and 3
+                          with one (SSP3-IMEX(4,3,3), App. C)                       */
+  int32_t nc_face_mode; /* crkfr_nc_face: the face non-conservative terms (Sec. 3):
+                          only CRKFR_NC_FROZEN is built                               */
+  int32_t coef_dissipation; /* 0: the coefficient c (a or b) is static, no dissipation
+                          acts on it (built); 1: the literal augmented form w = (u, c)
+                          whose Rusanov term would let c drift (not built)            */
+  int32_t reserved;    /* must be 0                                                   */
 } crkfr_config;
+
+/* Face non-conservative terms of Sec. 3 when B depends on the evolving
+ * variables.  FROZEN: F^{nc,+-} = B(w^{n,+-}) W^{+-}, the B of Eq.
+ * good.numflux.non.cons frozen at t^n for both the numerical and the
+ * extrapolated term (the reading this library builds); LITERAL: the
+ * extrapolation under Eq. total.F.non.cons with stage values as printed;
+ * STAGEWISE: Eq. bad.numflux.non.cons stage by stage.  The last two keep
+ * every stage's traces; they exist in the CPU oracle, not here. */
+typedef enum {
+  CRKFR_NC_FROZEN = 0,
+  CRKFR_NC_LITERAL = 1,
+  CRKFR_NC_STAGEWISE = 2
+} crkfr_nc_face;
 
 /* Create a context for one system / degree / node family / source.  Runs
  * the library's von Neumann analysis of the scheme for linear advection when
  * cfg->cfl_number <= 0 (Sec. 5, under Eq. time.step.2d).  *out is set to NULL
- * on failure. */
+ * on failure, and crkfr_last_error(NULL) gives the reason. */
 crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg);
 
 /* Free the context and every device buffer it owns (synchronises the device).
  * Resource management only: the paper has no counterpart. */
 void crkfr_destroy(crkfr_ctx* ctx);
 
-/* Uniform periodic mesh (Sec. 2, Eqs. reference.element, ref.map).
+/* Uniform mesh (Sec. 2, Eqs. reference.element, ref.map).
  * dim must match the system (1 or 2); n_elem[dim] > 0 (Ex first, then Ey);
- * lo[dim] < hi[dim].  Allocates the context's device buffers (about
- * 6x the state size in 1D, 5x in 2D).  Invalidates the coefficients. */
+ * lo[dim] < hi[dim]; periodic_mask: bit d set = periodic in direction d.
+ * Only periodic meshes are built (periodic_mask = 1 in 1D, 3 in 2D;
+ * otherwise CRKFR_ERR_UNSUPPORTED).  Allocates the context's device buffers
+ * (about 6x the state size in 1D, 5x in 2D).  Invalidates the coefficients. */
 crkfr_status crkfr_set_mesh(crkfr_ctx* ctx, int32_t dim, const int64_t* n_elem,
-                            const double* lo, const double* hi);
+                            const double* lo, const double* hi, int32_t periodic_mask);
 
 /* Number of FP64 values of the state u (vars x nodes: (N+1)^dim nodal
  * values of the solution polynomial per element, Sec. 2, Eq. soln.poly) and
@@ -167,9 +199,13 @@ crkfr_status crkfr_residual(crkfr_ctx* ctx, const double* u_dev, double dt, doub
                             void* stream);
 
 /* Advance u_dev in place by nsteps >= 0 cRK-FR steps.  dt > 0: that fixed
- * step; dt <= 0: the step of Eq. time.step.2d recomputed on the device from
- * the current state before every step (no host synchronisation).  The
- * context accumulates simulated time on the device (crkfr_get_time). */
+ * step; dt <= 0 (or -inf): the step of Eq. time.step.2d recomputed on the
+ * device from the current state before every step (no host
+ * synchronisation); a NaN or +inf dt returns CRKFR_ERR_ARG.  The context
+ * accumulates simulated time on the device; the size of the last step
+ * taken, which in the CFL mode exists only on the device, is returned by
+ * crkfr_get_time (which synchronises), so that crkfr_step itself stays
+ * asynchronous. */
 crkfr_status crkfr_step(crkfr_ctx* ctx, double* u_dev, double dt, int64_t nsteps,
                         void* stream);
 
@@ -353,11 +389,12 @@ crkfr_status crkfr_profile_enable(crkfr_ctx* ctx, int32_t enable);
 crkfr_status crkfr_profile_read(crkfr_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms);
 
 /* (Testing aid; the paper has no counterpart.)
- * Self-check of the two FP64 elementary operations the kernels implement
+ * Self-check of the FP64 elementary operations the kernels implement
  * themselves instead of the IEEE division and square root: out[i] = 1/x[i]
- * (op 0) or sqrt(x[i]) (op 1) for n values, device arrays, computed by the
- * same device functions the step uses (FP32 seed built from the bit pattern,
- * one third-order refinement).  Lets a test bound their error. */
+ * (op 0), sqrt(x[i]) (op 1) or 1/sqrt(x[i]) (op 2) for n values, device
+ * arrays, computed by the same device functions the step uses (FP32 seed
+ * built from the bit pattern, one third-order refinement).  Lets a test
+ * bound their error. */
 crkfr_status crkfr_math_check(const double* x_dev, double* out_dev, int64_t n, int32_t op,
                               void* stream);
 
@@ -402,11 +439,18 @@ crkfr_status crkfr_fp64_probe(int32_t mode, int32_t blocks, int32_t iters, doubl
  * a uniform periodic mesh of n_elem elements on [lo, hi]; c_dev: the
  * coefficient field [elem][p]; u_in_dev, u_out_dev: the state
  * [var][elem][p], the same buffer or not overlapping at all; dt > 0: fixed
- * step, dt <= 0: the step of Sec. 5, Eq. time.step.2d recomputed before
- * every step; nsteps >= 0 (0 copies u_in to u_out).
+ * step, dt <= 0 (or -inf): the CFL step that crkfr_step uses, recomputed
+ * before every step; a NaN or +inf dt returns CRKFR_ERR_ARG; nsteps >= 0
+ * (0 copies u_in to u_out).
  * Limit: n_elem * (N+1) * (vars + 1) + 2 n_elem (plus alignment) must fit
  * the array, e.g. about 123,000 elements for shallow water at N = 4;
  * larger meshes return CRKFR_ERR_ARG without touching the GPU.
+ * This entry point cannot report a non-physical state: the kernels' flag
+ * (h <= 0 or a non-finite value) stays in the shared array and the next call
+ * clears it, and in the CFL mode such a state gives a zero step, so later
+ * steps leave it unchanged and the call still returns CRKFR_OK.  Callers
+ * that need the check use crkfr_step and crkfr_get_status, or test the
+ * output themselves.
  * The first call on a device looks up the device address of the array
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the array and the array
@@ -471,9 +515,20 @@ crkfr_status crkfr_batch_autotune(crkfr_batch* batch, const double* u_dev, int32
                                   void* stream);
 crkfr_status crkfr_batch_get_status(crkfr_batch* batch, void* stream);
 int64_t crkfr_batch_launch_count(const crkfr_batch* batch);
+/* Kernel timing of an ensemble (measurement aid; the paper has no
+ * counterpart).  While enabled, every step kernel launched by
+ * crkfr_batch_step without a graph is bracketed by a CUDA event pair on its
+ * stream; crkfr_batch_profile_read synchronises on them and returns the
+ * number of timed launches and their summed device time (ms) since
+ * profiling was enabled.  Enabling (again) clears the sums.  Calls with a
+ * graph are not timed: compare their wall time with this sum to see the
+ * time between kernels. */
+crkfr_status crkfr_batch_profile_enable(crkfr_batch* batch, int32_t enable);
+crkfr_status crkfr_batch_profile_read(crkfr_batch* batch, int64_t* launches, double* total_ms);
 const char* crkfr_batch_last_error(const crkfr_batch* batch);
 
-/* Static strings (the paper has no counterpart). */
+/* Static strings (the paper has no counterpart).  crkfr_last_error(NULL):
+ * the calling thread's last error of a call without a context. */
 const char* crkfr_error_string(crkfr_status status);
 const char* crkfr_last_error(const crkfr_ctx* ctx);
 

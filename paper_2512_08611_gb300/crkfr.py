@@ -39,12 +39,20 @@ class Config(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int32), ("degree", ctypes.c_int32),
                 ("nodes", ctypes.c_int32), ("source", ctypes.c_int32),
                 ("gravity", ctypes.c_double), ("cfl_safety", ctypes.c_double),
-                ("cfl_number", ctypes.c_double), ("source_coef", ctypes.c_double)]
+                ("cfl_number", ctypes.c_double), ("source_coef", ctypes.c_double),
+                ("rk", ctypes.c_int32), ("nc_face_mode", ctypes.c_int32),
+                ("coef_dissipation", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-def make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source, source_coef):
+# face non-conservative terms (crkfr_nc_face): only "frozen" is built
+NC_FACE = {"frozen": 0, "literal": 1, "stagewise": 2}
+
+
+def make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source, source_coef,
+                rk=0, nc_face="frozen", coef_dissipation=False):
     return Config(SYSTEMS[system], degree, NODES[nodes], SOURCES[source], gravity, cfl_safety,
-                  cfl_number, float(source_coef))
+                  cfl_number, float(source_coef), int(rk), NC_FACE[nc_face],
+                  1 if coef_dissipation else 0, 0)
 
 
 _P = ctypes.c_void_p
@@ -58,7 +66,7 @@ _PI64 = ctypes.POINTER(ctypes.c_int64)
 SIGNATURES = {
     "crkfr_create": (_I32, [ctypes.POINTER(_P), ctypes.POINTER(Config)]),
     "crkfr_destroy": (None, [_P]),
-    "crkfr_set_mesh": (_I32, [_P, _I32, _PI64, _PD, _PD]),
+    "crkfr_set_mesh": (_I32, [_P, _I32, _PI64, _PD, _PD, _I32]),
     "crkfr_sizes": (_I32, [_P, _PI64, _PI64]),
     "crkfr_get_nodes": (_I32, [_P, _PD, _PD]),
     "crkfr_get_cfl": (_I32, [_P, _PD]),
@@ -102,6 +110,8 @@ SIGNATURES = {
     "crkfr_batch_get_times": (_I32, [_P, _PD, _P]),
     "crkfr_batch_get_status": (_I32, [_P, _P]),
     "crkfr_batch_launch_count": (_I64, [_P]),
+    "crkfr_batch_profile_enable": (_I32, [_P, _I32]),
+    "crkfr_batch_profile_read": (_I32, [_P, _PI64, _PD]),
     "crkfr_batch_last_error": (ctypes.c_char_p, [_P]),
     "crkfr_error_string": (ctypes.c_char_p, [_I32]),
     "crkfr_last_error": (ctypes.c_char_p, [_P]),
@@ -143,14 +153,14 @@ class _DeviceBlock:
 
 
 def math_check(x, op):
-    """out = 1/x (op 'rcp') or sqrt(x) (op 'sqrt') by the kernels' own FP64
-    routines; x a contiguous float64 CUDA tensor."""
+    """out = 1/x (op 'rcp'), sqrt(x) (op 'sqrt') or 1/sqrt(x) (op 'rsqrt') by
+    the kernels' own FP64 routines; x a contiguous float64 CUDA tensor."""
     import torch
     if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
         raise ValueError("expected a contiguous float64 CUDA tensor")
     out = torch.empty_like(x)
     st = lib().crkfr_math_check(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                x.numel(), {"rcp": 0, "sqrt": 1}[op], _stream())
+                                x.numel(), {"rcp": 0, "sqrt": 1, "rsqrt": 2}[op], _stream())
     if st != CRKFR_OK:
         raise CrkfrError(st, lib().crkfr_error_string(st).decode())
     return out
@@ -188,15 +198,29 @@ def fp64_probe(mode, blocks=None, iters=4096, repeats=5):
 
 def step_1d_noalloc(system, degree, n_elem, lo, hi, c, u_in, u_out, dt=0.0, nsteps=1,
                     nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0, source=None,
-                    source_coef=0.0):
+                    source_coef=0.0, rk=0, nc_face="frozen", coef_dissipation=False):
     """crkfr_step_1d_noalloc: 1D steps whose scratch lives in the library's
     static device array, for callers that cannot allocate device memory."""
-    cfg = make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source, source_coef)
+    import torch
+    if system not in NVARS or DIM[system] != 1:
+        raise ValueError(f"step_1d_noalloc takes a 1D system, got {system!r}")
+    n_elem, n = int(n_elem), int(degree) + 1
+    shapes = {"c": (n_elem, n), "u_in": (NVARS[system], n_elem, n),
+              "u_out": (NVARS[system], n_elem, n)}
+    for name, t in (("c", c), ("u_in", u_in), ("u_out", u_out)):
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise TypeError(f"{name}: expected a CUDA tensor")
+        if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != shapes[name]:
+            raise ValueError(f"{name}: expected contiguous float64 of shape {shapes[name]}, got "
+                             f"{t.dtype} {tuple(t.shape)}")
+    cfg = make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source, source_coef,
+                      rk, nc_face, coef_dissipation)
     ptr = lambda t: ctypes.c_void_p(t.data_ptr())
     st = lib().crkfr_step_1d_noalloc(ctypes.byref(cfg), int(n_elem), float(lo), float(hi), ptr(c),
                                      ptr(u_in), ptr(u_out), float(dt), int(nsteps), _stream())
     if st != CRKFR_OK:
-        raise CrkfrError(st, lib().crkfr_error_string(st).decode())
+        raise CrkfrError(st, lib().crkfr_last_error(None).decode() or
+                         lib().crkfr_error_string(st).decode())
     return u_out
 
 
@@ -212,7 +236,7 @@ class Solver:
     SSP3-IMEX(4,3,3)."""
 
     def __init__(self, system, degree, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0,
-                 source=None, source_coef=0.0):
+                 source=None, source_coef=0.0, rk=0, nc_face="frozen", coef_dissipation=False):
         self.system, self.degree, self.family = system, degree, nodes
         self.source, self.source_coef = source, source_coef
         self.limiter = (None, 0.0)
@@ -220,7 +244,7 @@ class Solver:
         self.dim = DIM[system]
         self.n = degree + 1
         cfg = make_config(system, degree, nodes, gravity, cfl_safety, cfl_number, source,
-                          source_coef)
+                          source_coef, rk, nc_face, coef_dissipation)
         h = ctypes.c_void_p()
         self._check(lib().crkfr_create(ctypes.byref(h), ctypes.byref(cfg)), None)
         self.h = h
@@ -229,8 +253,7 @@ class Solver:
     def _check(self, status, h="self"):
         if status != CRKFR_OK:
             handle = self.h if h == "self" else h
-            msg = lib().crkfr_last_error(handle).decode() if handle else \
-                lib().crkfr_error_string(status).decode()
+            msg = lib().crkfr_last_error(handle).decode()   # NULL: this thread's last error
             raise CrkfrError(status, msg or lib().crkfr_error_string(status).decode())
 
     def close(self):
@@ -245,14 +268,15 @@ class Solver:
             pass
 
     # -- set-up ----------------------------------------------------------------
-    def set_mesh(self, n_elem, lo, hi):
+    def set_mesh(self, n_elem, lo, hi, periodic=True):
         n_elem = [int(v) for v in np.atleast_1d(n_elem)]
         lo = [float(v) for v in np.atleast_1d(lo)]
         hi = [float(v) for v in np.atleast_1d(hi)]
         d = len(n_elem)
         arr = (ctypes.c_int64 * d)(*n_elem)
         self._check(lib().crkfr_set_mesh(self.h, d, arr, (ctypes.c_double * d)(*lo),
-                                         (ctypes.c_double * d)(*hi)))
+                                         (ctypes.c_double * d)(*hi),
+                                         (1 << d) - 1 if periodic else 0))
         self.n_elem, self.lo, self.hi = n_elem, lo, hi
         self.limiter = (None, 0.0)   # a new mesh switches the limiter off
         n = self.n
@@ -498,12 +522,13 @@ class Batch:
     (crkfr_batch_*).  ``members``: list of (degree, n_elem, lo, hi)."""
 
     def __init__(self, system, members, nodes="gl", gravity=9.81, cfl_safety=0.5, cfl_number=0.0,
-                 source=None, source_coef=0.0):
+                 source=None, source_coef=0.0, rk=0, nc_face="frozen", coef_dissipation=False):
         self.system = system
         self.M = NVARS[system]
         self.members = [(int(d), int(e), float(a), float(b)) for d, e, a, b in members]
         n = len(self.members)
-        cfg = make_config(system, 0, nodes, gravity, cfl_safety, cfl_number, source, source_coef)
+        cfg = make_config(system, 0, nodes, gravity, cfl_safety, cfl_number, source, source_coef,
+                          rk, nc_face, coef_dissipation)
         deg = (ctypes.c_int32 * n)(*[m[0] for m in self.members])
         ne = (ctypes.c_int64 * n)(*[m[1] for m in self.members])
         lo = (ctypes.c_double * n)(*[m[2] for m in self.members])
@@ -511,7 +536,8 @@ class Batch:
         h = ctypes.c_void_p()
         st = lib().crkfr_batch_create(ctypes.byref(h), ctypes.byref(cfg), n, deg, ne, lo, hi)
         if st != CRKFR_OK:
-            raise CrkfrError(st, lib().crkfr_error_string(st).decode())
+            raise CrkfrError(st, lib().crkfr_last_error(None).decode() or
+                             lib().crkfr_error_string(st).decode())
         self.h = h
         so, co = (ctypes.c_int64 * (n + 1))(), (ctypes.c_int64 * (n + 1))()
         self._check(lib().crkfr_batch_layout(self.h, so, co))
@@ -580,3 +606,13 @@ class Batch:
 
     def launch_count(self):
         return lib().crkfr_batch_launch_count(self.h)
+
+    def profile(self, enable=True):
+        """Time every step kernel of calls without a graph (crkfr_batch_profile_*)."""
+        self._check(lib().crkfr_batch_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(timed launches, summed kernel ms) since profiling was enabled."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        self._check(lib().crkfr_batch_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value

@@ -181,7 +181,7 @@ __global__ void k_math_check(const double* __restrict__ x, double* __restrict__ 
                              int op) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  out[i] = op == 0 ? drcp(x[i]) : dsqrt_pos(x[i]);
+  out[i] = op == 0 ? drcp(x[i]) : op == 1 ? dsqrt_pos(x[i]) : drsqrt_pos(x[i]);
 }
 
 __global__ void k_set_time(DevState* st, int slot, double t) {
@@ -430,6 +430,35 @@ double source_coef(const crkfr_config& cfg) {
   return cfg.source == CRKFR_SRC_NONE ? 0.0 : cfg.source_coef;
 }
 
+thread_local std::string g_last_error;
+
+crkfr_status fail_global(crkfr_status s, const char* msg) {
+  g_last_error = msg;
+  return s;
+}
+
+void clear_global_error() { g_last_error.clear(); }
+
+crkfr_status check_options(const crkfr_config* cfg, int N) {
+  if (cfg->reserved != 0) return fail_global(CRKFR_ERR_ARG, "crkfr_config.reserved must be 0");
+  const int order = cfg->source != CRKFR_SRC_NONE ? 3 : N + 1;
+  if (cfg->rk != 0 && cfg->rk != order)
+    return fail_global(CRKFR_ERR_UNSUPPORTED,
+                       "rk: only the default tableau is built (order N+1 without a source, "
+                       "3 with one)");
+  if (cfg->nc_face_mode == CRKFR_NC_LITERAL || cfg->nc_face_mode == CRKFR_NC_STAGEWISE)
+    return fail_global(CRKFR_ERR_UNSUPPORTED,
+                       "nc_face_mode: only the frozen face terms are built (the literal and "
+                       "stagewise readings exist in the CPU oracle)");
+  if (cfg->nc_face_mode != CRKFR_NC_FROZEN)
+    return fail_global(CRKFR_ERR_ARG, "nc_face_mode: not a crkfr_nc_face value");
+  if (cfg->coef_dissipation == 1)
+    return fail_global(CRKFR_ERR_UNSUPPORTED,
+                       "coef_dissipation: only the static coefficient is built");
+  if (cfg->coef_dissipation != 0) return fail_global(CRKFR_ERR_ARG, "coef_dissipation: 0 or 1");
+  return CRKFR_OK;
+}
+
 }  // namespace crkfr
 
 extern "C" {
@@ -447,24 +476,33 @@ const char* crkfr_error_string(crkfr_status s) {
   return "unknown status";
 }
 
-const char* crkfr_last_error(const crkfr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+const char* crkfr_last_error(const crkfr_ctx* c) {
+  return c ? c->err.c_str() : g_last_error.c_str();
+}
 
 int64_t crkfr_launch_count(const crkfr_ctx* c) { return c ? c->launches : 0; }
 
 
 crkfr_status crkfr_create(crkfr_ctx** out, const crkfr_config* cfg) {
-  if (!out) return CRKFR_ERR_ARG;
+  clear_global_error();
+  if (!out) return fail_global(CRKFR_ERR_ARG, "null argument");
   *out = nullptr;
-  if (!cfg) return CRKFR_ERR_ARG;
-  if (!sys_valid(cfg->system)) return CRKFR_ERR_UNSUPPORTED;
-  if (crkfr_status st = check_source(cfg); st != CRKFR_OK) return st;
-  if (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL) return CRKFR_ERR_UNSUPPORTED;
+  if (!cfg) return fail_global(CRKFR_ERR_ARG, "null argument");
+  if (!sys_valid(cfg->system)) return fail_global(CRKFR_ERR_UNSUPPORTED, "unknown system");
+  if (crkfr_status st = check_source(cfg); st != CRKFR_OK)
+    return fail_global(st, "source term invalid or not built for this system");
+  if (cfg->nodes != CRKFR_NODES_GL && cfg->nodes != CRKFR_NODES_GLL)
+    return fail_global(CRKFR_ERR_UNSUPPORTED, "unknown node family");
   const int minN = (sys_is_2d(cfg->system) || cfg->nodes == CRKFR_NODES_GLL) ? 1 : 0;
-  if (cfg->degree < minN || cfg->degree > kMaxN) return CRKFR_ERR_UNSUPPORTED;
-  if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
-  if (cfg->system != CRKFR_SYS_VARADV_1D && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
+  if (cfg->degree < minN || cfg->degree > kMaxN)
+    return fail_global(CRKFR_ERR_UNSUPPORTED, "degree not built for this system and node family");
+  if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0)
+    return fail_global(CRKFR_ERR_ARG, "cfl_safety must lie in (0, 1]");
+  if (cfg->system != CRKFR_SYS_VARADV_1D && !(cfg->gravity > 0.0))
+    return fail_global(CRKFR_ERR_ARG, "gravity must be positive");
+  if (crkfr_status st = check_options(cfg, cfg->degree); st != CRKFR_OK) return st;
   crkfr_ctx* c = new (std::nothrow) crkfr_ctx();
-  if (!c) return CRKFR_ERR_ALLOC;
+  if (!c) return fail_global(CRKFR_ERR_ALLOC, "host allocation failed");
   c->cfg = *cfg;
   c->M = sys_vars(cfg->system);
   if (!build_basis(cfg->degree, cfg->nodes == CRKFR_NODES_GLL, &c->basis)) {
@@ -501,10 +539,14 @@ void crkfr_destroy(crkfr_ctx* c) {
 }
 
 crkfr_status crkfr_set_mesh(crkfr_ctx* c, int32_t dim, const int64_t* n_elem, const double* lo,
-                            const double* hi) {
+                            const double* hi, int32_t periodic_mask) {
   if (!c || !n_elem || !lo || !hi) return fail(c, CRKFR_ERR_ARG, "null argument");
   const int want = sys_is_2d(c->cfg.system) ? 2 : 1;
   if (dim != want) return fail(c, CRKFR_ERR_ARG, "dimension does not match the system");
+  if (periodic_mask < 0 || periodic_mask >= (1 << dim))
+    return fail(c, CRKFR_ERR_ARG, "periodic_mask has bits beyond the mesh's dimension");
+  if (periodic_mask != (1 << dim) - 1)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "only periodic meshes are built");
   for (int d = 0; d < dim; ++d) {
     if (n_elem[d] <= 0) return fail(c, CRKFR_ERR_ARG, "element count must be positive");
     if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
@@ -731,7 +773,8 @@ crkfr_status crkfr_step(crkfr_ctx* c, double* u, double dt, int64_t nsteps, void
   if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "subdomain: use crkfr_step_local / faces");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (nsteps < 0) return fail(c, CRKFR_ERR_ARG, "nsteps must be >= 0");
-  if (!std::isfinite(dt) && dt > 0.0) return fail(c, CRKFR_ERR_ARG, "dt must be finite");
+  if (std::isnan(dt) || (std::isinf(dt) && dt > 0.0))
+    return fail(c, CRKFR_ERR_ARG, "dt must be finite (or <= 0 for the CFL step)");
   return run_steps(c, u, dt, nsteps, std::numeric_limits<double>::infinity(),
                    (cudaStream_t)stream);
 }
@@ -1070,7 +1113,7 @@ crkfr_status crkfr_set_time(crkfr_ctx* c, double t, void* stream) {
 }
 
 crkfr_status crkfr_math_check(const double* x, double* out, int64_t n, int32_t op, void* stream) {
-  if (!x || !out || n < 0 || (op != 0 && op != 1)) return CRKFR_ERR_ARG;
+  if (!x || !out || n < 0 || op < 0 || op > 2) return CRKFR_ERR_ARG;
   if (n == 0) return CRKFR_OK;
   const int64_t blocks = (n + 255) / 256;
   if (blocks > 0x7fffffff) return CRKFR_ERR_ARG;

@@ -218,6 +218,9 @@ void fill_tables(const HostBasis& b, double dx, double dy, double gravity, bool 
   T->face_g = gravity / T->b0;
   T->inv_b0 = 1.0 / T->b0;
   T->inv_gravity = gravity > 0.0 ? 1.0 / gravity : 0.0;
+  T->sqrt_gravity = gravity > 0.0 ? std::sqrt(gravity) : 0.0;
+  for (int q = 0; q < n; ++q)
+    for (int p = 0; p < n; ++p) T->w2[q][p] = b.w[q] * b.w[p];
   T->src_coef = src_coef;
   // smoothness indicator (Hennemann et al. 2021): inverse Vandermonde of the
   // orthonormal Legendre polynomials sqrt((2j+1)/2) P_j(2 xi - 1) at the

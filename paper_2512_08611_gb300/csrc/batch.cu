@@ -70,6 +70,11 @@ struct crkfr_batch {
   double* g_u = nullptr;
   double g_dt = 0.0;
   int64_t g_nsteps = -1;
+  // kernel timing of calls without a graph (crkfr_batch_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs (start, end) of the recorded launches
+  int64_t prof_n = 0;
+  double prof_ms = 0.0;
 };
 
 namespace {
@@ -109,6 +114,8 @@ void drop_graph(crkfr_batch* b) {
 
 void free_all(crkfr_batch* b) {
   drop_graph(b);
+  for (auto e : b->prof_ev) cudaEventDestroy(e);
+  b->prof_ev.clear();
   if (b->cap) cudaStreamDestroy(b->cap);
   for (int k = 0; k < kMaxNodes; ++k) {
     if (b->side[k]) cudaStreamDestroy(b->side[k]);
@@ -148,9 +155,10 @@ crkfr_status class_rates(crkfr_batch* b, int N, double* u, cudaStream_t s) {
   return CRKFR_OK;
 }
 
-// step k of one degree class
+// step k of one degree class (timed with an event pair when profiling a
+// call that is not captured)
 crkfr_status class_step(crkfr_batch* b, int N, StepCtl ctl, int64_t k, double* const* bufs,
-                        int cur, cudaStream_t s) {
+                        int cur, cudaStream_t s, bool timed) {
   ctl.slot_read = (int)(k % 3);
   ctl.slot_write = (int)((k + 1) % 3);
   ctl.slot_reset = (int)((k + 2) % 3);
@@ -160,14 +168,42 @@ crkfr_status class_step(crkfr_batch* b, int N, StepCtl ctl, int64_t k, double* c
   B.ctl = ctl;
   B.u_in = bufs[cur];
   B.u_out = bufs[cur ^ 1];
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (timed) {
+    for (auto& e : ev) BCK(b, cudaEventCreate(&e));
+    b->prof_ev.push_back(ev[0]);
+    b->prof_ev.push_back(ev[1]);
+    BCK(b, cudaEventRecord(ev[0], s));
+  }
   if (launch_step_1d_batch(B, s)) return bfail(b, CRKFR_ERR_CUDA, "batch step kernel");
+  if (timed) BCK(b, cudaEventRecord(ev[1], s));
   b->launches += 1;
   return CRKFR_OK;
 }
 
+// sums the recorded kernel times (synchronises on the events) and frees them
+crkfr_status drain_profile(crkfr_batch* b) {
+  crkfr_status st = CRKFR_OK;
+  for (size_t i = 0; i + 1 < b->prof_ev.size(); i += 2) {
+    float ms = 0.0f;
+    if (st == CRKFR_OK) {
+      cudaError_t e = cudaEventSynchronize(b->prof_ev[i + 1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->prof_ev[i], b->prof_ev[i + 1]);
+      if (e != cudaSuccess) st = bfail(b, CRKFR_ERR_CUDA, "profile events");
+    }
+    b->prof_n += 1;
+    b->prof_ms += ms;
+    cudaEventDestroy(b->prof_ev[i]);
+    cudaEventDestroy(b->prof_ev[i + 1]);
+  }
+  b->prof_ev.clear();
+  return st;
+}
+
 // the launches of one call: [prepare], [copy], per class [rates] and nsteps
 // steps (interleaved by step, or one concurrent branch per class), [finish]
-crkfr_status record(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaStream_t s) {
+crkfr_status record(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaStream_t s,
+                    bool timed = false) {
   const bool cfl_mode = !(dt > 0.0);
   const int nb = (b->n_inst + 127) / 128;
   if (cfl_mode) {
@@ -197,7 +233,7 @@ crkfr_status record(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaSt
       }
       int cur = cur0;
       for (int64_t k = 0; k < nsteps; ++k) {
-        crkfr_status st = class_step(b, N, ctl, k, bufs, cur, q);
+        crkfr_status st = class_step(b, N, ctl, k, bufs, cur, q, timed);
         if (st != CRKFR_OK) return st;
         cur ^= 1;
       }
@@ -216,7 +252,7 @@ crkfr_status record(crkfr_batch* b, double* u, double dt, int64_t nsteps, cudaSt
     for (int64_t k = 0; k < nsteps; ++k) {
       for (int N = 0; N < kMaxNodes; ++N) {
         if (!b->nwork[N]) continue;
-        crkfr_status st = class_step(b, N, ctl, k, bufs, cur, s);
+        crkfr_status st = class_step(b, N, ctl, k, bufs, cur, s, timed);
         if (st != CRKFR_OK) return st;
       }
       cur ^= 1;
@@ -292,6 +328,7 @@ extern "C" {
 crkfr_status crkfr_batch_create(crkfr_batch** out, const crkfr_config* cfg, int32_t n,
                                 const int32_t* degrees, const int64_t* n_elem, const double* lo,
                                 const double* hi) {
+  clear_global_error();
   if (!out) return CRKFR_ERR_ARG;
   *out = nullptr;
   if (!cfg || !degrees || !n_elem || !lo || !hi || n <= 0) return CRKFR_ERR_ARG;
@@ -314,6 +351,10 @@ crkfr_status crkfr_batch_create(crkfr_batch** out, const crkfr_config* cfg, int3
     if (N < (gll ? 1 : 0) || N > kMaxN) {
       delete b;
       return CRKFR_ERR_UNSUPPORTED;
+    }
+    if (crkfr_status so = check_options(cfg, N); so != CRKFR_OK) {
+      delete b;
+      return so;
     }
     if (n_elem[i] <= 0 || !(hi[i] > lo[i]) || !std::isfinite(lo[i]) || !std::isfinite(hi[i])) {
       delete b;
@@ -428,10 +469,11 @@ crkfr_status crkfr_batch_step(crkfr_batch* b, double* u, double dt, int64_t nste
   crkfr_status st = ready(b);
   if (st != CRKFR_OK) return st;
   if (!u || nsteps < 0) return bfail(b, CRKFR_ERR_ARG, "bad argument");
-  if (!std::isfinite(dt) && dt > 0.0) return bfail(b, CRKFR_ERR_ARG, "dt must be finite");
+  if (std::isnan(dt) || (std::isinf(dt) && dt > 0.0))
+    return bfail(b, CRKFR_ERR_ARG, "dt must be finite (or <= 0 for the CFL step)");
   if (nsteps == 0) return CRKFR_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!use_graph) return record(b, u, dt, nsteps, s);
+  if (!use_graph) return record(b, u, dt, nsteps, s, b->prof);
   const bool same = b->gexec && b->g_u == u && b->g_nsteps == nsteps &&
                     ((dt > 0.0) == (b->g_dt > 0.0)) && (!(dt > 0.0) || dt == b->g_dt);
   if (!same) {
@@ -577,6 +619,23 @@ crkfr_status crkfr_batch_get_status(crkfr_batch* b, void* stream) {
 }
 
 int64_t crkfr_batch_launch_count(const crkfr_batch* b) { return b ? b->launches : 0; }
+
+crkfr_status crkfr_batch_profile_enable(crkfr_batch* b, int32_t enable) {
+  if (!b) return CRKFR_ERR_ARG;
+  crkfr_status st = drain_profile(b);
+  b->prof_n = 0;
+  b->prof_ms = 0.0;
+  b->prof = enable != 0;
+  return st;
+}
+
+crkfr_status crkfr_batch_profile_read(crkfr_batch* b, int64_t* launches, double* total_ms) {
+  if (!b) return CRKFR_ERR_ARG;
+  crkfr_status st = drain_profile(b);
+  if (launches) *launches = b->prof_n;
+  if (total_ms) *total_ms = b->prof_ms;
+  return st;
+}
 
 const char* crkfr_batch_last_error(const crkfr_batch* b) { return b ? b->err.c_str() : "null"; }
 

@@ -45,6 +45,8 @@ struct Tables {
   double face_g;   // g / b_ref
   double inv_b0;   // 1 / b_ref
   double inv_gravity;  // 1 / g (0 without gravity)
+  double sqrt_gravity; // sqrt(g) (0 without gravity)
+  double w2[kMaxNodes][kMaxNodes];  // w_q w_p (element means of 2D nodal fields)
   double src_coef; // source coefficient: K (linear damping) or C_f (Chezy)
   // smoothness indicator of the subcell limiter: nodal values -> coefficients
   // in the orthonormal Legendre basis, threshold T(N) and s / T
@@ -102,6 +104,14 @@ struct HostBasis {
 // (CRKFR_OK, CRKFR_ERR_ARG or CRKFR_ERR_UNSUPPORTED), and the coefficient the
 // kernels take (0 without a source)
 crkfr_status check_source(const crkfr_config* cfg);
+// api.cu: the scheme switches of cfg (rk, nc_face_mode, coef_dissipation,
+// reserved) for degree N: CRKFR_OK for the built defaults, otherwise
+// CRKFR_ERR_UNSUPPORTED (or CRKFR_ERR_ARG) with the reason recorded for
+// crkfr_last_error(NULL)
+crkfr_status check_options(const crkfr_config* cfg, int N);
+// api.cu: records the reason of a failed call without a context (thread-local)
+crkfr_status fail_global(crkfr_status s, const char* msg);
+void clear_global_error();
 double source_coef(const crkfr_config& cfg);
 
 // basis.cpp

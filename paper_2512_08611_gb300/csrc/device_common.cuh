@@ -63,9 +63,44 @@ __device__ __forceinline__ double dsqrt_pos(double x) {
   return fma(q, p, t);
 }
 
-// sigma(f' + B) of shallow water in one direction: |m/h| + sqrt(g h)
-__device__ __forceinline__ double swe_speed(double h, double m, double g) {
-  return fabs(m * drcp(h)) + dsqrt_pos(g * h);
+// 1/sqrt(x) for FP64 x > 0.  Seed as in dsqrt_pos; with e = 1 - x y^2,
+// 1/sqrt(x) = y (1 - e)^(-1/2), and the binomial series to second order,
+// y + y e (1/2 + 3e/8), takes the ~2^-21 seed error to ~2^-63.  Five FP64
+// instructions.  Non-positive inputs and exponents outside the FP32 seed
+// range fall back to the IEEE operations.
+__device__ __forceinline__ double drsqrt_pos(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (hi < 0 || ex < 1023 - 124 || ex > 1023 + 124) return 1.0 / sqrt(x);
+  const int fb = (((hi - ((1023 - 127) << 20)) << 3) | (int)(lo >> 29));
+  const float yf = rsqrtf(__int_as_float(fb));
+  const int yb = __float_as_int(yf);
+  const double y = __hiloint2double((yb >> 3) + ((1023 - 127) << 20), yb << 29);
+  const double t = x * y;
+  const double e = fma(-t, y, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  const double q = y * e;
+  return fma(q, p, y);
+}
+
+// sigma(f' + B) of shallow water in one direction, |m/h| + sqrt(g h), as
+// r (|m| r + sqrt(g) h) with r = 1/sqrt(h): eight FP64 instructions (one
+// reciprocal square root) instead of a reciprocal and a square root.
+// sg = sqrt(g).
+__device__ __forceinline__ double swe_speed(double h, double m, double sg) {
+  const double r = drsqrt_pos(h);
+  return fma(sg, h, fabs(m) * r) * r;
+}
+
+// sigma_x / dx + sigma_y / dy of the element means (h, hu, hv) (Sec. 5,
+// Eq. time.step.2d) with one reciprocal square root.
+__device__ __forceinline__ double swe_rate_2d(double h, double mx, double my, double sg,
+                                              double inv_dx, double inv_dy) {
+  const double r = drsqrt_pos(h);
+  const double rr = r * r;
+  const double c = (sg * h) * r;
+  return fma(fma(fabs(mx), rr, c), inv_dx, fma(fabs(my), rr, c) * inv_dy);
 }
 
 // max of two non-negative doubles through their bit patterns (integer pipe)

@@ -39,8 +39,9 @@ constexpr int kWarps2D = kBlock2D / 32;
 // g (eta+ - eta-) in the units of the time averages is g dU_h + gdb.
 template <bool WB>
 __device__ __forceinline__ void face_terms(const double* tm, const double* tp, int nv, double gdb,
-                                           double g, double inv_g, double Tm[3], double Tp[3]) {
-  const double lam = max_nonneg(swe_speed(tm[5], tm[6], g), swe_speed(tp[5], tp[6], g));
+                                           double g, double inv_g, double sg, double Tm[3],
+                                           double Tp[3]) {
+  const double lam = max_nonneg(swe_speed(tm[5], tm[6], sg), swe_speed(tp[5], tp[6], sg));
   // time-averaged normal flux of h is the time-averaged normal momentum
   const double dF[3] = {tp[nv] - tm[nv], tp[3] - tm[3], tp[4] - tm[4]};
   double dU[3] = {tp[0] - tm[0], tp[1] - tm[1], tp[2] - tm[2]};
@@ -75,7 +76,8 @@ __device__ __forceinline__ void face_limited(const double* tm, const double* tp,
   const double cm = lm[7], cp = lp[7];
   // high-order fluxes F^num,+- and totals F^tot,+- (Eqs. numflux.cons,
   // good.numflux.non.cons, total.F.non.cons), in the units of the traces
-  const double lam = max_nonneg(swe_speed(tm[5], tm[6], g), swe_speed(tp[5], tp[6], g));
+  const double lam = max_nonneg(swe_speed(tm[5], tm[6], T.sqrt_gravity),
+                                swe_speed(tp[5], tp[6], T.sqrt_gravity));
   const double dUh = WB ? (tp[0] + cp * ib0) - (tm[0] + cm * ib0) : tp[0] - tm[0];
   double FHm[3], FHp[3], FTm[3], FTp[3];
   FHm[0] = fma(-0.5 * lam, dUh, 0.5 * (tm[nv] + tp[nv]));
@@ -143,6 +145,10 @@ template <int N, bool LIMIT>
 struct FaceShape {
   static constexpr int TY = LIMIT ? 4 : kWarps2D;   // tile rows (warps)
   static constexpr int block = TY * 32;
+  // resident blocks per SM the register allocation must allow (the plain
+  // kernel: 4 x 8 warps, half the SM's warp slots, to hide the shared-memory
+  // latency of the face terms)
+  static constexpr int min_blocks = LIMIT ? 1 : 4;
 };
 
 // Face kernel on tiles of TY x EPW elements (one tile row per warp).
@@ -152,7 +158,8 @@ struct FaceShape {
 // memory; phase 2 applies them along the rows and columns of each element.
 
 template <int N, bool GLL, bool RES, bool WB, bool LIMIT = false, bool IMEX = false>
-__global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const Launch2D L) {
+__global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT>::min_blocks)
+    k_face_2d(const Launch2D L) {
   static_assert(!(LIMIT && RES), "the limiter needs a step");
   constexpr int n = N + 1;
   constexpr int nn = n * n;
@@ -176,6 +183,14 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
   // the traces hold time averages divided by b_0: so do the face terms
   const double dtp = RES ? 1.0 : L.st->dt_cur;
   const double dt = dtp * T.b0;
+  // correction tables times -dt (phase 2 adds the face terms to W with one
+  // FMA each); written here, read after the barrier between the phases
+  __shared__ double cor[4][n];
+  if (threadIdx.x < 4 * n) {
+    const int t = threadIdx.x / n, p = threadIdx.x - t * n;
+    const double g = t == 0 ? T.gRx[p] : t == 1 ? T.gLx[p] : t == 2 ? T.gRy[p] : T.gLy[p];
+    cor[t][p] = -dt * g;
+  }
 
   // ---- phase 1: every face node of the tile once --------------------------
   for (int f = threadIdx.x; f < NX + NY; f += BT) {
@@ -207,7 +222,8 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
           fxp[r][k][q][v] = Fp[v];
         }
       } else {
-        face_terms<WB>(a, b, 1, L.sface[ep * n + q], T.gravity, T.inv_gravity, Tm, Tp);
+        face_terms<WB>(a, b, 1, L.sface[ep * n + q], T.gravity, T.inv_gravity, T.sqrt_gravity,
+                       Tm, Tp);
       }
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
         }
       } else {
         face_terms<WB>(a, b, 2, L.sface[Ne * n + (ey0 + k) * plane + ex * n + p], T.gravity,
-                       T.inv_gravity, Tm, Tp);
+                       T.inv_gravity, T.sqrt_gravity, Tm, Tp);
       }
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
@@ -271,23 +287,12 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
   for (int v = 0; v < 3; ++v)
 #pragma unroll
     for (int p = 0; p < n; ++p) {
-      double R = 0.0;
-      bool any = false;
-      if (!GLL || p == N) { R = sxm[r][cc + 1][q][v] * T.gRx[p]; any = true; }
-      if (!GLL || p == 0) {
-        R = any ? fma(sxp[r][cc][q][v], T.gLx[p], R) : sxp[r][cc][q][v] * T.gLx[p];
-        any = true;
-      }
-      if (!GLL || q == N) {
-        R = any ? fma(sym[r + 1][cc][p][v], T.gRy[q], R) : sym[r + 1][cc][p][v] * T.gRy[q];
-        any = true;
-      }
-      if (!GLL || q == 0) {
-        R = any ? fma(syp[r][cc][p][v], T.gLy[q], R) : syp[r][cc][p][v] * T.gLy[q];
-        any = true;
-      }
-      const double w = L.w[(v * Ne + ge) * nn + q * n + p];
-      out[v][p] = any ? fma(-dt, R, w) : w;
+      double o = L.w[(v * Ne + ge) * nn + q * n + p];
+      if (!GLL || p == N) o = fma(sxm[r][cc + 1][q][v], cor[0][p], o);
+      if (!GLL || p == 0) o = fma(sxp[r][cc][q][v], cor[1][p], o);
+      if (!GLL || q == N) o = fma(sym[r + 1][cc][p][v], cor[2][q], o);
+      if (!GLL || q == 0) o = fma(syp[r][cc][p][v], cor[3][q], o);
+      out[v][p] = o;
     }
   if constexpr (LIMIT) {
     // first-order subcell update: the local kernel's part plus the
@@ -371,27 +376,44 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block) k_face_2d(const La
     double m[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      double s = T.w[0] * out[v][0];
+      double s = T.w2[q][0] * out[v][0];
 #pragma unroll
-      for (int p = 1; p < n; ++p) s = fma(T.w[p], out[v][p], s);
-      m[v] = T.w[q] * s;
+      for (int p = 1; p < n; ++p) s = fma(T.w2[q][p], out[v][p], s);
+      m[v] = s;
     }
-    // sum over the n rows of the element (lanes c*n .. c*n+n-1), rows in order
+    // sum over the n rows of the element (lanes c*n .. c*n+n-1): a butterfly
+    // when n is a power of two (every lane ends with the same sum), else the
+    // rows in order
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
       double s = m[v];
+      if constexpr ((n & (n - 1)) == 0) {
 #pragma unroll
-      for (int k = 1; k < n; ++k) {
-        const int src = c * n + ((q + k) % n);
-        s += __shfl_sync(0xffffffffu, m[v], src < 32 ? src : lane);
+        for (int o = 1; o < n; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      } else {
+#pragma unroll
+        for (int k = 1; k < n; ++k) {
+          const int src = c * n + ((q + k) % n);
+          s += __shfl_sync(0xffffffffu, m[v], src < 32 ? src : lane);
+        }
       }
       m[v] = s;
     }
+    // the rates: one element per thread of the first TY * TX threads, so that
+    // a warp computes 32 of them (from the n lanes of an element only one
+    // would be busy)
+    __shared__ double mean_s[TY][TX][3];
+    if (lane_ok && q == 0) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v) mean_s[r][c][v] = m[v];
+    }
+    __syncthreads();
     double rate = 0.0;
-    if (active && q == 0) {
-      const double rr = drcp(m[0]);
-      const double cs = dsqrt_pos(T.gravity * m[0]);
-      rate = fma(fabs(m[1] * rr) + cs, T.inv_dx, (fabs(m[2] * rr) + cs) * T.inv_dy);
+    if (threadIdx.x < TY * TX) {
+      const int er = threadIdx.x / TX, ec = threadIdx.x - er * TX;
+      if (ey0 + er < Ey && ex0 + ec < Ex)
+        rate = swe_rate_2d(mean_s[er][ec][0], mean_s[er][ec][1], mean_s[er][ec][2],
+                           T.sqrt_gravity, T.inv_dx, T.inv_dy);
     }
     block_max_atomic<BT>(rate, &L.st->rate[L.ctl.slot_write]);
   }

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kBlock1D) k_rate_1d(const Launch1D L, int slot
         hb = fma(T.w[p], L.u_in[e * n + p], hb);
         mb = fma(T.w[p], L.u_in[(L.E + e) * n + p], mb);
       }
-      rate = swe_speed(hb, mb, T.gravity) * L.xs;
+      rate = swe_speed(hb, mb, T.sqrt_gravity) * L.xs;
     } else {
       double ab = 0.0;
 #pragma unroll
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBlock1D) k_rate_1d_batch(const LaunchBatch1D 
         hb = fma(T.w[p], u[e * n + p], hb);
         mb = fma(T.w[p], u[(I.E + e) * n + p], mb);
       }
-      rate = swe_speed(hb, mb, T.gravity) * I.xs;
+      rate = swe_speed(hb, mb, T.sqrt_gravity) * I.xs;
     } else {
       double ab = 0.0;
 #pragma unroll

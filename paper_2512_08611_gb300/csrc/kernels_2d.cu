@@ -59,9 +59,7 @@ __global__ void __launch_bounds__(kBlock2D) k_rate_2d(const Launch2D L, int slot
       }
       m[v] = s;
     }
-    const double r = drcp(m[0]);
-    const double c = dsqrt_pos(T.gravity * m[0]);
-    rate = fma(fabs(m[1] * r) + c, T.inv_dx, (fabs(m[2] * r) + c) * T.inv_dy);
+    rate = swe_rate_2d(m[0], m[1], m[2], T.sqrt_gravity, T.inv_dx, T.inv_dy);
   }
   block_max_atomic<kBlock2D>(rate, &L.st->rate[slot]);
 }

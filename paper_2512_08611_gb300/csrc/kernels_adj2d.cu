@@ -36,28 +36,31 @@ constexpr int kBlockAdj = 128;
 constexpr int kWarpsAdj = kBlockAdj / 32;
 constexpr int kTr = 7;
 
-// d sigma / d h and d sigma / d m of sigma(h, m) = |m/h| + sqrt(g h)
-__device__ __forceinline__ void speed_grad(double h, double m, double g, double* dh, double* dm,
+// d sigma / d h and d sigma / d m of sigma(h, m) = |m/h| + sqrt(g h), and
+// sigma itself as the forward kernels compute it (so that the side of the
+// maximum is the one the forward step selected).  sg = sqrt(g); with
+// r1 = 1/sqrt(h): d sigma/dm = sign(m) / h, d sigma/dh = -|m|/h^2 + sg r1 / 2.
+__device__ __forceinline__ void speed_grad(double h, double m, double sg, double* dh, double* dm,
                                            double* sigma) {
-  const double r = drcp(h);
+  const double r1 = drsqrt_pos(h);
+  const double r = r1 * r1;
   const double v = m * r;
   const double s = v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0);
-  const double c = dsqrt_pos(g * h);
-  *sigma = fabs(v) + c;
+  *sigma = swe_speed(h, m, sg);
   *dm = s * r;
-  *dh = fma(-s * v, r, 0.5 * g * drcp(c));
+  *dh = fma(-s * v, r, 0.5 * sg * r1);
 }
 
 // Adjoint of the doubled face terms of one face node.  tm/tp: the two sides'
 // traces (fields as in kernels_2d.cu); Tbm/Tbp: adjoints of T'^- and T'^+;
 // outputs the adjoint traces of both sides and the adjoint of gdb.
 __device__ __forceinline__ void face_terms_adj(const double* tm, const double* tp, int nv,
-                                               double gdb, double g, const double* Tbm,
+                                               double gdb, double sg, const double* Tbm,
                                                const double* Tbp, double* am, double* ap,
                                                double* gdb_bar) {
   double dhm, dmm, sm, dhp, dmp, sp;
-  speed_grad(tm[5], tm[6], g, &dhm, &dmm, &sm);
-  speed_grad(tp[5], tp[6], g, &dhp, &dmp, &sp);
+  speed_grad(tm[5], tm[6], sg, &dhm, &dmm, &sm);
+  speed_grad(tp[5], tp[6], sg, &dhp, &dmp, &sp);
   const bool left = sm > sp;   // the forward maximum picks the right side on a tie
   const double lam = left ? sm : sp;
 #pragma unroll
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(256) k_face_adj_2d(const Launch2DAdj A) {
         tm[fi] = A.trx[(2 * fi + 1) * ts + em * n + k];
         tp[fi] = A.trx[(2 * fi + 0) * ts + e * n + k];
       }
-      face_terms_adj(tm, tp, 1, A.sface[e * n + k], T.gravity, Tbm, Tbp, am, ap, &gbar);
+      face_terms_adj(tm, tp, 1, A.sface[e * n + k], T.sqrt_gravity, Tbm, Tbp, am, ap, &gbar);
 #pragma unroll
       for (int fi = 0; fi < kTr; ++fi) {
         A.atrx[(2 * fi + 1) * ts + em * n + k] = am[fi];
@@ -155,8 +158,8 @@ __global__ void __launch_bounds__(256) k_face_adj_2d(const Launch2DAdj A) {
         tm[fi] = A.try_[((ey * 2 + 1) * kTr + fi) * plane + ex * n + k];
         tp[fi] = A.try_[(((ey + 1) * 2 + 0) * kTr + fi) * plane + ex * n + k];
       }
-      face_terms_adj(tm, tp, 2, A.sface[Ne * n + ey * plane + ex * n + k], T.gravity, Tbm, Tbp,
-                     am, ap, &gbar);
+      face_terms_adj(tm, tp, 2, A.sface[Ne * n + ey * plane + ex * n + k], T.sqrt_gravity, Tbm,
+                     Tbp, am, ap, &gbar);
       // adjoint y traces: [row][side][field][ex][node], no halo rows
 #pragma unroll
       for (int fi = 0; fi < kTr; ++fi) {

@@ -53,6 +53,7 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
                                               double hi, const double* c_dev,
                                               const double* u_in_dev, double* u_out_dev,
                                               double dt, int64_t nsteps, void* stream) {
+  clear_global_error();
   if (!cfg || !c_dev || !u_in_dev || !u_out_dev) return CRKFR_ERR_ARG;
   if (!sys_valid(cfg->system) || sys_is_2d(cfg->system)) return CRKFR_ERR_UNSUPPORTED;
   if (cfg->nodes < CRKFR_NODES_GL || cfg->nodes > CRKFR_NODES_GLL) return CRKFR_ERR_ARG;
@@ -60,11 +61,12 @@ extern "C" crkfr_status crkfr_step_1d_noalloc(const crkfr_config* cfg, int64_t n
   const bool imex = cfg->source != CRKFR_SRC_NONE;
   const bool gll = cfg->nodes == CRKFR_NODES_GLL;
   if (cfg->degree < (gll ? 1 : 0) || cfg->degree > kMaxN) return CRKFR_ERR_UNSUPPORTED;
+  if (crkfr_status so = check_options(cfg, cfg->degree); so != CRKFR_OK) return so;
   if (!(cfg->cfl_safety > 0.0) || cfg->cfl_safety > 1.0) return CRKFR_ERR_ARG;
   if (sys_is_swe(cfg->system) && !(cfg->gravity > 0.0)) return CRKFR_ERR_ARG;
   if (n_elem <= 0 || nsteps < 0 || !(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
     return CRKFR_ERR_ARG;
-  if (!std::isfinite(dt) && dt > 0.0) return CRKFR_ERR_ARG;
+  if (std::isnan(dt) || (std::isinf(dt) && dt > 0.0)) return CRKFR_ERR_ARG;
 
   HostBasis b;
   if (!build_basis(cfg->degree, gll, &b)) return CRKFR_ERR_UNSUPPORTED;

@@ -103,7 +103,8 @@ __device__ __forceinline__ void lo_flux(const double* uL, const double* uR, doub
     constexpr bool WB = (SYS == CRKFR_SYS_SWE_1D_WB);
     const double g = T.gravity;
     const double hL = uL[0], mL = uL[1], hR = uR[0], mR = uR[1];
-    const double lam = max_nonneg(swe_speed(hL, mL, g), swe_speed(hR, mR, g));
+    const double lam =
+        max_nonneg(swe_speed(hL, mL, T.sqrt_gravity), swe_speed(hR, mR, T.sqrt_gravity));
     const double vL = mL * drcp(hL), vR = mR * drcp(hR);
     const double fL = WB ? mL * vL : fma(0.5 * g * hL, hL, mL * vL);
     const double fR = WB ? mR * vR : fma(0.5 * g * hR, hR, mR * vR);
@@ -418,7 +419,8 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
       const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
                    hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
       const double g = T.gravity;
-      const double lam = max_nonneg(swe_speed(hm, mm, g), swe_speed(hp, mp, g));
+      const double lam =
+          max_nonneg(swe_speed(hm, mm, T.sqrt_gravity), swe_speed(hp, mp, T.sqrt_gravity));
       const double dUh = WB ? (Hp + bp * T.inv_b0) - (Hm + bm * T.inv_b0) : Hp - Hm;
       const double Fn0 = fma(-0.5 * lam, dUh, 0.5 * (Mm + Mp));
       const double Fn1 = fma(-0.5 * lam, Mp - Mm, 0.5 * (Fm + Fp));
@@ -495,7 +497,8 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
                    bm = tr_r[5];
       const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
                    hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
-      const double lam = max_nonneg(swe_speed(hm, mm, T.gravity), swe_speed(hp, mp, T.gravity));
+      const double lam =
+          max_nonneg(swe_speed(hm, mm, T.sqrt_gravity), swe_speed(hp, mp, T.sqrt_gravity));
       // F_h = U_m (the h flux is the momentum)
       const double dFh = Mp - Mm;
       const double dFm = Fp - Fm, dUm = Mp - Mm;
@@ -601,7 +604,7 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
           double mb = T.w[0] * out[1][0];
 #pragma unroll
           for (int p = 1; p < n; ++p) mb = fma(T.w[p], out[1][p], mb);
-          rate = swe_speed(hb, mb, T.gravity) * xs;
+          rate = swe_speed(hb, mb, T.sqrt_gravity) * xs;
         } else {
           // the speed of advection is |a| averaged over the element
           double ab = T.w[0] * sn[0];

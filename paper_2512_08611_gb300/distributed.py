@@ -22,6 +22,27 @@ def neighbours(rank, world):
     return (rank - 1) % world, (rank + 1) % world
 
 
+def exchange_plan(rank, world):
+    """The point-to-point operations of one halo exchange in issue order:
+    (kind, buffer, peer, tag) with kind 'send' or 'recv'.
+
+    NCCL ignores tags: between two ranks it pairs the k-th send of one with
+    the k-th receive of the other.  Every rank therefore issues its two sends
+    in the order (top traces up, bottom traces down) and its two receives in
+    the order (bottom halo from below, top halo from above).  With two ranks,
+    where the rank below is also the rank above, the peer's first send (its
+    top traces) meets this rank's first receive (the bottom halo) and its
+    second send (its bottom traces) the second receive (the top halo), as the
+    ring requires; with more ranks each pair of ranks exchanges one message
+    per direction.  The tags agree with this pairing, for backends that
+    honour them (gloo)."""
+    below, above = neighbours(rank, world)
+    return [("send", "send_top", above, TAG_UP),
+            ("send", "send_bottom", below, TAG_DOWN),
+            ("recv", "recv_bottom", below, TAG_UP),
+            ("recv", "recv_top", above, TAG_DOWN)]
+
+
 def halo_exchange(send_bottom, send_top, recv_bottom, recv_top, group=None):
     """Exchange the slab-boundary traces with the two ring neighbours.
 
@@ -29,18 +50,19 @@ def halo_exchange(send_bottom, send_top, recv_bottom, recv_top, group=None):
                  rank below and becomes its ``recv_top``;
     send_top:    traces of this slab's top row (top side), goes to the rank
                  above and becomes its ``recv_bottom``.
-    With one rank the slab is its own neighbour (periodic)."""
+    With one rank the slab is its own neighbour (periodic).  The operations
+    are issued in the order of ``exchange_plan``, which pairs them without
+    relying on tags."""
     world = dist.get_world_size(group) if dist.is_initialized() else 1
     if world == 1:
         recv_top.copy_(send_bottom)
         recv_bottom.copy_(send_top)
         return
     rank = dist.get_rank(group)
-    below, above = neighbours(rank, world)
-    ops = [dist.P2POp(dist.isend, send_top, above, group, TAG_UP),
-           dist.P2POp(dist.irecv, recv_bottom, below, group, TAG_UP),
-           dist.P2POp(dist.isend, send_bottom, below, group, TAG_DOWN),
-           dist.P2POp(dist.irecv, recv_top, above, group, TAG_DOWN)]
+    bufs = {"send_bottom": send_bottom, "send_top": send_top, "recv_bottom": recv_bottom,
+            "recv_top": recv_top}
+    ops = [dist.P2POp(dist.isend if kind == "send" else dist.irecv, bufs[name], peer, group, tag)
+           for kind, name, peer, tag in exchange_plan(rank, world)]
     for req in dist.batch_isend_irecv(ops):
         req.wait()
 

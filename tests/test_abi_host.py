@@ -40,10 +40,64 @@ def test_every_declared_symbol_is_exported(crk):
 
 
 def test_config_struct_layout(crk):
-    assert ctypes.sizeof(crk.Config) == 48
+    assert ctypes.sizeof(crk.Config) == 64
     assert crk.Config.source.offset == 12
     assert crk.Config.gravity.offset == 16
     assert crk.Config.source_coef.offset == 40
+    assert crk.Config.rk.offset == 48
+    assert crk.Config.nc_face_mode.offset == 52
+    assert crk.Config.coef_dissipation.offset == 56
+    assert crk.Config.reserved.offset == 60
+
+
+def test_scheme_switches_accept_only_the_built_readings(crk):
+    """rk, nc_face_mode and coef_dissipation: the zero defaults and the
+    explicit built values create a context; the other readings of the paper
+    are refused with CRKFR_ERR_UNSUPPORTED and a reason, on every entry point
+    that takes a config (contexts, ensembles, the allocation-free step)."""
+    from paper_2512_08611_gb300.crkfr import Batch, CrkfrError, Solver
+    for N in range(5):
+        Solver("swe1d", N, rk=0)
+        Solver("swe1d", N, rk=N + 1)
+    Solver("swe1d", 2, source="chezy", source_coef=0.1, rk=3)
+    Solver("swe2d", 3, nc_face="frozen", coef_dissipation=False)
+    cases = [dict(rk=4, N=2), dict(rk=2, N=3), dict(rk=4, N=2, source="chezy", source_coef=0.1),
+             dict(nc_face="literal", N=3), dict(nc_face="stagewise", N=3),
+             dict(coef_dissipation=True, N=3)]
+    for kw in cases:
+        N = kw.pop("N")
+        with pytest.raises(CrkfrError) as e:
+            Solver("swe1d", N, **kw)
+        assert e.value.status == -2, kw
+        assert any(k in str(e.value) for k in ("rk", "nc_face_mode", "coef_dissipation")), str(e.value)
+        with pytest.raises(CrkfrError) as e:
+            Batch("swe1d", [(N, 10, 0.0, 1.0)], **kw)
+        assert e.value.status == -2
+    # values outside the enums and a non-zero reserved field are argument errors
+    h = ctypes.c_void_p()
+    for field, value in (("nc_face_mode", 7), ("coef_dissipation", 2), ("reserved", 1)):
+        cfg = crk.make_config("swe1d", 2, "gl", 9.81, 0.5, 0.0, None, 0.0)
+        setattr(cfg, field, value)
+        assert crk.lib().crkfr_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
+        assert crk.lib().crkfr_last_error(None).decode() != ""
+    # the allocation-free step checks the switches before touching the GPU
+    cfg = crk.make_config("swe1d", 2, "gl", 9.81, 0.5, 0.0, None, 0.0, nc_face="literal")
+    p = ctypes.c_void_p(16)
+    assert crk.lib().crkfr_step_1d_noalloc(ctypes.byref(cfg), 10, 0.0, 1.0, p, p, p, 0.01, 1,
+                                           None) == -2
+    assert "nc_face_mode" in crk.lib().crkfr_last_error(None).decode()
+
+
+def test_only_periodic_meshes_are_built(crk):
+    from paper_2512_08611_gb300.crkfr import CrkfrError, Solver
+    s = Solver("swe2d", 2)
+    for mask, status in ((0, -2), (1, -2), (2, -2), (4, -1), (-1, -1)):
+        arr = (ctypes.c_int64 * 2)(4, 3)
+        d2 = (ctypes.c_double * 2)
+        assert crk.lib().crkfr_set_mesh(s.h, 2, arr, d2(0.0, 0.0), d2(1.0, 1.0), mask) == status
+    with pytest.raises(CrkfrError) as e:
+        Solver("swe1d", 2).set_mesh([5], [0.0], [1.0], periodic=False)
+    assert e.value.status == -2 and "periodic" in str(e.value)
 
 
 def test_bad_configs_are_rejected(crk):
@@ -73,7 +127,7 @@ def test_bad_source_configs_are_rejected(crk):
             Solver("swe1d", 2, source="chezy", source_coef=coef)
         assert e.value.status == -1
     h = ctypes.c_void_p()
-    cfg = Config(1, 2, 0, 7, 9.81, 0.5, 0.0, 1.0)   # no such source
+    cfg = Config(1, 2, 0, 7, 9.81, 0.5, 0.0, 1.0, 0, 0, 0, 0)   # no such source
     assert crk.lib().crkfr_create(ctypes.byref(h), ctypes.byref(cfg)) == -1
     # a coefficient without a source is ignored
     Solver("swe1d", 2, source=None, source_coef=-5.0)

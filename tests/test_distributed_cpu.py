@@ -55,6 +55,30 @@ def test_halo_exchange_ring(world):
     assert all(out[r] for r in range(world))
 
 
+@pytest.mark.parametrize("world", [2, 3, 4])
+def test_exchange_pairs_by_issue_order_without_tags(world):
+    """Pair every rank's sends with its peers' receives the way NCCL does,
+    by issue order per (sender, receiver) pair and ignoring tags: each halo
+    still receives the right neighbour's traces (with two ranks the rank
+    below is also the rank above, so only the order can tell the two
+    messages apart)."""
+    from paper_2512_08611_gb300.distributed import exchange_plan, neighbours
+    sends, recvs = {}, {}
+    for r in range(world):
+        for kind, name, peer, _tag in exchange_plan(r, world):
+            (sends if kind == "send" else recvs).setdefault((r, peer) if kind == "send"
+                                                            else (peer, r), []).append(name)
+    got = {}
+    for (src, dst), names in sends.items():
+        assert len(names) == len(recvs[(src, dst)])
+        for sent, into in zip(names, recvs[(src, dst)]):
+            got[(dst, into)] = (src, sent)
+    for r in range(world):
+        below, above = neighbours(r, world)
+        assert got[(r, "recv_top")] == (above, "send_bottom")
+        assert got[(r, "recv_bottom")] == (below, "send_top")
+
+
 def _case(Ey, Ex, N, seed=3):
     from oracle.basis import Basis
     rng = np.random.default_rng(seed)

@@ -1,7 +1,8 @@
-"""The kernels replace the IEEE FP64 division 1/h and square root sqrt(g h)
-by their own routines (FP32 seed from the bit pattern, one third-order
-refinement).  Their error against the correctly rounded result must stay
-within one ulp over the range the path uses and far beyond it."""
+"""The kernels replace the IEEE FP64 division 1/h, square root sqrt(g h) and
+reciprocal square root by their own routines (FP32 seed from the bit
+pattern, one third-order refinement).  Their error against the correctly
+rounded result must stay within one ulp over the range the path uses and
+far beyond it."""
 import numpy as np
 import pytest
 
@@ -38,6 +39,15 @@ def test_sqrt_within_one_ulp(crk):
     x = samples()
     got = to_host(crk.math_check(to_dev(x), "sqrt"))
     assert np.max(ulps(got, np.sqrt(x))) <= 1.0
+
+
+def test_rsqrt_within_one_ulp(crk):
+    """1/sqrt(x) (the shallow-water wave speed and the time-step rate use it)
+    against the reciprocal square root in extended precision, rounded once."""
+    x = samples()
+    got = to_host(crk.math_check(to_dev(x), "rsqrt"))
+    ref = (1.0 / np.sqrt(x.astype(np.longdouble))).astype(np.float64)
+    assert np.max(ulps(got, ref)) <= 1.0
 
 
 def test_fp64_probe_rates_are_plausible():
