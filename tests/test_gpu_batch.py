@@ -158,3 +158,27 @@ def test_full_size_ensemble_sampled():
     for _ in range(3):
         v = sch.step(v, cs[i], sch.compute_dt(v, cs[i], golden_cfl(N, "gl"), 0.5))
     assert rel_l2(to_host(batch.state_view(u, i)), v) < 1e-12
+
+
+def test_batch_kernel_timing_counts_the_step_kernels():
+    """crkfr_batch_profile_*: every step kernel of a call without a graph is
+    timed (classes x steps launches, positive summed time); calls with a
+    graph are not; enabling again clears the sums."""
+    crk = load()
+    us, cs = inputs(MEMBERS)
+    batch = crk.Batch("swe1d", MEMBERS, gravity=G, cfl_safety=0.5)
+    u, c = packed(batch, us, cs)
+    batch.set_coefficients(c)
+    classes = len({m[0] for m in MEMBERS})
+    batch.profile(True)
+    batch.step(u, 0.0, 4, graph=False)
+    n, ms = batch.profile_read()
+    assert n == 4 * classes and ms > 0.0
+    batch.step(u, 0.0, 3, graph=True)
+    assert batch.profile_read()[0] == 4 * classes
+    batch.profile(True)
+    assert batch.profile_read() == (0, 0.0)
+    batch.profile(False)
+    batch.step(u, 0.0, 2, graph=False)
+    assert batch.profile_read() == (0, 0.0)
+    batch.status()
