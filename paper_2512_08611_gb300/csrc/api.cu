@@ -52,6 +52,7 @@ struct crkfr_ctx {
   // last step back while the face kernel updates the next rows
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_rows[kHostChunks] = {};
+  cudaEvent_t ev_in[kHostChunks] = {};   // upload parts arrived (upload_ahead)
   cudaEvent_t ev_copied = nullptr;
   DevState* d_state = nullptr;
   bool coef_set = false;
@@ -264,13 +265,20 @@ crkfr_status launch_rate(crkfr_ctx* c, const double* u, int slot, cudaStream_t s
 // of part 0, then local of part k+1 before the face kernel of part k.  The
 // local kernels read only their own rows of u, which no earlier face kernel
 // of this step writes.  The first local launch does the step's bookkeeping.
-crkfr_status step_with_readback(crkfr_ctx* c, Launch2D L, const double* u, double* host_out,
-                                cudaStream_t s) {
+crkfr_status ensure_copy_stream(crkfr_ctx* c) {
   if (!c->copy_stream) {
     CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     for (auto& ev : c->ev_rows) CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    for (auto& ev : c->ev_in) CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     CK(c, cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
   }
+  return CRKFR_OK;
+}
+
+crkfr_status step_with_readback(crkfr_ctx* c, Launch2D L, const double* u, double* host_out,
+                                cudaStream_t s) {
+  crkfr_status sc = ensure_copy_stream(c);
+  if (sc != CRKFR_OK) return sc;
   const int64_t Ey = c->Ey, Ne = c->Ex * c->Ey;
   const int64_t nn = (int64_t)c->basis.n * c->basis.n;
   int64_t rows = (Ey + kHostChunks - 1) / kHostChunks;
@@ -318,17 +326,68 @@ crkfr_status step_with_readback(crkfr_ctx* c, Launch2D L, const double* u, doubl
   return CRKFR_OK;
 }
 
+// The upload of a host state for crkfr_step_host (2D standard form): the
+// rows are copied in parts on the copy stream, and as soon as a part has
+// arrived the compute stream computes its wave-speed rate (CFL mode) and the
+// first stage's local operator L(u^n), which needs no time step, into the
+// work buffer; the step then starts from those (run_steps, first_ahead).  So
+// that work, about an eighth of the step, overlaps the upload, which the CFL
+// step cannot otherwise overlap: its time step needs the rate of every
+// element.
+crkfr_status upload_ahead(crkfr_ctx* c, const double* host_in, double* u, bool cfl_mode,
+                          cudaStream_t s) {
+  crkfr_status st = ensure_copy_stream(c);
+  if (st != CRKFR_OK) return st;
+  const int64_t Ey = c->Ey, Ne = c->Ex * c->Ey;
+  const int64_t nn = (int64_t)c->basis.n * c->basis.n;
+  int64_t rows = (Ey + kHostChunks - 1) / kHostChunks;
+  rows = (rows + 7) / 8 * 8;
+  const int parts = (int)((Ey + rows - 1) / rows);
+  const int slot = (int)(c->nstep % 3);
+  if (cfl_mode) CK(c, cudaMemsetAsync(c->d_state->rate, 0, sizeof(c->d_state->rate), s));
+  // the copies into u follow everything queued on s before this call
+  CK(c, cudaEventRecord(c->ev_copied, s));
+  CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_copied, 0));
+  for (int k = 0; k < parts; ++k) {
+    const int64_t rb = (int64_t)k * rows, re = rb + rows < Ey ? rb + rows : Ey;
+    const size_t off = (size_t)(rb * c->Ex) * nn;
+    const size_t bytes = sizeof(double) * (size_t)((re - rb) * c->Ex) * nn;
+    for (int v = 0; v < c->M; ++v)
+      CK(c, cudaMemcpyAsync(u + v * Ne * nn + off, host_in + v * Ne * nn + off, bytes,
+                            cudaMemcpyHostToDevice, c->copy_stream));
+    CK(c, cudaEventRecord(c->ev_in[k], c->copy_stream));
+    CK(c, cudaStreamWaitEvent(s, c->ev_in[k], 0));
+    Launch2D L = make2d(c);
+    L.u_in = u;
+    L.row_begin = rb;
+    L.row_end = re;
+    if (cfl_mode) {
+      int e = timed(c, CRKFR_KERNEL_RATE, s, [&] { return launch_rate_2d(L, slot, s); });
+      if (e) return cuda_fail(c, e, "rate kernel");
+      c->launches += 1;
+    }
+    int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d_first(L, s); });
+    if (e) return cuda_fail(c, e, "2D local kernel (first stage)");
+    c->launches += 1;
+  }
+  return CRKFR_OK;
+}
+
 // nsteps steps of u in place.  dt > 0 fixed, otherwise CFL (clipped to t_end).
 // host_out (2D, optional): the last step runs in row parts and each part's
 // rows are copied to host_out on the context's copy stream as soon as they
 // are final (step_with_readback); the caller's stream waits for the copies.
 // *copied tells whether that happened.
 crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, double t_end,
-                       cudaStream_t s, double* host_out = nullptr, bool* copied = nullptr) {
+                       cudaStream_t s, double* host_out = nullptr, bool* copied = nullptr,
+                       bool first_ahead = false) {
   if (copied) *copied = false;
   if (nsteps <= 0) return CRKFR_OK;
   const bool cfl_mode = !(dt > 0.0);
-  if (cfl_mode) {
+  // first_ahead (2D standard form): the caller has already computed the
+  // first stage's local operator of u into the work buffer and, in the CFL
+  // mode, the rate of u into slot nstep % 3 (upload_ahead)
+  if (cfl_mode && !first_ahead) {
     CK(c, cudaMemsetAsync(c->d_state->rate, 0, sizeof(c->d_state->rate), s));
     crkfr_status st = launch_rate(c, u, (int)(c->nstep % 3), s);
     if (st != CRKFR_OK) return st;
@@ -387,6 +446,7 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
       L.ctl = ctl;
       L.u_in = u;
       L.u_out = u;
+      L.pre = (first_ahead && k == 0) ? 2 : 0;
       if (c->limit_mode != CRKFR_LIMITER_NONE) {
         int ea = timed(c, CRKFR_KERNEL_INDICATOR, s,
                        [&] { return launch_alpha_2d(L, c->d_alpha_raw, c->d_alpha, s); });
@@ -531,6 +591,7 @@ void crkfr_destroy(crkfr_ctx* c) {
     if (c->copy_stream) {
       cudaStreamDestroy(c->copy_stream);
       for (auto ev : c->ev_rows) cudaEventDestroy(ev);
+      for (auto ev : c->ev_in) cudaEventDestroy(ev);
       cudaEventDestroy(c->ev_copied);
     }
     if (prev != c->device && prev >= 0) cudaSetDevice(prev);
@@ -823,12 +884,25 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
       return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
     }
   }
-  CK(c, cudaMemcpyAsync(c->d_stage, u_in, bytes, cudaMemcpyHostToDevice, s));
-  // 2D: the last step's rows are read back while the face kernel finishes
-  // the rows after them
+  // 2D standard form: the upload runs in parts, overlapped with the rate and
+  // the first stage's local operator of the parts already there; otherwise
+  // one copy.  The last step's rows are read back while the face kernel
+  // finishes the rows after them.
+  const bool ahead = c->dim == 2 && nsteps > 0 && c->cfg.system == CRKFR_SYS_SWE_2D &&
+                     c->cfg.source == CRKFR_SRC_NONE && c->limit_mode == CRKFR_LIMITER_NONE;
+  if (ahead) {
+    st = upload_ahead(c, u_in, c->d_stage, !(dt > 0.0), s);
+    if (st != CRKFR_OK) {
+      if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+      cudaStreamSynchronize(s);
+      return st;
+    }
+  } else {
+    CK(c, cudaMemcpyAsync(c->d_stage, u_in, bytes, cudaMemcpyHostToDevice, s));
+  }
   bool copied = false;
   st = run_steps(c, c->d_stage, dt, nsteps, std::numeric_limits<double>::infinity(), s,
-                 c->dim == 2 ? u_out : nullptr, &copied);
+                 c->dim == 2 ? u_out : nullptr, &copied, ahead);
   if (st != CRKFR_OK) {
     // copies already queued on the copy stream still target u_out
     if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);

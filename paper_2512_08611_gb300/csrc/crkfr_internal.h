@@ -223,6 +223,10 @@ struct Launch2D {
   // recorded steps (crkfr_step_record): the local kernel also stores the
   // inner stage values 1..S-1, [S-1][3][Ey][Ex][n][n]
   double* stages;
+  // local operator of the first stage computed ahead (the host-buffer step
+  // overlaps it with the upload of the state): 1 = compute L(u^n) only and
+  // store it in w; 2 = the step, reading L(u^n) from w (standard form only)
+  int pre;
 };
 // Adjoint of one 2D step (kernels_adj2d.cu); the forward local kernel must
 // have written the traces of u^n first.
@@ -251,7 +255,8 @@ struct Launch2DAdj {
 int launch_local_2d_stages(const Launch2D& L, void* stream);
 int launch_adjoint_2d(const Launch2DAdj& A, void* stream);   // A.stages null or not
 
-int launch_local_2d(const Launch2D& L, void* stream);
+int launch_local_2d(const Launch2D& L, void* stream);   // L.pre 0 or 2
+int launch_local_2d_first(const Launch2D& L, void* stream);   // L_0 only (pre = 1)
 int launch_local_2d_imex(const Launch2D& L, void* stream);   // kernels_imex.cu
 int launch_face_2d(const Launch2D& L, void* stream);
 // well-balanced instantiations (kernels_wb.cu)

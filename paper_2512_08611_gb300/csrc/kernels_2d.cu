@@ -43,9 +43,10 @@ __global__ void __launch_bounds__(kBlock2D) k_rate_2d(const Launch2D L, int slot
   constexpr int nn = n * n;
   const Tables& T = L.tab;
   const int64_t Ne = L.Ex * L.Ey;
-  const int64_t e = (int64_t)blockIdx.x * kBlock2D + threadIdx.x;
+  // the elements of the rows [row_begin, row_end)
+  const int64_t e = L.row_begin * L.Ex + (int64_t)blockIdx.x * kBlock2D + threadIdx.x;
   double rate = 0.0;
-  if (e < Ne) {
+  if (e < L.row_end * L.Ex) {
     double m[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
@@ -125,7 +126,45 @@ __global__ void k_coef_2d(int64_t Ex, int64_t Ey, const double* __restrict__ c, 
 }  // namespace
 
 
+namespace {
+
+template <int N, bool GLL, int PRE>
+int launch_local_pre_t(const Launch2D& L, cudaStream_t s) {
+  constexpr int per_block = kWarpsLocal * (32 / (N + 1));
+  if (L.row_begin < 0 || L.row_end <= L.row_begin || L.row_end > L.Ey)
+    return (int)cudaErrorInvalidValue;
+  const int64_t blocks = ((L.row_end - L.row_begin) * L.Ex + per_block - 1) / per_block;
+  if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
+  k_local_2d<N, GLL, false, false, false, false, false, PRE>
+      <<<(unsigned)blocks, kBlockLocal, 0, s>>>(L);
+  return (int)cudaGetLastError();
+}
+
+template <int PRE>
+int launch_local_pre(const Launch2D& L, cudaStream_t s) {
+  if (L.imex || L.wb || L.lim.mode != CRKFR_LIMITER_NONE || L.ctl.residual)
+    return (int)cudaErrorInvalidValue;
+  switch (L.N * 2 + (L.gll ? 1 : 0)) {
+    case 2: return launch_local_pre_t<1, false, PRE>(L, s);
+    case 3: return launch_local_pre_t<1, true, PRE>(L, s);
+    case 4: return launch_local_pre_t<2, false, PRE>(L, s);
+    case 5: return launch_local_pre_t<2, true, PRE>(L, s);
+    case 6: return launch_local_pre_t<3, false, PRE>(L, s);
+    case 7: return launch_local_pre_t<3, true, PRE>(L, s);
+    case 8: return launch_local_pre_t<4, false, PRE>(L, s);
+    case 9: return launch_local_pre_t<4, true, PRE>(L, s);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int launch_local_2d_first(const Launch2D& L, void* stream) {
+  return launch_local_pre<1>(L, (cudaStream_t)stream);
+}
+
 int launch_local_2d(const Launch2D& L, void* stream) {
+  if (L.pre == 2) return launch_local_pre<2>(L, (cudaStream_t)stream);
   if (L.lim.mode != CRKFR_LIMITER_NONE && !L.ctl.residual) return launch_local_2d_limit(L, stream);
   if (L.wb) return launch_local_2d_wb(L, stream);
   if (L.imex) return launch_local_2d_imex(L, stream);
@@ -140,7 +179,9 @@ int launch_face_2d(const Launch2D& L, void* stream) {
 
 int launch_rate_2d(const Launch2D& L, int slot, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  const unsigned blocks = (unsigned)((L.Ex * L.Ey + kBlock2D - 1) / kBlock2D);
+  if (L.row_begin < 0 || L.row_end <= L.row_begin || L.row_end > L.Ey)
+    return (int)cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)(((L.row_end - L.row_begin) * L.Ex + kBlock2D - 1) / kBlock2D);
   switch (L.N) {
     case 1: k_rate_2d<1><<<blocks, kBlock2D, 0, s>>>(L, slot); break;
     case 2: k_rate_2d<2><<<blocks, kBlock2D, 0, s>>>(L, slot); break;

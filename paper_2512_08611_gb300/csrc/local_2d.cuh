@@ -44,10 +44,16 @@ constexpr int kTrFields = 7;
 // hu and hv), h^n, hu^n.  y-face trace fields: U_h, U_hu, U_hv, G_hu, G_hv,
 // h^n, hv^n.  (The time-averaged h fluxes are U_hu and U_hv.)
 
-template <int N, bool GLL, bool RES, bool IMEX, bool WB, bool LIMIT = false, bool STAGES = false>
+template <int N, bool GLL, bool RES, bool IMEX, bool WB, bool LIMIT = false, bool STAGES = false,
+          int PRE = 0>
 __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(const Launch2D L) {
   static_assert(!(STAGES && (IMEX || WB || LIMIT)), "stages are recorded for the standard form");
+  // PRE 1: only the first stage's local operator L(u^n), which needs no dt,
+  // stored in L.w; PRE 2: the step, taking L(u^n) from L.w (same arithmetic)
+  static_assert(PRE == 0 || !(RES || IMEX || WB || LIMIT || STAGES),
+                "the first-stage pre-pass is built for the standard form");
   using TB = Tab<N, IMEX>;
+  static_assert(PRE == 0 || TB::need_L(0), "the first stage has a local operator");
   constexpr int n = N + 1;
   constexpr int nn = n * n;
   constexpr int EPW = 32 / n;          // elements per warp
@@ -71,8 +77,8 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
   const int lec = lane_ok ? le : 0;
   double (*X)[n][n] = sm[warp][lec];
 
-  const double dt = RES ? L.ctl.dt_fixed : step_dt(L.ctl, L.st);
-  if (!RES && blockIdx.x == 0 && threadIdx.x == 0 && !L.ctl.skip_bookkeeping)
+  const double dt = (RES || PRE == 1) ? L.ctl.dt_fixed : step_dt(L.ctl, L.st);
+  if (!RES && PRE != 1 && blockIdx.x == 0 && threadIdx.x == 0 && !L.ctl.skip_bookkeeping)
     step_bookkeeping(L.ctl, L.st, dt);
 
   // ---- load row q of u^n and of the static terms g b_x, g b_y ---------------
@@ -88,6 +94,14 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
   }
 
   double Ls[S][3][n];
+  if constexpr (PRE == 2) {
+    // this row of L(u^n), computed ahead by the PRE 1 instantiation; the
+    // thread overwrites the same values with W at the end
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) Ls[0][v][p] = L.w[(v * Ne + ge) * nn + q * n + p];
+  }
   double Ss[S][2][n];                  // source of hu, hv at each stage (IMEX)
   double V[3][n], U[3][n], F2[n], F3[n], G3[n];
   double Sb[2][n];                     // sum_j (b_j/b_ref) s(u^(j)) (IMEX)
@@ -166,51 +180,63 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
         f3[p] = mx * vy;
       }
       // y-fluxes (hv, hu hv / h, hv^2/h + g h^2/2) go through shared memory
-      __syncwarp();
-      if (lane_ok) {
+      // (not for the first stage of PRE 2: its operator was loaded)
+      if (!(PRE == 2 && i == 0)) {
+        __syncwarp();
+        if (lane_ok) {
+#pragma unroll
+          for (int p = 0; p < n; ++p) {
+            X[0][q][p] = cur[2][p];
+            X[1][q][p] = f3[p];
+            X[2][q][p] = g3[p];
+            if (WB) X[3][q][p] = cur[0][p];
+          }
+        }
+        __syncwarp();
 #pragma unroll
         for (int p = 0; p < n; ++p) {
-          X[0][q][p] = cur[2][p];
-          X[1][q][p] = f3[p];
-          X[2][q][p] = g3[p];
-          if (WB) X[3][q][p] = cur[0][p];
-        }
-      }
-      __syncwarp();
+          // non-conservative factors: g b_x, g b_y, and for the well-balanced
+          // form also g h_x, g h_y
+          double nbx = gbx[p], nby = gby[p];
+          if (WB) {
+            double hx = T.Dx[p][0] * cur[0][0];
+            double hy = T.Dy[q][0] * X[3][0][p];
 #pragma unroll
-      for (int p = 0; p < n; ++p) {
-        // non-conservative factors: g b_x, g b_y, and for the well-balanced
-        // form also g h_x, g h_y
-        double nbx = gbx[p], nby = gby[p];
-        if (WB) {
-          double hx = T.Dx[p][0] * cur[0][0];
-          double hy = T.Dy[q][0] * X[3][0][p];
+            for (int j = 1; j < n; ++j) {
+              hx = fma(T.Dx[p][j], cur[0][j], hx);
+              hy = fma(T.Dy[q][j], X[3][j][p], hy);
+            }
+            nbx = fma(T.gravity, hx, nbx);
+            nby = fma(T.gravity, hy, nby);
+          }
+          double a0 = T.Dy[q][0] * X[0][0][p];
+          double a1 = fma(cur[0][p], nbx, T.Dy[q][0] * X[1][0][p]);
+          double a2 = fma(cur[0][p], nby, T.Dy[q][0] * X[2][0][p]);
 #pragma unroll
           for (int j = 1; j < n; ++j) {
-            hx = fma(T.Dx[p][j], cur[0][j], hx);
-            hy = fma(T.Dy[q][j], X[3][j][p], hy);
+            a0 = fma(T.Dy[q][j], X[0][j][p], a0);
+            a1 = fma(T.Dy[q][j], X[1][j][p], a1);
+            a2 = fma(T.Dy[q][j], X[2][j][p], a2);
           }
-          nbx = fma(T.gravity, hx, nbx);
-          nby = fma(T.gravity, hy, nby);
-        }
-        double a0 = T.Dy[q][0] * X[0][0][p];
-        double a1 = fma(cur[0][p], nbx, T.Dy[q][0] * X[1][0][p]);
-        double a2 = fma(cur[0][p], nby, T.Dy[q][0] * X[2][0][p]);
 #pragma unroll
-        for (int j = 1; j < n; ++j) {
-          a0 = fma(T.Dy[q][j], X[0][j][p], a0);
-          a1 = fma(T.Dy[q][j], X[1][j][p], a1);
-          a2 = fma(T.Dy[q][j], X[2][j][p], a2);
+          for (int j = 0; j < n; ++j) {
+            a0 = fma(T.Dx[p][j], cur[1][j], a0);
+            a1 = fma(T.Dx[p][j], f2[j], a1);
+            a2 = fma(T.Dx[p][j], f3[j], a2);
+          }
+          Ls[i][0][p] = a0;
+          Ls[i][1][p] = a1;
+          Ls[i][2][p] = a2;
         }
+      }
+      if constexpr (PRE == 1) {
+        if (active) {
 #pragma unroll
-        for (int j = 0; j < n; ++j) {
-          a0 = fma(T.Dx[p][j], cur[1][j], a0);
-          a1 = fma(T.Dx[p][j], f2[j], a1);
-          a2 = fma(T.Dx[p][j], f3[j], a2);
+          for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int p = 0; p < n; ++p) L.w[(v * Ne + ge) * nn + q * n + p] = Ls[0][v][p];
         }
-        Ls[i][0][p] = a0;
-        Ls[i][1][p] = a1;
-        Ls[i][2][p] = a2;
+        return;
       }
       // time averages with the weights b_i / b_ref (first weighted stage: a copy)
       if (wi != 0.0) {

@@ -164,10 +164,13 @@ def test_checkpoint_resume_repeats_the_run():
 @pytest.mark.parametrize("Ex,Ey", [(5, 3), (7, 8), (6, 37), (3, 70)])
 @pytest.mark.parametrize("limited", [False, True])
 def test_host_step_reads_rows_back_in_chunks(crk, Ex, Ey, limited):
-    """crkfr_step_host runs the last face kernel in chunks of element rows and
-    copies each chunk back while the next one computes: the result is the
-    device step's, bit for bit (CFL steps, one and three per call, with and
-    without the limiter), from pinned and from ordinary host memory."""
+    """crkfr_step_host uploads the state in parts of element rows while the
+    rate and the first stage's local operator of the parts already there are
+    computed, runs the last face kernel in chunks of rows and copies each
+    chunk back while the next one computes: the result is the device step's,
+    bit for bit (CFL steps, one and three per call, with and without the
+    limiter, and fixed steps in place), from pinned and from ordinary host
+    memory."""
     import torch
     N = 3
     u, b, dx, dy = swe2d_case(N, "gl", Ex, Ey)
@@ -186,6 +189,16 @@ def test_host_step_reads_rows_back_in_chunks(crk, Ex, Ey, limited):
         assert np.array_equal(plain, to_host(du))
         # two host calls from the same state: twice the simulated time
         assert s2.time()[0] == pytest.approx(2 * s1.time()[0], rel=1e-15)
+    # a fixed step (no rate in the upload) and a second call in place
+    s1 = solver(crk, N, "gl", Ex, Ey, b)
+    s2 = solver(crk, N, "gl", Ex, Ey, b)
+    dt = 0.5 * s1.compute_dt(to_dev(u))
+    du = to_dev(u)
+    s1.step(du, dt, 2)
+    h = torch.tensor(u).pin_memory().numpy()
+    s2.step_host(h, h, dt=dt, nsteps=1)
+    s2.step_host(h, h, dt=dt, nsteps=1)
+    assert np.array_equal(h, to_host(du))
 
 
 def test_thousand_steps_2d(crk):
