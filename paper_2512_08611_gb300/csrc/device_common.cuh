@@ -103,6 +103,14 @@ __device__ __forceinline__ double swe_rate_2d(double h, double mx, double my, do
   return fma(fma(fabs(mx), rr, c), inv_dx, fma(fabs(my), rr, c) * inv_dy);
 }
 
+// Doubles per element in a shared-memory exchange area of `fields` n x n
+// fields, padded to 2 mod 16: consecutive elements then start 16 bytes apart
+// modulo the 32 banks, so the lanes of a warp that read the same row and
+// column of different elements hit different banks.
+__host__ __device__ constexpr int exchange_stride(int fields, int n) {
+  return (fields * n * n + 13) / 16 * 16 + 2;
+}
+
 // max of two non-negative doubles through their bit patterns (integer pipe)
 __device__ __forceinline__ double max_nonneg(double a, double b) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);

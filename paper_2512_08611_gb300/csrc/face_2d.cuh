@@ -172,11 +172,12 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
   const Tables& T = L.tab;
   // x faces: [row][face k between elements k-1 and k][node]; y faces:
   // [face k between rows k-1 and k][column][node]; both sides, 3 variables
-  __shared__ double sxm[TY][TX + 1][n][3], sxp[TY][TX + 1][n][3];
-  __shared__ double sym[TY + 1][TX][n][3], syp[TY + 1][TX][n][3];
+  // (the variable outermost: the lanes of a warp touch consecutive doubles)
+  __shared__ double sxm[3][TY][TX + 1][n], sxp[3][TY][TX + 1][n];
+  __shared__ double sym[3][TY + 1][TX][n], syp[3][TY + 1][TX][n];
   // limiter: the face fluxes F^-, F^+ of the first-order update
-  __shared__ double fxm[LY][LX + 1][n][3], fxp[LY][LX + 1][n][3];
-  __shared__ double fym[LY + 1][LX][n][3], fyp[LY + 1][LX][n][3];
+  __shared__ double fxm[3][LY][LX + 1][n], fxp[3][LY][LX + 1][n];
+  __shared__ double fym[3][LY + 1][LX][n], fyp[3][LY + 1][LX][n];
 
   const int64_t Ex = L.Ex, Ey = L.Ey, Ne = Ex * Ey, ts = Ne * n;
   const int64_t ex0 = (int64_t)blockIdx.x * TX, ey0 = L.row_begin + (int64_t)blockIdx.y * TY;
@@ -218,8 +219,8 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
         face_limited<0, WB>(a, b, lm, lp, af, c2 * T.inv_w[N], c2 * T.inv_w[0], T, Tm, Tp, Fm, Fp);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          fxm[r][k][q][v] = Fm[v];
-          fxp[r][k][q][v] = Fp[v];
+          fxm[v][r][k][q] = Fm[v];
+          fxp[v][r][k][q] = Fp[v];
         }
       } else {
         face_terms<WB>(a, b, 1, L.sface[ep * n + q], T.gravity, T.inv_gravity, T.sqrt_gravity,
@@ -227,8 +228,8 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
       }
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        sxm[r][k][q][v] = Tm[v];
-        sxp[r][k][q][v] = Tp[v];
+        sxm[v][r][k][q] = Tm[v];
+        sxp[v][r][k][q] = Tp[v];
       }
     } else {
       const int g = f - NX;
@@ -258,8 +259,8 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
         face_limited<1, WB>(a, b, lm, lp, af, c2 * T.inv_w[N], c2 * T.inv_w[0], T, Tm, Tp, Fm, Fp);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          fym[k][c][p][v] = Fm[v];
-          fyp[k][c][p][v] = Fp[v];
+          fym[v][k][c][p] = Fm[v];
+          fyp[v][k][c][p] = Fp[v];
         }
       } else {
         face_terms<WB>(a, b, 2, L.sface[Ne * n + (ey0 + k) * plane + ex * n + p], T.gravity,
@@ -267,8 +268,8 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
       }
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        sym[k][c][p][v] = Tm[v];
-        syp[k][c][p][v] = Tp[v];
+        sym[v][k][c][p] = Tm[v];
+        syp[v][k][c][p] = Tp[v];
       }
     }
   }
@@ -288,10 +289,10 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
 #pragma unroll
     for (int p = 0; p < n; ++p) {
       double o = L.w[(v * Ne + ge) * nn + q * n + p];
-      if (!GLL || p == N) o = fma(sxm[r][cc + 1][q][v], cor[0][p], o);
-      if (!GLL || p == 0) o = fma(sxp[r][cc][q][v], cor[1][p], o);
-      if (!GLL || q == N) o = fma(sym[r + 1][cc][p][v], cor[2][q], o);
-      if (!GLL || q == 0) o = fma(syp[r][cc][p][v], cor[3][q], o);
+      if (!GLL || p == N) o = fma(sxm[v][r][cc + 1][q], cor[0][p], o);
+      if (!GLL || p == 0) o = fma(sxp[v][r][cc][q], cor[1][p], o);
+      if (!GLL || q == N) o = fma(sym[v][r + 1][cc][p], cor[2][q], o);
+      if (!GLL || q == 0) o = fma(syp[v][r][cc][p], cor[3][q], o);
       out[v][p] = o;
     }
   if constexpr (LIMIT) {
@@ -308,10 +309,10 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
         double o = L.lim.ulo[(v * Ne + ge) * nn + q * n + p];
-        if (p == 0) o = fma(ax0, fxp[r][cc][q][v], o);
-        if (p == N) o = fma(-axN, fxm[r][cc + 1][q][v], o);
-        if (q == 0) o = fma(ay0, fyp[r][cc][p][v], o);
-        if (q == N) o = fma(-ayN, fym[r + 1][cc][p][v], o);
+        if (p == 0) o = fma(ax0, fxp[v][r][cc][q], o);
+        if (p == N) o = fma(-axN, fxm[v][r][cc + 1][q], o);
+        if (q == 0) o = fma(ay0, fyp[v][r][cc][p], o);
+        if (q == N) o = fma(-ayN, fym[v][r + 1][cc][p], o);
         x[v] = o;
       }
       if constexpr (IMEX) {

@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(kBlockAdj) k_local_adj_2d(const Launch2DAdj A)
   constexpr int EPW = 32 / n;
   constexpr int S = tab_stages(N);
   const Tables& T = A.tab;
-  __shared__ double sm[kWarpsAdj][EPW][3][n][n];
+  constexpr int ES = exchange_stride(3, n);
+  __shared__ __align__(16) double sm[kWarpsAdj][EPW * ES];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int le = lane / n, q = lane - le * n;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kBlockAdj) k_local_adj_2d(const Launch2DAdj A)
   const bool active = lane_ok && g < Ne;
   const int64_t ge = active ? g : 0;
   const int lec = lane_ok ? le : 0;
-  double (*X)[n][n] = sm[warp][lec];
+  double (*X)[n][n] = reinterpret_cast<double (*)[n][n]>(&sm[warp][lec * ES]);
   const int64_t ey = ge / Ex, ex = ge - ey * Ex;
   const double dt = A.dt;
   constexpr double b0 = tab_b(N, 0);

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
   constexpr int NB = 4;                // fields per shared-memory exchange round
   const Tables& T = L.tab;
   // (the limiter's first-order part exchanges kLimRowFields fields at once)
-  __shared__ double sm[kWarpsLocal][EPW][LIMIT ? kLimRowFields : NB][n][n];
+  constexpr int ES = exchange_stride(LIMIT ? kLimRowFields : NB, n);
+  __shared__ __align__(16) double sm[kWarpsLocal][EPW * ES];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int le = lane / n, q = lane - le * n;
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kBlockLocal, CRKFR_LOCAL2D_MINB) k_local_2d(co
   const bool active = lane_ok && (g < L.row_end * L.Ex);
   const int64_t ge = active ? g : 0;
   const int lec = lane_ok ? le : 0;
-  double (*X)[n][n] = sm[warp][lec];
+  double (*X)[n][n] = reinterpret_cast<double (*)[n][n]>(&sm[warp][lec * ES]);
 
   const double dt = (RES || PRE == 1) ? L.ctl.dt_fixed : step_dt(L.ctl, L.st);
   if (!RES && PRE != 1 && blockIdx.x == 0 && threadIdx.x == 0 && !L.ctl.skip_bookkeeping)
