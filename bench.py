@@ -340,27 +340,34 @@ def run_ours(args, wl):
     from paper_2512_08611_gb300 import crkfr
 
     split = world > 1
-    if split and wl.dim != 2:
-        raise SystemExit("multi-GPU runs use the 2D workload")
+    if split and wl.limiter:
+        raise SystemExit("multi-GPU runs use the unlimited workloads")
     s = crkfr.Solver(wl.system, wl.N, gravity=G, cfl_safety=0.5, source=wl.source,
                      source_coef=wl.source_coef)
-    if split:
+    if split and wl.dim == 2:
         # weak scaling: this rank's slab is a full 1024 x 1024 workload, stacked
         # in y with the other ranks' slabs into one periodic mesh
         s.set_mesh(list(wl.E), [0.0, rank * wl.L], [wl.L, (rank + 1) * wl.L])
         s.set_subdomain(True)
+    elif split:
+        # 1D: this rank's range is a full workload mesh, the ranges side by side
+        s.set_mesh(list(wl.E), [rank * wl.L], [(rank + 1) * wl.L])
+        s.set_subdomain(True)
     else:
         s.set_mesh(list(wl.E), [0.0] * wl.dim, [wl.L] * wl.dim)
     pos = s.positions()
-    if split:
+    if split and wl.dim == 2:
         pos = (pos[0], pos[1] - rank * wl.L)
+    elif split:
+        pos = pos - rank * wl.L
     u0, b = wl.inputs(pos if wl.dim == 2 else (pos,))
     u = torch.tensor(u0, dtype=torch.float64, device="cuda")
     if split:
-        # slabs are identical (the inputs are periodic over one slab height), so
-        # the rows below and above this slab are its own top and bottom rows
-        Ey = wl.E[1]
-        b = np.ascontiguousarray(b[[Ey - 1] + list(range(Ey)) + [0]])
+        # slabs (ranges) are identical (the inputs are periodic over one of
+        # them), so the rows (elements) beyond this one's ends are its own
+        # last and first ones
+        K = wl.E[-1]
+        b = np.ascontiguousarray(b[[K - 1] + list(range(K)) + [0]])
     s.set_coefficients(torch.tensor(b, dtype=torch.float64, device="cuda"))
     if wl.limiter:
         s.set_limiter(wl.limiter)
@@ -485,8 +492,10 @@ def run_ours(args, wl):
                    "cfl_safety": 0.5, "cfl": s.cfl(), "dt_last": dt_last, "t_sim": t_sim,
                    "l2": "no flush: state + work buffers ~3 GB >> 129 MB L2",
                    "parallelism": "single GPU" if world == 1 else
-                   f"{world} slabs of a 1024 x {1024 * world} mesh, one NCCL trace exchange per step, "
-                   f"fixed dt {dt_fixed:.6g}"},
+                   (f"{world} slabs of a 1024 x {1024 * world} mesh, one NCCL trace exchange per "
+                    f"step, fixed dt {dt_fixed:.6g}" if wl.dim == 2 else
+                    f"{world} ranges of a {wl.E[0] * world}-element periodic mesh, one NCCL "
+                    f"exchange of the end elements per step, fixed dt {dt_fixed:.6g}")},
         "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": traffic, "avg_launch_ms": avg_ms,

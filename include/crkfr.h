@@ -229,7 +229,7 @@ crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_
                              double dt, int64_t nsteps, void* stream);
 
 /* Domain decomposition of the 2D step into horizontal slabs (one per rank
- * or per GPU).  The only coupling of a cRK-FR step across the slab boundary
+ * or per GPU), and of the 1D step into element ranges (below).  The only coupling of a cRK-FR step across the slab boundary
  * is the face Riemann problem after the element-local stages (Sec. 3), so a
  * step of a slab is: crkfr_step_local; exchange of one block of face traces
  * with each neighbour; crkfr_step_faces.
@@ -254,7 +254,22 @@ crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_
  * crkfr_step_local runs the element-local kernel with the step dt > 0 and
  * writes the send blocks; crkfr_step_faces (after recv_bottom and recv_top
  * have been filled) solves the face problems, applies the corrections and
- * writes u_dev in place. */
+ * writes u_dev in place.
+ *
+ * 1D: the same entry points make a context one contiguous range of elements
+ * of a periodic 1D mesh.  The fused 1D step recomputes the stages of each
+ * element's neighbours itself, so what crosses a range boundary is the
+ * state of the element beyond it: crkfr_set_coefficients expects
+ * c[E_local + 2][n] (element 0 the left neighbour element, E_local + 1 the
+ * right one); crkfr_halo_buffers gives send_bottom (the state [var][n] of
+ * this range's first element: the rank on the left stores it as its
+ * recv_top), send_top (its last element: becomes the right rank's
+ * recv_bottom), recv_bottom (the left neighbour element's state) and
+ * recv_top (the right one's), `count` = vars (N+1) doubles each, in a
+ * context-owned buffer allocated by crkfr_set_subdomain; crkfr_step_local
+ * (dt > 0) writes the send blocks; crkfr_step_faces runs the step of the
+ * range with those neighbour states and writes u_dev (through the
+ * context's work buffer).  The limiter is refused in this mode. */
 crkfr_status crkfr_set_subdomain(crkfr_ctx* ctx, int32_t enable);
 crkfr_status crkfr_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** send_top,
                                 double** recv_bottom, double** recv_top, int64_t* count);

@@ -289,13 +289,17 @@ class Solver:
         return self
 
     def set_subdomain(self, enable=True):
-        """Make the (2D) context one horizontal slab of a larger mesh; the
-        coefficient field then carries one halo row below and one above."""
+        """Make the context one part of a larger mesh: in 2D a horizontal slab
+        whose coefficient field carries one halo row below and one above, in
+        1D a range of elements whose coefficient field carries the element
+        left of it and the element right of it."""
         self._check(lib().crkfr_set_subdomain(self.h, 1 if enable else 0))
         self.subdomain = bool(enable)
         if self.shape is not None and self.dim == 2:
             n, (Ex, Ey) = self.n, self.n_elem
             self.coef_shape = (Ey + 2 if enable else Ey, Ex, n, n)
+        elif self.shape is not None:
+            self.coef_shape = (self.n_elem[0] + 2 if enable else self.n_elem[0], self.n)
 
     def halo_buffers(self):
         """(send_bottom, send_top, recv_bottom, recv_top) as float64 CUDA

@@ -46,6 +46,9 @@ struct crkfr_ctx {
   double* d_ulo = nullptr;        // 2D limiter: first-order update without face terms
   double* d_lx = nullptr;         // 2D limiter: x- and y-face data
   double* d_ly = nullptr;
+  double* d_ghost = nullptr;      // 1D subdomain: the two neighbour elements (Launch1D::ghost)
+  double* d_send = nullptr;       // 1D subdomain: this slab's two end elements' u
+  double sub_dt = 0.0;            // 1D subdomain: dt of the step between local and faces
   int limit_mode = CRKFR_LIMITER_NONE;
   double alpha_fixed = 0.0;
   // crkfr_step_host: a copy stream and events to read finished rows of the
@@ -108,6 +111,9 @@ void free_buffers(crkfr_ctx* c) {
   cudaFree(c->d_ulo);
   cudaFree(c->d_lx);
   cudaFree(c->d_ly);
+  cudaFree(c->d_ghost);
+  cudaFree(c->d_send);
+  c->d_ghost = c->d_send = nullptr;
   c->d_cnode = c->d_alpha_raw = c->d_alpha = c->d_ulo = c->d_lx = c->d_ly = nullptr;
   c->d_atrx = c->d_atry = c->d_gbar = nullptr;
   c->d_snode = c->d_sface = c->d_work = c->d_trx = c->d_try = c->d_stage = nullptr;
@@ -185,6 +191,15 @@ __global__ void k_math_check(const double* __restrict__ x, double* __restrict__ 
   out[i] = op == 0 ? drcp(x[i]) : op == 1 ? dsqrt_pos(x[i]) : drsqrt_pos(x[i]);
 }
 
+// the two end elements' states of a 1D subdomain: send[side][v][p]
+__global__ void k_pack_ends_1d(const double* __restrict__ u, double* __restrict__ send,
+                               int64_t E, int M, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * M * n) return;
+  const int side = i / (M * n), v = (i / n) % M, p = i % n;
+  send[i] = u[((int64_t)v * E + (side ? E - 1 : 0)) * n + p];
+}
+
 __global__ void k_set_time(DevState* st, int slot, double t) {
   st->time[slot] = t;
   st->time[slot ^ 1] = t;
@@ -207,6 +222,7 @@ Launch1D make1d(crkfr_ctx* c) {
   L.lim.alpha_raw = c->d_alpha_raw;
   L.lim.cnode = c->d_cnode;
   L.lim.alpha_out = c->d_alpha;
+  L.ghost = c->subdomain ? c->d_ghost : nullptr;
   return L;
 }
 
@@ -717,6 +733,19 @@ crkfr_status crkfr_set_coefficients(crkfr_ctx* c, const double* coef, void* stre
   cudaStream_t s = (cudaStream_t)stream;
   int e;
   e = timed(c, CRKFR_KERNEL_COEF, s, [&] {
+    if (c->dim == 1 && c->subdomain) {
+      // coef[E + 2][n]: the left neighbour element, the subdomain, the right
+      // neighbour element; the neighbours' static terms go to the ghosts
+      const int n = c->basis.n, gs = ghost_stride_1d(c->M, n), mn = c->M * n;
+      int r = launch_coef_1d(c->cfg.system, c->cfg.degree, c->Ex, coef + n, c->d_snode,
+                             c->d_sface, c->tab, s);
+      for (int side = 0; side < 2 && !r; ++side) {
+        double* g = c->d_ghost + side * gs;
+        r = launch_coef_1d(c->cfg.system, c->cfg.degree, 1, coef + (side ? c->Ex + 1 : 0) * n,
+                           g + mn, g + mn + n, c->tab, s);
+      }
+      return r;
+    }
     if (c->dim == 1)
       return launch_coef_1d(c->cfg.system, c->cfg.degree, c->Ex, coef, c->d_snode, c->d_sface,
                             c->tab, s);
@@ -916,9 +945,17 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
 
 crkfr_status crkfr_set_subdomain(crkfr_ctx* c, int32_t enable) {
   if (!c) return CRKFR_ERR_ARG;
-  if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "subdomains are 2D slabs");
+  if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
   if (enable && c->limit_mode != CRKFR_LIMITER_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter is built for whole periodic meshes");
+  if (enable && c->dim == 1 && !c->d_ghost) {
+    const int n = c->basis.n;
+    if (cudaMalloc(&c->d_ghost, sizeof(double) * 2 * ghost_stride_1d(c->M, n)) != cudaSuccess ||
+        cudaMalloc(&c->d_send, sizeof(double) * 2 * c->M * n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+    }
+  }
   c->subdomain = enable != 0;
   c->coef_set = false;
   return CRKFR_OK;
@@ -927,7 +964,18 @@ crkfr_status crkfr_set_subdomain(crkfr_ctx* c, int32_t enable) {
 crkfr_status crkfr_halo_buffers(crkfr_ctx* c, double** send_bottom, double** send_top,
                                 double** recv_bottom, double** recv_top, int64_t* count) {
   if (!c) return CRKFR_ERR_ARG;
-  if (c->dim != 2) return fail(c, CRKFR_ERR_STATE, "no 2D mesh set");
+  if (c->dim == 1) {
+    // the end elements' states (left = bottom, right = top) and the ghosts
+    if (!c->subdomain || !c->d_ghost) return fail(c, CRKFR_ERR_STATE, "not a 1D subdomain");
+    const int64_t mn = (int64_t)c->M * c->basis.n;
+    if (send_bottom) *send_bottom = c->d_send;
+    if (send_top) *send_top = c->d_send + mn;
+    if (recv_bottom) *recv_bottom = c->d_ghost;
+    if (recv_top) *recv_top = c->d_ghost + ghost_stride_1d(c->M, c->basis.n);
+    if (count) *count = mn;
+    return CRKFR_OK;
+  }
+  if (c->dim != 2) return fail(c, CRKFR_ERR_STATE, "no mesh set");
   const int64_t n = c->basis.n;
   const int64_t block = 7 * c->Ex * n;           // one (row, side) block of the y traces
   double* base = c->d_try;
@@ -943,12 +991,22 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* c, double** send_bottom, double** sen
 crkfr_status crkfr_step_local(crkfr_ctx* c, const double* u, double dt, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
-  if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "phased steps are 2D");
   if (c->limit_mode != CRKFR_LIMITER_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->dim == 1) {
+    // 1D: the fused step recomputes the neighbours' stages itself, so the
+    // local phase only packs this slab's end elements for the exchange
+    if (!c->subdomain) return fail(c, CRKFR_ERR_STATE, "phased 1D steps need a subdomain");
+    const int n = c->basis.n, total = 2 * c->M * n;
+    k_pack_ends_1d<<<(total + 127) / 128, 128, 0, s>>>(u, c->d_send, c->Ex, c->M, n);
+    CK(c, cudaGetLastError());
+    c->launches += 1;
+    c->sub_dt = dt;
+    return CRKFR_OK;
+  }
   StepCtl ctl{};
   ctl.dt_fixed = dt;
   ctl.cs_cfl = c->cfg.cfl_safety * c->cfl;
@@ -970,11 +1028,36 @@ crkfr_status crkfr_step_local(crkfr_ctx* c, const double* u, double dt, void* st
 crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
-  if (c->dim != 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "phased steps are 2D");
   if (c->limit_mode != CRKFR_LIMITER_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->dim == 1) {
+    // 1D: the whole fused step with the received ghosts, into the work
+    // buffer (the step reads neighbour elements of the same time level),
+    // then back into u
+    if (!c->subdomain) return fail(c, CRKFR_ERR_STATE, "phased 1D steps need a subdomain");
+    if (!(c->sub_dt > 0.0)) return fail(c, CRKFR_ERR_STATE, "crkfr_step_local first");
+    StepCtl ctl{};
+    ctl.dt_fixed = c->sub_dt;
+    ctl.cs_cfl = c->cfg.cfl_safety * c->cfl;
+    ctl.t_end = std::numeric_limits<double>::infinity();
+    ctl.slot_read = (int)(c->nstep % 3);
+    ctl.slot_write = (int)((c->nstep + 1) % 3);
+    ctl.slot_reset = (int)((c->nstep + 2) % 3);
+    ctl.tslot = (int)(c->nstep % 2);
+    Launch1D L = make1d(c);
+    L.ctl = ctl;
+    L.u_in = u;
+    L.u_out = c->d_work;
+    int e = timed(c, CRKFR_KERNEL_STEP_1D, s, [&] { return launch_step_1d(L, s); });
+    if (e) return cuda_fail(c, e, "1D step kernel");
+    CK(c, cudaMemcpyAsync(u, c->d_work, sizeof(double) * c->n_state, cudaMemcpyDeviceToDevice, s));
+    c->launches += 1;
+    c->nstep += 1;
+    c->sub_dt = 0.0;
+    return CRKFR_OK;
+  }
   StepCtl ctl{};
   ctl.dt_fixed = 1.0;   // the face kernel reads the step size the local phase stored
   ctl.slot_write = (int)((c->nstep + 1) % 3);

@@ -139,7 +139,16 @@ struct Launch1D {
   double xs;             // 1 / dx
   StepCtl ctl;
   LimitArgs lim;         // mode 0: no limiter
+  // subdomain of a larger 1D mesh: the element left of element 0 and the
+  // element right of element E-1 come from here instead of the periodic
+  // wrap; per side ghost_stride_1d(M, n) doubles: u [M][n], the static node
+  // terms [n], the face traces of c [2] (null: periodic)
+  const double* ghost;
 };
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int ghost_stride_1d(int M, int n) { return M * n + n + 2; }
 int launch_step_1d(const Launch1D& L, void* stream);
 int launch_step_1d_limit(const Launch1D& L, void* stream);   // kernels_limit.cu
 int launch_alpha_1d(const Launch1D& L, double* alpha_raw, void* stream);

@@ -173,7 +173,8 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
                                              const double* __restrict__ snode,
                                              const double* __restrict__ sface, int64_t E,
                                              int64_t tile, DevState* st, const StepCtl& ctl,
-                                             bool first_tile, const LimitArgs& LA = LimitArgs{}) {
+                                             bool first_tile, const LimitArgs& LA = LimitArgs{},
+                                             const double* __restrict__ ghost = nullptr) {
   using TB = Tab<N, IMEX>;
   constexpr int n = N + 1;
   constexpr int M = Sys1D<SYS>::M;
@@ -197,15 +198,31 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   const double dtx = dt * xs;
 
   // ---- load u^n and the static coefficient terms of this element ----------
+  // (on a subdomain the elements beyond its ends are the neighbours' ghosts)
   double u0[M][n];
-#pragma unroll
-  for (int v = 0; v < M; ++v)
-#pragma unroll
-    for (int p = 0; p < n; ++p) u0[v][p] = u_in[((int64_t)v * E + e) * n + p];
   double sn[n];
+  double c_l, c_r;
+  const bool from_ghost = ghost != nullptr && (e_raw < 0 || e_raw >= E);
+  if (from_ghost) {
+    const double* gs = ghost + (e_raw < 0 ? 0 : ghost_stride_1d(M, n));
 #pragma unroll
-  for (int p = 0; p < n; ++p) sn[p] = snode[e * n + p];
-  const double c_l = sface[2 * e], c_r = sface[2 * e + 1];
+    for (int v = 0; v < M; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) u0[v][p] = gs[v * n + p];
+#pragma unroll
+    for (int p = 0; p < n; ++p) sn[p] = gs[M * n + p];
+    c_l = gs[M * n + n];
+    c_r = gs[M * n + n + 1];
+  } else {
+#pragma unroll
+    for (int v = 0; v < M; ++v)
+#pragma unroll
+      for (int p = 0; p < n; ++p) u0[v][p] = u_in[((int64_t)v * E + e) * n + p];
+#pragma unroll
+    for (int p = 0; p < n; ++p) sn[p] = snode[e * n + p];
+    c_l = sface[2 * e];
+    c_r = sface[2 * e + 1];
+  }
 
   // ---- limiter: alpha_e, nodal c, first-order fluxes of the inner subfaces --
   static_assert(!LIMIT || (N >= 1 && !RES), "the limiter needs N >= 1 and a step");
@@ -625,7 +642,7 @@ template <int SYS, int N, bool GLL, bool RES, bool IMEX, bool LIMIT = false>
 __global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
   step_1d_tile<SYS, N, GLL, RES, IMEX, LIMIT>(L.tab, L.xs, L.u_in, L.u_out, L.snode, L.sface,
                                               L.E, blockIdx.x, L.st, L.ctl, blockIdx.x == 0,
-                                              L.lim);
+                                              L.lim, L.ghost);
 }
 
 // ragged ensembles: (instance, tile) pairs of a work list, a block taking

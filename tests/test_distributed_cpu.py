@@ -239,3 +239,57 @@ def test_benchmark_ranks_build_the_library_once():
         p.join(120)
         assert p.exitcode == 0
     assert all(out[r] for r in range(world))
+
+
+def _worker_step_1d(rank, world, port, out):
+    """1D ranges: each rank exchanges its two end elements with its ring
+    neighbours (the product's exchange) and steps its range with the
+    neighbours' end elements as ghosts (the oracle's arithmetic on the range
+    extended by one element on either side, whose own results are dropped)."""
+    from oracle.basis import Basis
+    from oracle.crkfr import Scheme1D
+    from oracle.systems import ShallowWater1D
+    from paper_2512_08611_gb300.distributed import halo_exchange, slab_rows
+    _init(rank, world, port)
+    N, E, L = 3, 23, 10.0
+    rng = np.random.default_rng(5)
+    bs = Basis(N)
+    x = (np.arange(E)[:, None] + bs.xi[None, :]) * (L / E)
+    b = 0.2 * np.exp(-((x - 4.0) ** 2))
+    u = np.stack([1.0 - b + 0.02 * np.sin(2 * np.pi * x / L) + 0.01 * rng.standard_normal(x.shape),
+                  0.1 * np.cos(2 * np.pi * x / L)])
+    sch = Scheme1D(ShallowWater1D(9.81), N, L / E)
+    first, count = slab_rows(E, rank, world)
+    mine = slice(first, first + count)
+    c_ext = b[[(first - 1) % E] + list(range(first, first + count)) + [(first + count) % E]]
+    v, want = u[:, mine].copy(), u.copy()
+    ok, err = True, 0.0
+    for _ in range(4):
+        send_left = torch.from_numpy(np.ascontiguousarray(v[:, 0, :]).ravel())
+        send_right = torch.from_numpy(np.ascontiguousarray(v[:, -1, :]).ravel())
+        ghost_left, ghost_right = torch.empty_like(send_right), torch.empty_like(send_left)
+        halo_exchange(send_left, send_right, ghost_left, ghost_right)
+        ext = np.concatenate([ghost_left.numpy().reshape(2, 1, N + 1), v,
+                              ghost_right.numpy().reshape(2, 1, N + 1)], axis=1)
+        v = sch.step(ext, c_ext, 0.01)[:, 1:-1]
+        want = sch.step(want, b, 0.01)
+        ok &= bool(np.array_equal(v, want[:, mine]))
+        err = max(err, float(np.max(np.abs(v - want[:, mine]))))
+    out[rank] = (ok, err)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_1d_step_equals_single_domain(world):
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_step_1d, args=(r, world, port, out))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert out[r][0], out[r]

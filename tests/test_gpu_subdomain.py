@@ -92,3 +92,90 @@ def test_monolithic_step_refused_in_subdomain_mode():
     with pytest.raises(crk.CrkfrError) as e:
         s.step(to_dev(u), 0.01, 1)
     assert e.value.status == -6
+
+
+# ---------------------------------------------------------------------------
+# 1D subdomains: contiguous element ranges; a step is the packing of the two
+# end elements, one exchange with each ring neighbour, and the fused step
+# with the neighbours' end elements as ghosts
+# ---------------------------------------------------------------------------
+def case_1d(N, E, L, system):
+    from paper_2512_08611_gb300.workloads import SWE1DInput
+    bs = Basis(N)
+    x = (np.arange(E)[:, None] + bs.xi[None, :]) * (L / E)
+    if system == "varadv1d":
+        from paper_2512_08611_gb300.workloads import VarAdvInput
+        inp = VarAdvInput(L=L)
+        return inp.v0(x)[None], inp.a(x)
+    inp, _ = accept_seed(lambda s: SWE1DInput(seed=s, L=L), (x,), 3)
+    u, b = inp.state(x)
+    u[1] = 0.1 * u[0] * np.sin(2 * np.pi * x / L)
+    return u, b
+
+
+def mono_1d(crk, N, E, L, u, b, dt, steps, system, source=None):
+    s = crk.Solver(system, N, gravity=G, cfl_number=golden_cfl(N, "gl"), source=source,
+                   source_coef=0.5 if source else 0.0)
+    s.set_mesh([E], [0.0], [L])
+    s.set_coefficients(to_dev(b))
+    du = to_dev(u)
+    s.step(du, dt, steps)
+    return to_host(du)
+
+
+def slab_1d(crk, N, E, L, b, first, count, system, source=None):
+    dx = L / E
+    s = crk.Solver(system, N, gravity=G, cfl_number=golden_cfl(N, "gl"), source=source,
+                   source_coef=0.5 if source else 0.0)
+    s.set_mesh([count], [first * dx], [(first + count) * dx])
+    s.set_subdomain(True)
+    elems = [(first - 1) % E] + list(range(first, first + count)) + [(first + count) % E]
+    s.set_coefficients(to_dev(np.ascontiguousarray(b[elems])))
+    return s
+
+
+@pytest.mark.parametrize("N,system,source", [(1, "swe1d", None), (4, "swe1d", None),
+                                             (3, "swe1d_wb", None), (2, "varadv1d", None),
+                                             (2, "swe1d", "chezy")])
+def test_three_1d_subdomains_equal_single_domain(N, system, source):
+    """Three ranges of a periodic 1D mesh (one shorter than a tile, one
+    spanning several), exchanging their end elements in one process, give
+    the single-domain step bitwise."""
+    crk = load()
+    # dx = 1/4 exactly, so that each range's 1/dx equals the whole mesh's
+    E, L, steps = 400, 100.0, 6
+    u, b = case_1d(N, E, L, system)
+    dt = 0.2 * (L / E) / 4.0 * golden_cfl(N, "gl")
+    want = mono_1d(crk, N, E, L, u, b, dt, steps, system, source)
+    parts = [(0, 37), (37, 300), (337, 63)]
+    solvers = [slab_1d(crk, N, E, L, b, f, c, system, source) for f, c in parts]
+    states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    bufs = [s.halo_buffers() for s in solvers]       # (send_left, send_right, ghost_left, ghost_right)
+    k_ = len(parts)
+    for _ in range(steps):
+        for s, x in zip(solvers, states):
+            s.step_local(x, dt)
+        for k in range(k_):
+            left, right = (k - 1) % k_, (k + 1) % k_
+            bufs[k][2].copy_(bufs[left][1])            # ghost left <- right end of the left range
+            bufs[k][3].copy_(bufs[right][0])           # ghost right <- left end of the right range
+        for s, x in zip(solvers, states):
+            s.step_faces(x)
+    got = np.concatenate([to_host(x) for x in states], axis=1)
+    assert np.array_equal(got, want), rel_l2(got, want)
+
+
+def test_single_1d_subdomain_is_its_own_neighbour():
+    from paper_2512_08611_gb300.distributed import SlabStepper
+    crk = load()
+    N, E, L, steps = 3, 300, 100.0, 5
+    u, b = case_1d(N, E, L, "swe1d")
+    dt = 0.05 * (L / E) * golden_cfl(N, "gl")
+    want = mono_1d(crk, N, E, L, u, b, dt, steps, "swe1d")
+    s = slab_1d(crk, N, E, L, b, 0, E, "swe1d")
+    x = to_dev(u)
+    SlabStepper(s).step(x, dt, steps)
+    assert np.array_equal(to_host(x), want)
+    with pytest.raises(crk.CrkfrError) as e:
+        s.step(x, dt, 1)
+    assert e.value.status == -6
