@@ -275,13 +275,14 @@ def _oracle_worker(job):
     return dof, time.perf_counter() - t0
 
 
-def oracle_on_all_cores(wl, budget_s, steps, warmup):
+def oracle_on_all_cores(wl, budget_s, steps, warmup, procs=None):
     """The oracle, unchanged, stepping one patch per host core in separate
     processes (spawned: no process inherits a CUDA context); throughput =
-    all processes' DoF-updates / the slowest process's time."""
+    all processes' DoF-updates / the slowest process's time.  ``procs``: one
+    process per core by default."""
     import multiprocessing
     cpu_threads()
-    procs = os.cpu_count() or 1
+    procs = procs or os.cpu_count() or 1
     sch, u, b, dof, side = time_oracle(wl, budget_s, steps + warmup)
     cfl = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_cfl.json")))[wl.cfl_key()][f"{wl.N}_gl"]
     job = (wl.name, wl.E[0], side, steps, warmup, cfl)
@@ -528,11 +529,16 @@ def run_ours(args, wl):
         out["adjoint"] = {k: v for k, v in a.items() if k != "dof"}
     if rank == 0 and world == 1 and not args.no_cpu:
         value_cpu, el_cpu, procs, patch, dof = oracle_on_all_cores(wl, 15.0, 2, 0)
+        # and on one core (the oracle is single-threaded numpy)
+        value_1, el_1, _, patch_1, _ = oracle_on_all_cores(wl, 8.0, 2, 0, procs=1)
         out["cpu_baseline"] = {
             "value": value_cpu, "unit": "DoF-updates/s", "cores": procs, "kind": "oracle",
             "sample": f"{procs} processes, one per host core, 2 oracle steps each on its own "
                       f"periodic {patch}-element patch cut from the {wl.label()} workload (same "
-                      f"per-element work), numpy FP64 single-threaded per process"}
+                      f"per-element work), numpy FP64 single-threaded per process",
+            "single_core": {"value": value_1, "unit": "DoF-updates/s", "cores": 1,
+                            "sample": f"one process, 2 oracle steps on a {patch_1}-element "
+                                      f"patch of the same workload"}}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
