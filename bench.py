@@ -179,6 +179,17 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def l2_note(wl):
+    """How the timed steps stand to the 129 MB L2 (no flush between steps):
+    the state, its copy and, in 2D, the face traces and work buffers."""
+    ws = wl.dof * 8 * (7.5 if wl.dim == 2 else 2.0)
+    if ws > 129e6:
+        size = "%.2f GB" % (ws / 1e9) if ws >= 1e9 else "%.0f MB" % (ws / 1e6)
+        return "no flush: state + work buffers (%s) exceed the 129 MB L2" % size
+    return ("no flush: state + work buffers (%.0f MB) stay in the 129 MB L2 between steps, as "
+            "in any run on this mesh; the step is FP64-bound" % (ws / 1e6))
+
+
 # ---------------------------------------------------------------------------
 # profiles/ summary of the dominant kernel: dram traffic, valid only while the
 # kernel source is unchanged
@@ -372,6 +383,8 @@ def run_ours(args, wl):
     s.set_coefficients(torch.tensor(b, dtype=torch.float64, device="cuda"))
     if wl.limiter:
         s.set_limiter(wl.limiter)
+    if wl.dim == 1 and args.tile_1d:
+        s.set_tile_1d(args.tile_1d)
     u_init = u.clone()
     stepper = None
     dt_fixed = 0.0
@@ -491,7 +504,7 @@ def run_ours(args, wl):
         "config": {"workload": wl.label(), "elements": wl.elements,
                    "nodes_per_element": wl.nodes_per_elem, "vars": wl.M, "dof": wl.dof,
                    "cfl_safety": 0.5, "cfl": s.cfl(), "dt_last": dt_last, "t_sim": t_sim,
-                   "l2": "no flush: state + work buffers ~3 GB >> 129 MB L2",
+                   "l2": l2_note(wl),
                    "parallelism": "single GPU" if world == 1 else
                    (f"{world} slabs of a 1024 x {1024 * world} mesh, one NCCL trace exchange per "
                     f"step, fixed dt {dt_fixed:.6g}" if wl.dim == 2 else
@@ -523,6 +536,8 @@ def run_ours(args, wl):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if wl.dim == 1:
+        out["config"]["tile_threads_1d"] = args.tile_1d or "per mesh"
     if rank == 0 and world == 1 and wl.name == "swe2d" and not args.no_adjoint:
         # the metric's third part: the adjoint's cost against the forward run
         a = measure_adjoint(crkfr)
@@ -785,6 +800,8 @@ def main():
                              "ensemble", "adjoint"])
     ap.add_argument("--mesh", type=int, default=None,
                     help="elements per side (2D) or elements (1D); profiling of small cases")
+    ap.add_argument("--tile-1d", type=int, default=0, choices=[0, 64, 96, 128],
+                    help="threads per block of the 1D step (0: chosen per mesh)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-adjoint", action="store_true",

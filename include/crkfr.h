@@ -365,6 +365,17 @@ typedef enum {
   CRKFR_LIMITER_FIXED = 2
 } crkfr_limiter;
 crkfr_status crkfr_set_limiter(crkfr_ctx* ctx, int32_t mode, double alpha);
+
+/* Threads per block of the fused 1D step kernel, which gives each element one
+ * thread and each block threads - 2 elements between two recomputed
+ * neighbours.  0 (the default): chosen per mesh among 64, 96 and 128 so that
+ * the busiest SM gets the fewest threads; 64, 96 or 128: that size for every
+ * step.  Only the schedule changes, not a bit of the results.  Applies to the
+ * unlimited step of 1D contexts (crkfr_step, crkfr_advance, crkfr_step_host,
+ * crkfr_step_local); the limited step and crkfr_residual run 128-thread
+ * blocks.  CRKFR_ERR_UNSUPPORTED on a 2D context, CRKFR_ERR_ARG for other
+ * values; kept across crkfr_set_mesh. */
+crkfr_status crkfr_set_tile_1d(crkfr_ctx* ctx, int32_t threads);
 crkfr_status crkfr_limiter_alpha(crkfr_ctx* ctx, double* alpha_dev, void* stream);
 
 /* Simulated time and the size of the last step taken (synchronises). */

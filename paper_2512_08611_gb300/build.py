@@ -20,7 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libcrkfr.so"
 
-SOURCES = ["api.cu", "kernels_1d.cu", "kernels_2d.cu", "kernels_imex.cu", "kernels_wb.cu",
+SOURCES = ["api.cu", "kernels_1d.cu", "kernels_2d.cu", "kernels_imex.cu", "kernels_imex1d.cu",
+           "kernels_wb.cu", "kernels_wb1d.cu",
            "kernels_limit.cu", "kernels_limit2d.cu", "kernels_limit2d_wb.cu", "noalloc.cu", "batch.cu",
            "kernels_adj2d.cu", "probe.cu", "basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -91,6 +91,7 @@ SIGNATURES = {
     "crkfr_launch_count": (_I64, [_P]),
     "crkfr_profile_enable": (_I32, [_P, _I32]),
     "crkfr_set_limiter": (_I32, [_P, _I32, _D]),
+    "crkfr_set_tile_1d": (_I32, [_P, _I32]),
     "crkfr_batch_set_tuning": (_I32, [_P, _I32, _I32, _I32]),
     "crkfr_batch_get_tuning": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                       ctypes.POINTER(_I32), _PD]),
@@ -496,6 +497,11 @@ class Solver:
         element) or None (off)."""
         self._check(lib().crkfr_set_limiter(self.h, self.LIMITERS[mode], float(alpha)))
         self.limiter = (mode, float(alpha))
+
+    def set_tile_1d(self, threads=0):
+        """Threads per block of the 1D step: 0 chooses per mesh, 64, 96 or 128
+        fixes it (the results do not change)."""
+        self._check(lib().crkfr_set_tile_1d(self.h, int(threads)))
 
     def limiter_alpha(self):
         """alpha_e of the last limited step (cuda float64 tensor: (E,) in 1D,

@@ -50,6 +50,7 @@ struct crkfr_ctx {
   double* d_send = nullptr;       // 1D subdomain: this slab's two end elements' u
   double sub_dt = 0.0;            // 1D subdomain: dt of the step between local and faces
   int limit_mode = CRKFR_LIMITER_NONE;
+  int tile_1d = 0;                // crkfr_set_tile_1d
   double alpha_fixed = 0.0;
   // crkfr_step_host: a copy stream and events to read finished rows of the
   // last step back while the face kernel updates the next rows
@@ -223,6 +224,7 @@ Launch1D make1d(crkfr_ctx* c) {
   L.lim.cnode = c->d_cnode;
   L.lim.alpha_out = c->d_alpha;
   L.ghost = c->subdomain ? c->d_ghost : nullptr;
+  L.tile_threads = c->tile_1d;
   return L;
 }
 
@@ -791,6 +793,16 @@ crkfr_status crkfr_set_limiter(crkfr_ctx* c, int32_t mode, double alpha) {
   }
   c->limit_mode = mode;
   c->alpha_fixed = mode == CRKFR_LIMITER_FIXED ? alpha : 0.0;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_set_tile_1d(crkfr_ctx* c, int32_t threads) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (sys_is_2d(c->cfg.system))
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "the tile size is a setting of the 1D step");
+  if (threads != 0 && threads != 64 && threads != 96 && threads != 128)
+    return fail(c, CRKFR_ERR_ARG, "threads must be 0, 64, 96 or 128");
+  c->tile_1d = threads;
   return CRKFR_OK;
 }
 

@@ -144,6 +144,9 @@ struct Launch1D {
   // wrap; per side ghost_stride_1d(M, n) doubles: u [M][n], the static node
   // terms [n], the face traces of c [2] (null: periodic)
   const double* ghost;
+  // threads per block of the unlimited step: 0 = chosen per mesh, else 64,
+  // 96 or 128
+  int tile_threads;
 };
 #ifdef __CUDACC__
 __host__ __device__

@@ -5,8 +5,9 @@
 // Mapping: one thread owns one element and keeps its N+1 nodes of every
 // variable, all inner stages and all time averages in registers (Sec. 3,
 // Eq. crkfr.non.cons.final, inner stages; Eqs. disc.avg.flux,
-// time.avg.soln, local.time.avg.non.cons).  A block of 128 threads updates
-// 126 consecutive elements; its first and last threads recompute the stages
+// time.avg.soln, local.time.avg.non.cons).  A block of B threads updates
+// B - 2 consecutive elements (B = 128, or 64 or 96 where those tiles spread
+// more evenly over the SMs); its first and last threads recompute the stages
 // of the two neighbouring elements (2 of 128 threads, 1.6% extra FP64) so
 // that the only inter-element coupling, one Riemann problem per face
 // (Eqs. numflux.cons, combined.wave.speed, good.numflux.non.cons,
@@ -161,12 +162,13 @@ __device__ __forceinline__ void lo_source(const Tables& T, double dt, double* u)
   }
 }
 
-// One tile (126 elements plus a halo element on each side) of the fused 1D
-// step of one mesh.  T holds reference-element tables (dx = 1: D, l(0), l(1),
-// 0.5 g'); xs = 1/dx scales the local operator and the corrections through
-// the scalar coefficients only (stage coefficients dt a_ij xs, update
-// coefficient dt b_ref xs), so one table serves meshes of any dx.
-template <int SYS, int N, bool GLL, bool RES, bool IMEX, bool LIMIT = false>
+// One tile (BLOCK - 2 elements plus a halo element on each side) of the fused
+// 1D step of one mesh.  T holds reference-element tables (dx = 1: D, l(0),
+// l(1), 0.5 g'); xs = 1/dx scales the local operator and the corrections
+// through the scalar coefficients only (stage coefficients dt a_ij xs, update
+// coefficient dt b_ref xs), so one table serves meshes of any dx.  Every
+// element's arithmetic is the same for any BLOCK.
+template <int SYS, int N, bool GLL, bool RES, bool IMEX, bool LIMIT = false, int BLOCK = kBlock1D>
 __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
                                              const double* __restrict__ u_in,
                                              double* __restrict__ u_out,
@@ -185,13 +187,13 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   constexpr bool SWE = (SYS == CRKFR_SYS_SWE_1D || SYS == CRKFR_SYS_SWE_1D_WB);
   constexpr bool WB = (SYS == CRKFR_SYS_SWE_1D_WB);
   const int t = threadIdx.x;
-  const int64_t e_raw = tile * (kBlock1D - 2) + t - 1;
+  const int64_t e_raw = tile * (BLOCK - 2) + t - 1;
   int64_t e = e_raw % E;
   if (e < 0) e += E;
-  const bool owner = (t >= 1) && (t <= kBlock1D - 2) && (e_raw < E);
+  const bool owner = (t >= 1) && (t <= BLOCK - 2) && (e_raw < E);
 
-  __shared__ double sm_left[NL][kBlock1D];
-  __shared__ double sm_T[M][kBlock1D];
+  __shared__ double sm_left[NL][BLOCK];
+  __shared__ double sm_T[M][BLOCK];
 
   const double dt = RES ? ctl.dt_fixed : step_dt(ctl, st);
   if (!RES && first_tile && t == 0) step_bookkeeping(ctl, st, dt);
@@ -226,7 +228,7 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
 
   // ---- limiter: alpha_e, nodal c, first-order fluxes of the inner subfaces --
   static_assert(!LIMIT || (N >= 1 && !RES), "the limiter needs N >= 1 and a step");
-  constexpr int LM = LIMIT ? M : 1, LN = LIMIT ? N : 1, LB = LIMIT ? kBlock1D : 1;
+  constexpr int LM = LIMIT ? M : 1, LN = LIMIT ? N : 1, LB = LIMIT ? BLOCK : 1;
   double alpha = 0.0;
   double cn[n];
   double fim[LM][LN];   // right flux of node p (B at node p)
@@ -423,120 +425,124 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   // ---- Riemann problem at the right face (t | t+1), both sides -------------
   double Tm[M];        // doubled face term on this element's right face (minus side)
   double Fm_lim[LM];   // limiter: blended, limited flux F^- of that face
-  if (LIMIT && t < kBlock1D - 1) {
-    // time-averaged numerical and total fluxes in the units of the time
-    // averages (divided by b_ref), Eqs. numflux.cons, good.numflux.non.cons,
-    // total.F.non.cons; the first-order face flux from the nodal values next
-    // to the face; Eq. Fblend; Algorithm 1 (h > 0) for shallow water
-    constexpr double b0 = TB::bref();
-    double FHm[M], FHp[M], FTm[M], FTp[M];
-    if constexpr (SWE) {
-      const double Hm = tr_r[0], Mm = tr_r[1], Fm = tr_r[2], hm = tr_r[3], mm = tr_r[4],
-                   bm = tr_r[5];
-      const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
-                   hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
-      const double g = T.gravity;
-      const double lam =
-          max_nonneg(swe_speed(hm, mm, T.sqrt_gravity), swe_speed(hp, mp, T.sqrt_gravity));
-      const double dUh = WB ? (Hp + bp * T.inv_b0) - (Hm + bm * T.inv_b0) : Hp - Hm;
-      const double Fn0 = fma(-0.5 * lam, dUh, 0.5 * (Mm + Mp));
-      const double Fn1 = fma(-0.5 * lam, Mp - Mm, 0.5 * (Fm + Fp));
-      const double bn = 0.5 * (bm + bp) * T.inv_b0;
-      const double Wn = WB ? 0.5 * (Hm + Hp) + bn : bn;
-      const double Wm = WB ? Hm + bm * T.inv_b0 : bm * T.inv_b0;
-      const double Wp = WB ? Hp + bp * T.inv_b0 : bp * T.inv_b0;
-      FHm[0] = Fn0;
-      FHp[0] = Fn0;
-      FHm[1] = Fn1 + g * hm * Wn;
-      FHp[1] = Fn1 + g * hp * Wn;
-      FTm[0] = Mm;
-      FTp[0] = Mp;
-      FTm[1] = Fm + g * hm * Wm;
-      FTp[1] = Fp + g * hp * Wp;
-    } else {
-      const double Vm = tr_r[0], am = tr_r[1];
-      const double Vp = sm_left[0][t + 1], ap = sm_left[1][t + 1];
-      const double lam = max_nonneg(fabs(am), fabs(ap));
-      const double Fn = -0.5 * lam * (Vp - Vm);
-      const double Vn = 0.5 * (Vm + Vp);
-      FHm[0] = Fn + am * Vn;
-      FHp[0] = Fn + ap * Vn;
-      FTm[0] = am * Vm;
-      FTp[0] = ap * Vp;
-    }
-    double uN[M], u0R[M], fLm[M], fLp[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      uN[v] = u0[v][N];
-      u0R[v] = sm_u0[v][t + 1];
-    }
-    lo_flux<SYS>(uN, u0R, cn[N], sm_c0[t + 1], T, fLm, fLp);
-    const double af = 0.5 * (alpha + sm_al[t + 1]);
-    // (af = 0 and theta = 1 are the common cases: there the blends reduce
-    // to their first terms and are skipped)
-    double Fm_[M], Fp_[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      Fm_[v] = b0 * FHm[v];
-      Fp_[v] = b0 * FHp[v];
-      if (af != 0.0) {
-        Fm_[v] = (1.0 - af) * Fm_[v] + af * fLm[v];
-        Fp_[v] = (1.0 - af) * Fp_[v] + af * fLp[v];
+  if constexpr (LIMIT) {
+    if (t < BLOCK - 1) {
+      // time-averaged numerical and total fluxes in the units of the time
+      // averages (divided by b_ref), Eqs. numflux.cons, good.numflux.non.cons,
+      // total.F.non.cons; the first-order face flux from the nodal values next
+      // to the face; Eq. Fblend; Algorithm 1 (h > 0) for shallow water
+      constexpr double b0 = TB::bref();
+      double FHm[M], FHp[M], FTm[M], FTp[M];
+      if constexpr (SWE) {
+        const double Hm = tr_r[0], Mm = tr_r[1], Fm = tr_r[2], hm = tr_r[3], mm = tr_r[4],
+                     bm = tr_r[5];
+        const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
+                     hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
+        const double g = T.gravity;
+        const double lam =
+            max_nonneg(swe_speed(hm, mm, T.sqrt_gravity), swe_speed(hp, mp, T.sqrt_gravity));
+        const double dUh = WB ? (Hp + bp * T.inv_b0) - (Hm + bm * T.inv_b0) : Hp - Hm;
+        const double Fn0 = fma(-0.5 * lam, dUh, 0.5 * (Mm + Mp));
+        const double Fn1 = fma(-0.5 * lam, Mp - Mm, 0.5 * (Fm + Fp));
+        const double bn = 0.5 * (bm + bp) * T.inv_b0;
+        const double Wn = WB ? 0.5 * (Hm + Hp) + bn : bn;
+        const double Wm = WB ? Hm + bm * T.inv_b0 : bm * T.inv_b0;
+        const double Wp = WB ? Hp + bp * T.inv_b0 : bp * T.inv_b0;
+        FHm[0] = Fn0;
+        FHp[0] = Fn0;
+        FHm[1] = Fn1 + g * hm * Wn;
+        FHp[1] = Fn1 + g * hp * Wn;
+        FTm[0] = Mm;
+        FTp[0] = Mp;
+        FTm[1] = Fm + g * hm * Wm;
+        FTp[1] = Fp + g * hp * Wp;
+      } else {
+        const double Vm = tr_r[0], am = tr_r[1];
+        const double Vp = sm_left[0][t + 1], ap = sm_left[1][t + 1];
+        const double lam = max_nonneg(fabs(am), fabs(ap));
+        const double Fn = -0.5 * lam * (Vp - Vm);
+        const double Vn = 0.5 * (Vm + Vp);
+        FHm[0] = Fn + am * Vn;
+        FHp[0] = Fn + ap * Vn;
+        FTm[0] = am * Vm;
+        FTp[0] = ap * Vp;
       }
-    }
-    if constexpr (SWE) {
-      const double c0 = dtx * T.inv_w[0], cN = dtx * T.inv_w[N];
-      const double fi0R = sm_fi0[0][t + 1], fiNL = fip[0][LN - 1];
-      const double low0 = u0R[0] - c0 * (fi0R - fLp[0]);
-      const double lowN = uN[0] - cN * (fLm[0] - fiNL);
-      const double t0 = u0R[0] - c0 * (fi0R - Fp_[0]);
-      const double tN = uN[0] - cN * (Fm_[0] - fiNL);
-      const double th = fmin(theta_lin(0.1 * low0, low0, t0), theta_lin(0.1 * lowN, lowN, tN));
-      if (th < 1.0) {
-#pragma unroll
-        for (int v = 0; v < M; ++v) {
-          Fm_[v] = th * Fm_[v] + (1.0 - th) * fLm[v];
-          Fp_[v] = th * Fp_[v] + (1.0 - th) * fLp[v];
+      double uN[M], u0R[M], fLm[M], fLp[M];
+  #pragma unroll
+      for (int v = 0; v < M; ++v) {
+        uN[v] = u0[v][N];
+        u0R[v] = sm_u0[v][t + 1];
+      }
+      lo_flux<SYS>(uN, u0R, cn[N], sm_c0[t + 1], T, fLm, fLp);
+      const double af = 0.5 * (alpha + sm_al[t + 1]);
+      // (af = 0 and theta = 1 are the common cases: there the blends reduce
+      // to their first terms and are skipped)
+      double Fm_[M], Fp_[M];
+  #pragma unroll
+      for (int v = 0; v < M; ++v) {
+        Fm_[v] = b0 * FHm[v];
+        Fp_[v] = b0 * FHp[v];
+        if (af != 0.0) {
+          Fm_[v] = (1.0 - af) * Fm_[v] + af * fLm[v];
+          Fp_[v] = (1.0 - af) * Fp_[v] + af * fLp[v];
         }
       }
+      if constexpr (SWE) {
+        const double c0 = dtx * T.inv_w[0], cN = dtx * T.inv_w[N];
+        const double fi0R = sm_fi0[0][t + 1], fiNL = fip[0][LN - 1];
+        const double low0 = u0R[0] - c0 * (fi0R - fLp[0]);
+        const double lowN = uN[0] - cN * (fLm[0] - fiNL);
+        const double t0 = u0R[0] - c0 * (fi0R - Fp_[0]);
+        const double tN = uN[0] - cN * (Fm_[0] - fiNL);
+        const double th = fmin(theta_lin(0.1 * low0, low0, t0), theta_lin(0.1 * lowN, lowN, tN));
+        if (th < 1.0) {
+  #pragma unroll
+          for (int v = 0; v < M; ++v) {
+            Fm_[v] = th * Fm_[v] + (1.0 - th) * fLm[v];
+            Fp_[v] = th * Fp_[v] + (1.0 - th) * fLp[v];
+          }
+        }
+      }
+      // face terms in the doubled units of the corrections: 2 (F - F^tot) / b_ref
+  #pragma unroll
+      for (int v = 0; v < M; ++v) {
+        Fm_lim[v] = Fm_[v];
+        Tm[v] = 2.0 * (Fm_[v] * T.inv_b0 - FTm[v]);
+        sm_T[v][t + 1] = 2.0 * (Fp_[v] * T.inv_b0 - FTp[v]);
+        sm_F[v][t + 1] = Fp_[v];
+      }
     }
-    // face terms in the doubled units of the corrections: 2 (F - F^tot) / b_ref
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      Fm_lim[v] = Fm_[v];
-      Tm[v] = 2.0 * (Fm_[v] * T.inv_b0 - FTm[v]);
-      sm_T[v][t + 1] = 2.0 * (Fp_[v] * T.inv_b0 - FTp[v]);
-      sm_F[v][t + 1] = Fp_[v];
-    }
-  } else if (!LIMIT && t < kBlock1D - 1) {
-    if constexpr (SWE) {
-      const double Hm = tr_r[0], Mm = tr_r[1], Fm = tr_r[2], hm = tr_r[3], mm = tr_r[4],
-                   bm = tr_r[5];
-      const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
-                   hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
-      const double lam =
-          max_nonneg(swe_speed(hm, mm, T.sqrt_gravity), swe_speed(hp, mp, T.sqrt_gravity));
-      // F_h = U_m (the h flux is the momentum)
-      const double dFh = Mp - Mm;
-      const double dFm = Fp - Fm, dUm = Mp - Mm;
-      // jump of the dissipated and fluctuating state: h, or eta = h + b for
-      // the well-balanced form (b is static, so in the units of the time
-      // averages, divided by b_ref, its jump carries 1 / b_ref)
-      const double dUh = WB ? fma(T.inv_b0, bp - bm, Hp - Hm) : Hp - Hm;
-      const double gdb = WB ? T.gravity * dUh : T.face_g * (bp - bm);
-      Tm[0] = fma(-lam, dUh, dFh);
-      Tm[1] = fma(hm, gdb, fma(-lam, dUm, dFm));
-      const double Tp0 = -fma(lam, dUh, dFh);
-      const double Tp1 = -fma(hp, gdb, fma(lam, dUm, dFm));
-      sm_T[0][t + 1] = Tp0;
-      sm_T[1][t + 1] = Tp1;
-    } else {
-      const double Vm = tr_r[0], am = tr_r[1];
-      const double Vp = sm_left[0][t + 1], ap = sm_left[1][t + 1];
-      const double lam = max_nonneg(fabs(am), fabs(ap));
-      const double dU = Vp - Vm;
-      Tm[0] = (am - lam) * dU;
-      sm_T[0][t + 1] = -(lam + ap) * dU;
+  } else {
+    if (t < BLOCK - 1) {
+      if constexpr (SWE) {
+        const double Hm = tr_r[0], Mm = tr_r[1], Fm = tr_r[2], hm = tr_r[3], mm = tr_r[4],
+                     bm = tr_r[5];
+        const double Hp = sm_left[0][t + 1], Mp = sm_left[1][t + 1], Fp = sm_left[2][t + 1],
+                     hp = sm_left[3][t + 1], mp = sm_left[4][t + 1], bp = sm_left[5][t + 1];
+        const double lam =
+            max_nonneg(swe_speed(hm, mm, T.sqrt_gravity), swe_speed(hp, mp, T.sqrt_gravity));
+        // F_h = U_m (the h flux is the momentum)
+        const double dFh = Mp - Mm;
+        const double dFm = Fp - Fm, dUm = Mp - Mm;
+        // jump of the dissipated and fluctuating state: h, or eta = h + b for
+        // the well-balanced form (b is static, so in the units of the time
+        // averages, divided by b_ref, its jump carries 1 / b_ref)
+        const double dUh = WB ? fma(T.inv_b0, bp - bm, Hp - Hm) : Hp - Hm;
+        const double gdb = WB ? T.gravity * dUh : T.face_g * (bp - bm);
+        Tm[0] = fma(-lam, dUh, dFh);
+        Tm[1] = fma(hm, gdb, fma(-lam, dUm, dFm));
+        const double Tp0 = -fma(lam, dUh, dFh);
+        const double Tp1 = -fma(hp, gdb, fma(lam, dUm, dFm));
+        sm_T[0][t + 1] = Tp0;
+        sm_T[1][t + 1] = Tp1;
+      } else {
+        const double Vm = tr_r[0], am = tr_r[1];
+        const double Vp = sm_left[0][t + 1], ap = sm_left[1][t + 1];
+        const double lam = max_nonneg(fabs(am), fabs(ap));
+        const double dU = Vp - Vm;
+        Tm[0] = (am - lam) * dU;
+        sm_T[0][t + 1] = -(lam + ap) * dU;
+      }
     }
   }
   __syncthreads();
@@ -634,15 +640,15 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   }
   if (!RES) {
     if (bad) atomicOr(&st->status, 1u);
-    if (ctl.want_rate) block_max_atomic<kBlock1D>(rate, &st->rate[ctl.slot_write]);
+    if (ctl.want_rate) block_max_atomic<BLOCK>(rate, &st->rate[ctl.slot_write]);
   }
 }
 
-template <int SYS, int N, bool GLL, bool RES, bool IMEX, bool LIMIT = false>
-__global__ void __launch_bounds__(kBlock1D) k_step_1d(const Launch1D L) {
-  step_1d_tile<SYS, N, GLL, RES, IMEX, LIMIT>(L.tab, L.xs, L.u_in, L.u_out, L.snode, L.sface,
-                                              L.E, blockIdx.x, L.st, L.ctl, blockIdx.x == 0,
-                                              L.lim, L.ghost);
+template <int SYS, int N, bool GLL, bool RES, bool IMEX, bool LIMIT = false, int BLOCK = kBlock1D>
+__global__ void __launch_bounds__(BLOCK) k_step_1d(const Launch1D L) {
+  step_1d_tile<SYS, N, GLL, RES, IMEX, LIMIT, BLOCK>(L.tab, L.xs, L.u_in, L.u_out, L.snode,
+                                                     L.sface, L.E, blockIdx.x, L.st, L.ctl,
+                                                     blockIdx.x == 0, L.lim, L.ghost);
 }
 
 // ragged ensembles: (instance, tile) pairs of a work list, a block taking
@@ -660,14 +666,73 @@ __global__ void __launch_bounds__(kBlock1D) k_step_1d_batch(const LaunchBatch1D 
   }
 }
 
+// Threads per block of the step, chosen per mesh among kTileBlocks.  A block
+// updates BLOCK - 2 elements, one per thread, and every thread does the same
+// work, so the step's time follows the busiest SM's thread count,
+// BLOCK x ceil(tiles / SMs).  At 1e5 elements 128-thread tiles (794) put 6
+// blocks = 768 threads on some SMs, 96-thread tiles (1064) 7 blocks = 672
+// threads on every SM: 8% faster.  Among block sizes within 2% of the least
+// such count the one with the most resident threads per SM, then the larger,
+// is taken (on large meshes 128: fewer halo elements, as many warps).
+// crkfr_set_tile_1d can fix the size instead.
+constexpr int kTileBlocks[3] = {64, 96, 128};
+
+inline int pick_tile_block(int64_t E, int sms, const int* resident) {
+  int64_t cost[3];
+  int64_t best = -1;
+  for (int i = 0; i < 3; ++i) {
+    const int64_t B = kTileBlocks[i];
+    const int64_t tiles = (E + B - 3) / (B - 2);
+    cost[i] = B * ((tiles + sms - 1) / sms);
+    if (best < 0 || cost[i] < best) best = cost[i];
+  }
+  int pick = 2;
+  for (int i = 0; i < 3; ++i) {
+    if (50 * cost[i] > 51 * best) continue;
+    const int64_t ri = (int64_t)resident[i] * kTileBlocks[i];
+    const int64_t rp = (int64_t)resident[pick] * kTileBlocks[pick];
+    if (50 * cost[pick] > 51 * best || ri > rp || (ri == rp && i > pick)) pick = i;
+  }
+  return kTileBlocks[pick];
+}
+
+template <int SYS, int N, bool GLL, bool IMEX, int BLOCK>
+int launch_step_block(const Launch1D& L, cudaStream_t s) {
+  const int64_t blocks = (L.E + BLOCK - 3) / (BLOCK - 2);
+  if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
+  k_step_1d<SYS, N, GLL, false, IMEX, false, BLOCK><<<(unsigned)blocks, BLOCK, 0, s>>>(L);
+  return (int)cudaGetLastError();
+}
+
 template <int SYS, int N, bool GLL, bool IMEX>
 int launch_step_t(const Launch1D& L, cudaStream_t s) {
-  const int64_t blocks = (L.E + kBlock1D - 3) / (kBlock1D - 2);
-  if (L.ctl.residual)
+  if (L.ctl.residual) {
+    const int64_t blocks = (L.E + kBlock1D - 3) / (kBlock1D - 2);
+    if (blocks > 0x7fffffff) return (int)cudaErrorInvalidConfiguration;
     k_step_1d<SYS, N, GLL, true, IMEX><<<(unsigned)blocks, kBlock1D, 0, s>>>(L);
-  else
-    k_step_1d<SYS, N, GLL, false, IMEX><<<(unsigned)blocks, kBlock1D, 0, s>>>(L);
-  return (int)cudaGetLastError();
+    return (int)cudaGetLastError();
+  }
+  // resident blocks per SM of each block size (the occupancy API, once)
+  static int sms = -1;
+  static int resident[3];
+  if (sms < 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &resident[0], k_step_1d<SYS, N, GLL, false, IMEX, false, 64>, 64, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &resident[1], k_step_1d<SYS, N, GLL, false, IMEX, false, 96>, 96, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &resident[2], k_step_1d<SYS, N, GLL, false, IMEX, false, 128>, 128, 0) != cudaSuccess)
+      return (int)cudaGetLastError();
+    sms = n > 0 ? n : 1;
+  }
+  switch (L.tile_threads > 0 ? L.tile_threads : pick_tile_block(L.E, sms, resident)) {
+    case 64: return launch_step_block<SYS, N, GLL, IMEX, 64>(L, s);
+    case 96: return launch_step_block<SYS, N, GLL, IMEX, 96>(L, s);
+  }
+  return launch_step_block<SYS, N, GLL, IMEX, 128>(L, s);
 }
 
 template <int SYS, bool IMEX>

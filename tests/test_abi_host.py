@@ -88,6 +88,22 @@ def test_scheme_switches_accept_only_the_built_readings(crk):
     assert "nc_face_mode" in crk.lib().crkfr_last_error(None).decode()
 
 
+def test_tile_size_setting(crk):
+    """crkfr_set_tile_1d takes 0 (per mesh), 64, 96 or 128 threads on a 1D
+    context; other values are argument errors, a 2D context refuses it."""
+    from paper_2512_08611_gb300.crkfr import CrkfrError, Solver
+    s = Solver("swe1d", 4)
+    for t in (0, 64, 96, 128):
+        s.set_tile_1d(t)
+    for t in (32, 100, 256, -1):
+        with pytest.raises(CrkfrError) as e:
+            s.set_tile_1d(t)
+        assert e.value.status == -1 and "threads" in str(e.value)
+    with pytest.raises(CrkfrError) as e:
+        Solver("swe2d", 3).set_tile_1d(96)
+    assert e.value.status == -2
+
+
 def test_only_periodic_meshes_are_built(crk):
     from paper_2512_08611_gb300.crkfr import CrkfrError, Solver
     s = Solver("swe2d", 2)

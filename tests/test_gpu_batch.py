@@ -103,6 +103,40 @@ def test_launch_shapes_give_the_same_bits(tpb, order, parallel, graph):
         assert times[i] == t
 
 
+@pytest.mark.parametrize("N,family", [(4, "gl"), (3, "gll")])
+@pytest.mark.parametrize("system", ["swe1d", "swe1d_wb"])
+def test_single_mesh_tile_sizes_give_the_same_bits(system, N, family):
+    """The single-mesh step picks its block size per mesh (on 152 SMs: 64
+    threads for 3001 elements, 128 for 19152 = 152 x 126, 96 for 1e5) unless
+    crkfr_set_tile_1d fixes it; the ensemble always runs 128-thread tiles.
+    Each element's arithmetic is the same in every tile size, so the mesh
+    stepped alone with any tile size equals a one-instance batch, bit for
+    bit, in CFL and fixed steps."""
+    crk = load()
+    for E in (3001, 19152, 100000):
+        x, dx = positions_1d(Basis(N, family), E, 0.0, 100.0)
+        inp, _ = accept_seed(lambda s: SWE1DInput(seed=s, L=100.0), (x,), 7)
+        u, b = inp.state(x)
+        for dt in (0.0, 0.1 * dx):
+            batch = crk.Batch(system, [(N, E, 0.0, 100.0)], nodes=family, gravity=G,
+                              cfl_safety=0.5)
+            got, c = packed(batch, [u], [b])
+            batch.set_coefficients(c)
+            batch.step(got, dt, 5)
+            batch.status()
+            ref = to_host(batch.state_view(got, 0))
+            for tile in (0, 64, 96, 128):
+                s = crk.Solver(system, N, nodes=family, gravity=G, cfl_safety=0.5)
+                s.set_tile_1d(tile)
+                s.set_mesh([E], [0.0], [100.0])
+                s.set_coefficients(to_dev(b))
+                want = to_dev(u)
+                s.step(want, dt, 5)
+                s.status()
+                assert np.array_equal(to_host(want), ref), (E, dt, tile)
+                assert batch.times()[0] == s.time()[0]
+
+
 def test_autotune_leaves_state_and_times_and_keeps_the_bits():
     crk = load()
     us, cs = inputs(MEMBERS)
