@@ -8,8 +8,12 @@ exchange: after the local phase each rank sends the face traces of its bottom
 element row (their bottom side) to the rank below, which stores them as its
 top halo, and those of its top row (their top side) to the rank above, which
 stores them as its bottom halo.  The face phase then runs on every rank with
-no further communication.  This module holds only that exchange; the
-arithmetic stays in the library.
+no further communication.  A 1D mesh splits the same way into contiguous
+element ranges, whose exchange carries the two end elements.  A CFL step
+needs the largest wave-speed rate of the whole mesh: each rank computes its
+slab's own step and the ranks take the minimum (one all-reduce per step).
+This module holds only that exchange and that reduction; the arithmetic
+stays in the library.
 """
 import torch
 import torch.distributed as dist
@@ -68,21 +72,31 @@ def halo_exchange(send_bottom, send_top, recv_bottom, recv_top, group=None):
 
 
 class SlabStepper:
-    """Steps one rank's slab of a 2D mesh: local phase, halo exchange, face
-    phase.  ``solver`` is a crkfr.Solver in subdomain mode.  With a single
-    process (no process group) the slab is its own periodic neighbour."""
+    """Steps one rank's slab of a 2D mesh (or range of a 1D mesh): local
+    phase, halo exchange, face phase.  ``solver`` is a crkfr.Solver in
+    subdomain mode.  With a single process (no process group) the slab is its
+    own periodic neighbour."""
 
     def __init__(self, solver, group=None):
         self.s = solver
         self.group = group
         self.send_bottom, self.send_top, self.recv_bottom, self.recv_top = solver.halo_buffers()
+        self.last_dt = None
 
-    def step(self, u, dt, nsteps=1):
+    def step(self, u, dt=0.0, nsteps=1):
+        """nsteps steps of u in place.  dt > 0: that step; dt <= 0: the CFL
+        step of the whole mesh (Sec. 5, Eq. time.step.2d), the minimum over
+        ranks of each slab's own step (crkfr_compute_dt), one all-reduce and
+        one host synchronisation per step.  The minimum of C / rate_r over
+        slabs is C / max_r rate_r to the last bit (IEEE division is monotone),
+        so the ranks take the single-domain step exactly."""
         for _ in range(nsteps):
-            self.s.step_local(u, dt)
+            h = dt if dt > 0.0 else min_over_ranks(self.s.compute_dt(u), self.group)
+            self.s.step_local(u, h)
             halo_exchange(self.send_bottom, self.send_top, self.recv_bottom, self.recv_top,
                           self.group)
             self.s.step_faces(u)
+            self.last_dt = h
         return u
 
 
@@ -93,6 +107,17 @@ def slab_rows(global_rows, rank, world):
     count = base + (1 if rank < extra else 0)
     first = rank * base + min(rank, extra)
     return first, count
+
+
+def min_over_ranks(x, group=None):
+    """Min of a float over the ranks of ``group`` (the time step of the whole
+    mesh from the slabs' own steps)."""
+    if not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend(group) == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+    return float(t.item())
 
 
 def max_over_ranks(x):

@@ -151,6 +151,48 @@ def _worker_step(rank, world, port, out):
     dist.destroy_process_group()
 
 
+def _worker_step_cfl(rank, world, port, out):
+    """CFL steps: each rank's own step from its slab (the oracle's
+    compute_dt), the minimum over ranks (the product's reduction), then the
+    split step; the single-domain run takes the step of the whole mesh."""
+    from oracle.crkfr import Scheme2D
+    from oracle.systems import ShallowWater2D
+    from paper_2512_08611_gb300.distributed import min_over_ranks, slab_rows
+    _init(rank, world, port)
+    N, Ey, Ex = 2, 7, 5
+    u, b, dx, dy = _case(Ey, Ex, N)
+    sch = Scheme2D(ShallowWater2D(9.81), N, dx, dy)
+    first, count = slab_rows(Ey, rank, world)
+    rows = slice(first, first + count)
+    v, want = u[:, rows].copy(), u.copy()
+    ok = True
+    for _ in range(3):
+        dt = min_over_ranks(sch.compute_dt(v, b[rows], 0.2, 0.5))
+        dt_all = sch.compute_dt(want, b, 0.2, 0.5)
+        ok &= dt == dt_all
+        v = _split_step(sch, v, b[rows], dt)
+        want = sch.step(want, b, dt_all)
+        ok &= bool(np.array_equal(v, want[:, rows]))
+    out[rank] = (ok, float(np.max(np.abs(v - want[:, rows]))))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_cfl_step_takes_the_single_domain_step(world):
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_step_cfl, args=(r, world, port, out))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert out[r][0], out[r]
+
+
 @pytest.mark.parametrize("world", [2, 3])
 def test_split_step_equals_single_domain(world):
     ctx = mp.get_context("spawn")

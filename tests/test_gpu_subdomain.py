@@ -73,6 +73,46 @@ def test_two_slabs_equal_single_domain(N, system, source):
     assert np.array_equal(got, want), rel_l2(got, want)
 
 
+def exchange_2d(bufs):
+    for k in range(len(bufs)):
+        below, above = (k - 1) % len(bufs), (k + 1) % len(bufs)
+        bufs[k][2].copy_(bufs[below][1])
+        bufs[k][3].copy_(bufs[above][0])
+
+
+@pytest.mark.parametrize("N,system", [(3, "swe2d"), (2, "swe2d_wb")])
+def test_two_slabs_cfl_steps_take_the_whole_mesh_step(N, system):
+    """CFL steps of a split mesh: the step is the minimum of the slabs' own
+    steps (crkfr_compute_dt), which equals the whole mesh's crkfr_compute_dt
+    bit for bit; the slabs then equal the single domain stepped with those
+    steps bitwise, and its own CFL run (whose later steps come from the face
+    kernel's rates) to round-off."""
+    crk = load()
+    Ex, Ey, L, steps = 16, 16, 64.0, 5
+    u, b = case(N, Ex, Ey, L)
+    m = crk.Solver(system, N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+    m.set_mesh([Ex, Ey], [0.0, 0.0], [L, L])
+    m.set_coefficients(to_dev(b))
+    want = to_dev(u)
+    parts = [(0, 5), (5, 11)]
+    solvers = [slab(crk, N, Ex, Ey, L, b, f, c, system) for f, c in parts]
+    states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    bufs = [s.halo_buffers() for s in solvers]
+    for _ in range(steps):
+        dt = min(s.compute_dt(x) for s, x in zip(solvers, states))
+        assert dt == m.compute_dt(want)
+        m.step(want, dt, 1)
+        for s, x in zip(solvers, states):
+            s.step_local(x, dt)
+        exchange_2d(bufs)
+        for s, x in zip(solvers, states):
+            s.step_faces(x)
+    got = np.concatenate([to_host(x) for x in states], axis=1)
+    assert np.array_equal(got, to_host(want)), rel_l2(got, to_host(want))
+    cfl = mono(crk, N, Ex, Ey, L, u, b, 0.0, steps, system)
+    assert rel_l2(got, cfl) < 1e-12
+
+
 def test_single_slab_is_its_own_neighbour():
     from paper_2512_08611_gb300.distributed import SlabStepper
     crk = load()
@@ -83,6 +123,18 @@ def test_single_slab_is_its_own_neighbour():
     x = to_dev(u)
     SlabStepper(s).step(x, dt, steps)
     assert np.array_equal(to_host(x), want)
+    # CFL steps through the stepper: one rank, so its own step is the mesh's
+    m = crk.Solver("swe2d", N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+    m.set_mesh([Ex, Ey], [0.0, 0.0], [L, L])
+    m.set_coefficients(to_dev(b))
+    y, z = to_dev(u), to_dev(u)
+    st = SlabStepper(s)
+    for _ in range(3):
+        dt = m.compute_dt(z)
+        m.step(z, dt, 1)
+        st.step(y, 0.0, 1)
+        assert st.last_dt == dt
+    assert np.array_equal(to_host(y), to_host(z))
 
 
 def test_monolithic_step_refused_in_subdomain_mode():
@@ -163,6 +215,35 @@ def test_three_1d_subdomains_equal_single_domain(N, system, source):
             s.step_faces(x)
     got = np.concatenate([to_host(x) for x in states], axis=1)
     assert np.array_equal(got, want), rel_l2(got, want)
+
+
+@pytest.mark.parametrize("N,system", [(4, "swe1d"), (2, "varadv1d")])
+def test_three_1d_subdomains_cfl_steps_take_the_whole_mesh_step(N, system):
+    crk = load()
+    E, L, steps = 400, 100.0, 6
+    u, b = case_1d(N, E, L, system)
+    m = crk.Solver(system, N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+    m.set_mesh([E], [0.0], [L])
+    m.set_coefficients(to_dev(b))
+    want = to_dev(u)
+    parts = [(0, 37), (37, 300), (337, 63)]
+    solvers = [slab_1d(crk, N, E, L, b, f, c, system) for f, c in parts]
+    states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    bufs = [s.halo_buffers() for s in solvers]
+    k_ = len(parts)
+    for _ in range(steps):
+        dt = min(s.compute_dt(x) for s, x in zip(solvers, states))
+        assert dt == m.compute_dt(want)
+        m.step(want, dt, 1)
+        for s, x in zip(solvers, states):
+            s.step_local(x, dt)
+        for k in range(k_):
+            bufs[k][2].copy_(bufs[(k - 1) % k_][1])
+            bufs[k][3].copy_(bufs[(k + 1) % k_][0])
+        for s, x in zip(solvers, states):
+            s.step_faces(x)
+    got = np.concatenate([to_host(x) for x in states], axis=1)
+    assert np.array_equal(got, to_host(want)), rel_l2(got, to_host(want))
 
 
 def test_single_1d_subdomain_is_its_own_neighbour():
