@@ -351,9 +351,11 @@ def run_ours(args, wl):
     build_once(world, dist)
     from paper_2512_08611_gb300 import crkfr
 
-    split = world > 1
+    # the slab (1D: range) path of the multi-GPU runs; --split runs it on one
+    # GPU, where the slab is its own periodic neighbour
+    split = world > 1 or args.split
     if split and wl.limiter:
-        raise SystemExit("multi-GPU runs use the unlimited workloads")
+        raise SystemExit("split runs use the unlimited workloads")
     s = crkfr.Solver(wl.system, wl.N, gravity=G, cfl_safety=0.5, source=wl.source,
                      source_coef=wl.source_coef)
     if split and wl.dim == 2:
@@ -390,10 +392,9 @@ def run_ours(args, wl):
     dt_fixed = 0.0
     if split:
         from paper_2512_08611_gb300.distributed import SlabStepper
+        from paper_2512_08611_gb300.distributed import min_over_ranks
         stepper = SlabStepper(s)
-        dt_local = torch.tensor([s.compute_dt(u)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(dt_local, op=dist.ReduceOp.MIN)
-        dt_fixed = float(dt_local.item())
+        dt_fixed = min_over_ranks(s.compute_dt(u))
 
     def advance(k):
         if stepper is None:
@@ -444,7 +445,8 @@ def run_ours(args, wl):
         host = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
         host.copy_(u_init.cpu())
         e2e_steps = max(3, min(args.steps, 20))
-        dist.barrier()
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
@@ -454,7 +456,8 @@ def run_ours(args, wl):
             torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = {"value": wl.dof * e2e_steps * world / float(t.item()), "unit": "DoF-updates/s",
                "h2d_bytes_per_step": state_bytes * world, "d2h_bytes_per_step": state_bytes * world,
                "note": "torch pinned copies around the split step (no host entry point for slabs)"}
@@ -505,8 +508,10 @@ def run_ours(args, wl):
                    "nodes_per_element": wl.nodes_per_elem, "vars": wl.M, "dof": wl.dof,
                    "cfl_safety": 0.5, "cfl": s.cfl(), "dt_last": dt_last, "t_sim": t_sim,
                    "l2": l2_note(wl),
-                   "parallelism": "single GPU" if world == 1 else
-                   (f"{world} slabs of a 1024 x {1024 * world} mesh, one NCCL trace exchange per "
+                   "parallelism": "single GPU" if not split else
+                   (f"one slab, its own periodic neighbour (the multi-GPU path on one GPU), "
+                    f"fixed dt {dt_fixed:.6g}" if world == 1 else
+                    f"{world} slabs of a 1024 x {1024 * world} mesh, one NCCL trace exchange per "
                     f"step, fixed dt {dt_fixed:.6g}" if wl.dim == 2 else
                     f"{world} ranges of a {wl.E[0] * world}-element periodic mesh, one NCCL "
                     f"exchange of the end elements per step, fixed dt {dt_fixed:.6g}")},
@@ -800,6 +805,8 @@ def main():
                              "ensemble", "adjoint"])
     ap.add_argument("--mesh", type=int, default=None,
                     help="elements per side (2D) or elements (1D); profiling of small cases")
+    ap.add_argument("--split", action="store_true",
+                    help="run the multi-GPU (slab / range) path on one GPU")
     ap.add_argument("--tile-1d", type=int, default=0, choices=[0, 64, 96, 128],
                     help="threads per block of the 1D step (0: chosen per mesh)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
