@@ -269,12 +269,37 @@ crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_
  * context-owned buffer allocated by crkfr_set_subdomain; crkfr_step_local
  * (dt > 0) writes the send blocks; crkfr_step_faces runs the step of the
  * range with those neighbour states and writes u_dev (through the
- * context's work buffer).  The limiter is refused in this mode. */
+ * context's work buffer).  The limiter is refused on ranges
+ * (CRKFR_ERR_UNSUPPORTED).
+ *
+ * The subcell blending limiter on 2D slabs (crkfr_set_limiter on a slab of
+ * at least two element rows, else CRKFR_ERR_UNSUPPORTED) adds two exchanges
+ * to a step.  Its coefficient alpha_e (Sec. 4) takes the largest neighbour's
+ * raw indicator into account, and the face between two slabs blends with
+ * both elements' alpha, so a limited slab step is: crkfr_step_indicator (the
+ * raw indicator of the slab's own rows; nothing in CRKFR_LIMITER_FIXED
+ * mode); exchange of the indicator rows (crkfr_limiter_halo_buffers kind 0:
+ * send_bottom its rows 0 and 1, send_top its rows Ey_local - 2 and
+ * Ey_local - 1, recv_bottom the two rows below the slab, recv_top the two
+ * above, count = 2 Ex doubles, pointers into the context's indicator
+ * buffers); crkfr_step_local (smoothing of alpha over the slab and the rows
+ * next to it, then the local kernel); exchange of the face traces
+ * (crkfr_halo_buffers) and of the limiter's face data (kind 1: the nodal
+ * states, coefficients and first-order inner fluxes next to the slab's
+ * boundary faces, laid out as the trace blocks, count = 8 Ex (N+1)
+ * doubles); crkfr_step_faces.  The pointers stay valid until the next
+ * crkfr_set_mesh.  A limited slab step equals the single-domain limited
+ * step bit for bit.  crkfr_step_indicator and crkfr_limiter_halo_buffers
+ * return CRKFR_ERR_STATE on a context that is not a limited 2D slab. */
 crkfr_status crkfr_set_subdomain(crkfr_ctx* ctx, int32_t enable);
 crkfr_status crkfr_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** send_top,
                                 double** recv_bottom, double** recv_top, int64_t* count);
 crkfr_status crkfr_step_local(crkfr_ctx* ctx, const double* u_dev, double dt, void* stream);
 crkfr_status crkfr_step_faces(crkfr_ctx* ctx, double* u_dev, void* stream);
+crkfr_status crkfr_step_indicator(crkfr_ctx* ctx, const double* u_dev, void* stream);
+crkfr_status crkfr_limiter_halo_buffers(crkfr_ctx* ctx, int32_t kind, double** send_bottom,
+                                        double** send_top, double** recv_bottom,
+                                        double** recv_top, int64_t* count);
 
 /* Adjoint of the step of Sec. 3, Eq. crkfr.non.cons.final (the paper has
  * no adjoint; it is this library's differentiation path).
@@ -349,12 +374,14 @@ crkfr_status crkfr_step_adjoint_recorded(crkfr_ctx* ctx, const double* u_dev,
  * Hennemann et al. (2021), on v (advection) or h (shallow water; in 2D on
  * the tensor-product modes), raised to half the largest neighbour value;
  * CRKFR_LIMITER_FIXED: alpha_e = alpha for every element (for checks);
- * CRKFR_LIMITER_NONE switches it off.  Contexts with N >= 1 only, 2D meshes
- * whole and periodic (not in subdomain mode) (else CRKFR_ERR_UNSUPPORTED);
- * call after crkfr_set_mesh, which switches the limiter off.  Applies to
- * crkfr_step, crkfr_advance and crkfr_step_host; crkfr_residual stays that
- * of the unlimited step; crkfr_step_local, crkfr_step_faces and
- * crkfr_step_adjoint refuse limited contexts.  A 2D context allocates the
+ * CRKFR_LIMITER_NONE switches it off.  Contexts with N >= 1 only; 1D meshes
+ * whole and periodic; 2D meshes whole and periodic or slabs of at least two
+ * element rows (crkfr_set_subdomain, whose limited step is described there)
+ * (else CRKFR_ERR_UNSUPPORTED); call after crkfr_set_mesh, which switches the
+ * limiter off.  Applies to crkfr_step, crkfr_advance and crkfr_step_host, and
+ * to the phased step of a 2D slab; crkfr_residual stays that of the
+ * unlimited step; crkfr_step_local and crkfr_step_faces refuse limited whole
+ * meshes, crkfr_step_adjoint every limited context.  A 2D context allocates the
  * limiter's buffers (one more state and 32 (Ey + 1) Ex (N+1) doubles of face
  * data) on the first call that switches it on.  crkfr_limiter_alpha copies
  * the alpha_e of the last limited step into alpha_dev (n_elem doubles,

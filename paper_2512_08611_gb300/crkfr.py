@@ -80,6 +80,9 @@ SIGNATURES = {
     "crkfr_halo_buffers": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                   ctypes.POINTER(_P), _PI64]),
     "crkfr_step_local": (_I32, [_P, _P, _D, _P]),
+    "crkfr_step_indicator": (_I32, [_P, _P, _P]),
+    "crkfr_limiter_halo_buffers": (_I32, [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                          ctypes.POINTER(_P), ctypes.POINTER(_P), _PI64]),
     "crkfr_step_faces": (_I32, [_P, _P, _P]),
     "crkfr_step_adjoint": (_I32, [_P, _P, _P, _P, _P, _D, _P]),
     "crkfr_record_size": (_I32, [_P, _PI64]),
@@ -312,6 +315,23 @@ class Solver:
                                              ctypes.byref(cnt)))
         return tuple(torch.as_tensor(_DeviceBlock(p.value, cnt.value), device="cuda")
                      for p in ptrs)
+
+    def limiter_halo_buffers(self, kind):
+        """Limited 2D slab: (send_bottom, send_top, recv_bottom, recv_top) of
+        the raw indicator rows (kind 0) or of the limiter's y-face data
+        (kind 1), float64 CUDA tensors viewing the context's buffers."""
+        import torch
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        cnt = ctypes.c_int64()
+        self._check(lib().crkfr_limiter_halo_buffers(self.h, int(kind),
+                                                     *[ctypes.byref(p) for p in ptrs],
+                                                     ctypes.byref(cnt)))
+        return tuple(torch.as_tensor(_DeviceBlock(p.value, cnt.value), device="cuda")
+                     for p in ptrs)
+
+    def step_indicator(self, u):
+        """Limited 2D slab: the raw indicator of the slab's own rows."""
+        self._check(lib().crkfr_step_indicator(self.h, self._dev(u, self.shape), _stream()))
 
     def step_local(self, u, dt):
         self._check(lib().crkfr_step_local(self.h, self._dev(u, self.shape), float(dt), _stream()))

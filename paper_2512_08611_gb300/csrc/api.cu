@@ -48,6 +48,9 @@ struct crkfr_ctx {
   double* d_ly = nullptr;
   double* d_ghost = nullptr;      // 1D subdomain: the two neighbour elements (Launch1D::ghost)
   double* d_send = nullptr;       // 1D subdomain: this slab's two end elements' u
+  double* d_araw_halo = nullptr;  // 2D slab with the limiter: the neighbours' raw indicator,
+                                  // rows -2, -1 (below) and Ey, Ey + 1 (above), [4][Ex]
+  double* d_alpha_halo = nullptr; // 2D slab with the limiter: smoothed rows -1, Ey, [2][Ex]
   double sub_dt = 0.0;            // 1D subdomain: dt of the step between local and faces
   int limit_mode = CRKFR_LIMITER_NONE;
   int tile_1d = 0;                // crkfr_set_tile_1d
@@ -114,7 +117,9 @@ void free_buffers(crkfr_ctx* c) {
   cudaFree(c->d_ly);
   cudaFree(c->d_ghost);
   cudaFree(c->d_send);
-  c->d_ghost = c->d_send = nullptr;
+  cudaFree(c->d_araw_halo);
+  cudaFree(c->d_alpha_halo);
+  c->d_ghost = c->d_send = c->d_araw_halo = c->d_alpha_halo = nullptr;
   c->d_cnode = c->d_alpha_raw = c->d_alpha = c->d_ulo = c->d_lx = c->d_ly = nullptr;
   c->d_atrx = c->d_atry = c->d_gbar = nullptr;
   c->d_snode = c->d_sface = c->d_work = c->d_trx = c->d_try = c->d_stage = nullptr;
@@ -254,6 +259,41 @@ crkfr_status ready(crkfr_ctx* c) {
   if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
   if (!c->coef_set) return fail(c, CRKFR_ERR_STATE, "no coefficients set");
   return check_device(c);
+}
+
+// The limiter's arguments of a 2D launch (mode none: left empty).  On a slab
+// of a larger mesh the face kernel takes the smoothed coefficient of the
+// rows next to the slab from alpha_halo.
+void fill_limit_2d(crkfr_ctx* c, Launch2D& L) {
+  if (c->limit_mode == CRKFR_LIMITER_NONE) return;
+  L.lim.mode = c->limit_mode;
+  L.lim.alpha_fixed = c->alpha_fixed;
+  L.lim.alpha = c->d_alpha;
+  L.lim.cnode = c->d_cnode;
+  L.lim.ulo = c->d_ulo;
+  L.lim.lx = c->d_lx;
+  L.lim.ly = c->d_ly;
+  L.lim.alpha_halo = c->subdomain ? c->d_alpha_halo : nullptr;
+}
+
+// A 2D slab with the limiter: at least two element rows (the two rows of
+// the raw indicator each neighbour needs), and the halo rows' buffers.
+crkfr_status check_limited_slab(crkfr_ctx* c) {
+  if (c->dim == 1)
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "the 1D limiter is built for whole periodic meshes");
+  if (c->Ey < 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "a limited slab needs two element rows");
+  if (c->d_araw_halo) return CRKFR_OK;
+  if (cudaMalloc(&c->d_araw_halo, sizeof(double) * 4 * c->Ex) != cudaSuccess ||
+      cudaMalloc(&c->d_alpha_halo, sizeof(double) * 2 * c->Ex) != cudaSuccess) {
+    cudaFree(c->d_araw_halo);
+    cudaFree(c->d_alpha_halo);
+    c->d_araw_halo = c->d_alpha_halo = nullptr;
+    cudaGetLastError();
+    return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+  }
+  CK(c, cudaMemset(c->d_araw_halo, 0, sizeof(double) * 4 * c->Ex));
+  CK(c, cudaMemset(c->d_alpha_halo, 0, sizeof(double) * 2 * c->Ex));
+  return CRKFR_OK;
 }
 
 // rate of state u (max over elements of the wave-speed rate) into `slot`
@@ -447,15 +487,7 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
     }
   } else {
     Launch2D L = make2d(c);
-    if (c->limit_mode != CRKFR_LIMITER_NONE) {
-      L.lim.mode = c->limit_mode;
-      L.lim.alpha_fixed = c->alpha_fixed;
-      L.lim.alpha = c->d_alpha;
-      L.lim.cnode = c->d_cnode;
-      L.lim.ulo = c->d_ulo;
-      L.lim.lx = c->d_lx;
-      L.lim.ly = c->d_ly;
-    }
+    fill_limit_2d(c, L);
     for (int64_t k = 0; k < nsteps; ++k) {
       ctl.slot_read = (int)(c->nstep % 3);
       ctl.slot_write = (int)((c->nstep + 1) % 3);
@@ -756,11 +788,12 @@ crkfr_status crkfr_set_coefficients(crkfr_ctx* c, const double* coef, void* stre
   });
   if (e) return cuda_fail(c, e, "coefficient kernel");
   c->launches += 1;
-  // the limiter's first-order fluxes read the nodal field (a subdomain's
-  // coefficients carry halo rows, and a subdomain has no limiter)
-  if (!c->subdomain)
-    CK(c, cudaMemcpyAsync(c->d_cnode, coef, sizeof(double) * c->n_coef, cudaMemcpyDeviceToDevice,
-                          s));
+  // the limiter's first-order fluxes read the nodal field of the context's
+  // own elements (a subdomain's coefficients start with a halo row/element)
+  const int64_t halo = !c->subdomain ? 0 : c->dim == 2 ? c->Ex * c->basis.n * c->basis.n
+                                                      : c->basis.n;
+  CK(c, cudaMemcpyAsync(c->d_cnode, coef + halo, sizeof(double) * c->n_coef,
+                        cudaMemcpyDeviceToDevice, s));
   c->coef_set = true;
   return CRKFR_OK;
 }
@@ -772,8 +805,10 @@ crkfr_status crkfr_set_limiter(crkfr_ctx* c, int32_t mode, double alpha) {
     return fail(c, CRKFR_ERR_ARG, "unknown limiter mode");
   if (mode != CRKFR_LIMITER_NONE) {
     if (c->cfg.degree < 1) return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter needs N >= 1");
-    if (c->subdomain)
-      return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter is built for whole periodic meshes");
+    if (c->subdomain) {
+      crkfr_status hs = check_limited_slab(c);
+      if (hs != CRKFR_OK) return hs;
+    }
   }
   if (mode == CRKFR_LIMITER_FIXED && !(alpha >= 0.0 && alpha <= 1.0))
     return fail(c, CRKFR_ERR_ARG, "alpha must lie in [0, 1]");
@@ -958,8 +993,10 @@ crkfr_status crkfr_step_host(crkfr_ctx* c, const double* u_in, double* u_out, do
 crkfr_status crkfr_set_subdomain(crkfr_ctx* c, int32_t enable) {
   if (!c) return CRKFR_ERR_ARG;
   if (c->dim == 0) return fail(c, CRKFR_ERR_STATE, "no mesh set");
-  if (enable && c->limit_mode != CRKFR_LIMITER_NONE)
-    return fail(c, CRKFR_ERR_UNSUPPORTED, "the limiter is built for whole periodic meshes");
+  if (enable && c->limit_mode != CRKFR_LIMITER_NONE) {
+    crkfr_status hs = check_limited_slab(c);
+    if (hs != CRKFR_OK) return hs;
+  }
   if (enable && c->dim == 1 && !c->d_ghost) {
     const int n = c->basis.n;
     if (cudaMalloc(&c->d_ghost, sizeof(double) * 2 * ghost_stride_1d(c->M, n)) != cudaSuccess ||
@@ -1003,8 +1040,8 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* c, double** send_bottom, double** sen
 crkfr_status crkfr_step_local(crkfr_ctx* c, const double* u, double dt, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
-  if (c->limit_mode != CRKFR_LIMITER_NONE)
-    return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps run through crkfr_step");
+  if (c->limit_mode != CRKFR_LIMITER_NONE && !(c->dim == 2 && c->subdomain))
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps of a whole mesh run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1028,20 +1065,78 @@ crkfr_status crkfr_step_local(crkfr_ctx* c, const double* u, double dt, void* st
   ctl.slot_reset = (int)((c->nstep + 2) % 3);
   ctl.tslot = (int)(c->nstep % 2);
   Launch2D L = make2d(c);
+  fill_limit_2d(c, L);
   L.ctl = ctl;
   L.u_in = u;
   L.u_out = nullptr;
+  if (c->limit_mode != CRKFR_LIMITER_NONE) {
+    // the blending coefficient of the slab's rows and of the rows next to it,
+    // from the raw indicator of crkfr_step_indicator and the neighbours' rows
+    int ea = timed(c, CRKFR_KERNEL_INDICATOR, s, [&] {
+      return launch_smooth_2d_halo(L, c->d_alpha_raw, c->d_araw_halo, c->d_araw_halo + 2 * c->Ex,
+                                   c->d_alpha, c->d_alpha_halo, s);
+    });
+    if (ea) return cuda_fail(c, ea, "indicator smoothing kernel");
+    c->launches += 1;
+  }
   int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
   if (e) return cuda_fail(c, e, "2D local kernel");
   c->launches += 1;
   return CRKFR_OK;
 }
 
+crkfr_status crkfr_step_indicator(crkfr_ctx* c, const double* u, void* stream) {
+  crkfr_status st = ready(c);
+  if (st != CRKFR_OK) return st;
+  if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (c->dim != 2 || !c->subdomain) return fail(c, CRKFR_ERR_STATE, "not a 2D slab");
+  if (c->limit_mode == CRKFR_LIMITER_NONE) return fail(c, CRKFR_ERR_STATE, "no limiter set");
+  cudaStream_t s = (cudaStream_t)stream;
+  Launch2D L = make2d(c);
+  fill_limit_2d(c, L);
+  L.u_in = u;
+  int e = timed(c, CRKFR_KERNEL_INDICATOR, s,
+                [&] { return launch_indicator_2d(L, c->d_alpha_raw, s); });
+  if (e) return cuda_fail(c, e, "indicator kernel");
+  if (c->limit_mode == CRKFR_LIMITER_BLEND) c->launches += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_limiter_halo_buffers(crkfr_ctx* c, int32_t kind, double** send_bottom,
+                                        double** send_top, double** recv_bottom,
+                                        double** recv_top, int64_t* count) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim != 2 || !c->subdomain) return fail(c, CRKFR_ERR_STATE, "not a 2D slab");
+  if (c->limit_mode == CRKFR_LIMITER_NONE || !c->d_araw_halo || !c->d_ly)
+    return fail(c, CRKFR_ERR_STATE, "no limiter set");
+  const int64_t Ex = c->Ex, Ey = c->Ey, n = c->basis.n;
+  if (kind == 0) {
+    // raw indicator: rows 0, 1 go down, rows Ey-2, Ey-1 go up; rows -2, -1
+    // and Ey, Ey+1 come in
+    if (send_bottom) *send_bottom = c->d_alpha_raw;
+    if (send_top) *send_top = c->d_alpha_raw + (Ey - 2) * Ex;
+    if (recv_bottom) *recv_bottom = c->d_araw_halo;
+    if (recv_top) *recv_top = c->d_araw_halo + 2 * Ex;
+    if (count) *count = 2 * Ex;
+    return CRKFR_OK;
+  }
+  if (kind != 1) return fail(c, CRKFR_ERR_ARG, "kind must be 0 (indicator) or 1 (face data)");
+  // y-face data, rows as the y traces: one (row, side) block of 8 fields
+  const int64_t block = 8 * Ex * n;
+  auto at = [&](int64_t row, int side) { return c->d_ly + (row * 2 + side) * block; };
+  if (send_bottom) *send_bottom = at(1, 0);
+  if (send_top) *send_top = at(Ey, 1);
+  if (recv_bottom) *recv_bottom = at(0, 1);
+  if (recv_top) *recv_top = at(Ey + 1, 0);
+  if (count) *count = block;
+  return CRKFR_OK;
+}
+
 crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
-  if (c->limit_mode != CRKFR_LIMITER_NONE)
-    return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps run through crkfr_step");
+  if (c->limit_mode != CRKFR_LIMITER_NONE && !(c->dim == 2 && c->subdomain))
+    return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps of a whole mesh run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->dim == 1) {
@@ -1075,6 +1170,7 @@ crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
   ctl.slot_write = (int)((c->nstep + 1) % 3);
   ctl.want_rate = 0;
   Launch2D L = make2d(c);
+  fill_limit_2d(c, L);
   L.ctl = ctl;
   L.u_in = u;
   L.u_out = u;

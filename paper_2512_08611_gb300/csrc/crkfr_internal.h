@@ -206,6 +206,9 @@ struct LimitArgs2D {
   double* lx;               // x-face data [8][2][Ey][Ex][n]: side 0 the element's
                             // node p = 0, side 1 node p = N
   double* ly;               // y-face data [Ey+2][2][8][Ex][n], rows as the y traces
+  // slab of a larger mesh (null: periodic in y): the smoothed coefficient of
+  // the element rows below and above the slab, [2][Ex] (row -1, row Ey)
+  const double* alpha_halo;
 };
 
 struct Launch2D {
@@ -285,6 +288,14 @@ int launch_face_2d_limit(const Launch2D& L, void* stream);
 int launch_local_2d_limit_wb(const Launch2D& L, void* stream);
 int launch_face_2d_limit_wb(const Launch2D& L, void* stream);
 int launch_alpha_2d(const Launch2D& L, double* alpha_raw, double* alpha, void* stream);
+// The indicator of the slab's own rows only (a slab of a larger mesh, before
+// the exchange of its boundary rows) and the smoothing with the neighbours'
+// raw rows: raw_below [2][Ex] (rows -2, -1), raw_above [2][Ex] (rows Ey,
+// Ey + 1); writes alpha [Ey][Ex] and alpha_halo [2][Ex] (rows -1, Ey).
+int launch_indicator_2d(const Launch2D& L, double* alpha_raw, void* stream);
+int launch_smooth_2d_halo(const Launch2D& L, const double* alpha_raw, const double* raw_below,
+                          const double* raw_above, double* alpha, double* alpha_halo,
+                          void* stream);
 // c: [Ey][Ex][n][n] (periodic in y) or, with halo_rows, [Ey+2][Ex][n][n]
 // holding the row below and the row above the mesh as rows 0 and Ey+1
 int launch_coef_2d(int N, bool gll, int64_t Ex, int64_t Ey, const double* c, bool halo_rows,

@@ -252,9 +252,19 @@ __global__ void __launch_bounds__(FaceShape<N, LIMIT>::block, FaceShape<N, LIMIT
           lm[fi] = L.lim.ly[((rm * 2 + 1) * kLimFields + fi) * plane + ex * n + p];
           lp[fi] = L.lim.ly[((rp * 2 + 0) * kLimFields + fi) * plane + ex * n + p];
         }
-        // the elements below and above the face (periodic in y)
-        const int64_t eym = (ey0 + k - 1 + Ey) % Ey, eyp = (ey0 + k) % Ey;
-        const double af = 0.5 * (L.lim.alpha[eym * Ex + ex] + L.lim.alpha[eyp * Ex + ex]);
+        // the elements below and above the face: periodic in y, or on a slab
+        // of a larger mesh the rows -1 and Ey from the neighbouring slabs
+        double am, ap;
+        if (L.lim.alpha_halo) {
+          const int64_t eym = ey0 + k - 1, eyp = ey0 + k;
+          am = eym < 0 ? L.lim.alpha_halo[ex] : L.lim.alpha[eym * Ex + ex];
+          ap = eyp >= Ey ? L.lim.alpha_halo[Ex + ex] : L.lim.alpha[eyp * Ex + ex];
+        } else {
+          const int64_t eym = (ey0 + k - 1 + Ey) % Ey, eyp = (ey0 + k) % Ey;
+          am = L.lim.alpha[eym * Ex + ex];
+          ap = L.lim.alpha[eyp * Ex + ex];
+        }
+        const double af = 0.5 * (am + ap);
         const double c2 = 2.0 * dtp * T.inv_dy;
         face_limited<1, WB>(a, b, lm, lp, af, c2 * T.inv_w[N], c2 * T.inv_w[0], T, Tm, Tp, Fm, Fp);
 #pragma unroll

@@ -97,7 +97,61 @@ __global__ void __launch_bounds__(kBlockAlpha) k_alpha_smooth_2d(int64_t Ex, int
   alpha[e] = fmax(raw[e], 0.5 * nb);
 }
 
+// Smoothing of a slab of a larger mesh: rows -1 .. Ey, the raw indicator of
+// rows -2, -1 (raw_below) and Ey, Ey + 1 (raw_above) from the neighbouring
+// slabs; rows 0 .. Ey-1 go to alpha, rows -1 and Ey to alpha_halo.  The same
+// expression as the periodic smoothing, so a split mesh gets the same bits.
+__global__ void __launch_bounds__(kBlockAlpha) k_alpha_smooth_2d_halo(
+    int64_t Ex, int64_t Ey, int mode, double fixed, const double* __restrict__ raw,
+    const double* __restrict__ raw_below, const double* __restrict__ raw_above,
+    double* __restrict__ alpha, double* __restrict__ alpha_halo) {
+  const int64_t i = (int64_t)blockIdx.x * kBlockAlpha + threadIdx.x;
+  if (i >= Ex * (Ey + 2)) return;
+  const int64_t ey = i / Ex - 1, ex = i - (ey + 1) * Ex;   // ey in [-1, Ey]
+  double* out = ey < 0 ? alpha_halo + ex : ey >= Ey ? alpha_halo + Ex + ex : alpha + ey * Ex + ex;
+  if (mode == CRKFR_LIMITER_FIXED) {
+    *out = fixed;
+    return;
+  }
+  // raw indicator of element row r in [-2, Ey + 1], column x
+  auto at = [&](int64_t r, int64_t x) -> double {
+    if (r < 0) return raw_below[(r + 2) * Ex + x];
+    if (r >= Ey) return raw_above[(r - Ey) * Ex + x];
+    return raw[r * Ex + x];
+  };
+  const int64_t xl = ex == 0 ? Ex - 1 : ex - 1, xr = ex == Ex - 1 ? 0 : ex + 1;
+  const double nb = fmax(fmax(at(ey - 1, ex), at(ey + 1, ex)), fmax(at(ey, xl), at(ey, xr)));
+  *out = fmax(at(ey, ex), 0.5 * nb);
+}
+
 }  // namespace
+
+int launch_indicator_2d(const Launch2D& L, double* alpha_raw, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (L.lim.mode != CRKFR_LIMITER_BLEND) return 0;
+  const int64_t Ne = L.Ex * L.Ey;
+  const unsigned blocks = (unsigned)((Ne + kBlockAlpha - 1) / kBlockAlpha);
+  switch (L.N) {
+    case 1: k_alpha_2d<1><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+    case 2: k_alpha_2d<2><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+    case 3: k_alpha_2d<3><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+    case 4: k_alpha_2d<4><<<blocks, kBlockAlpha, 0, s>>>(Ne, L.u_in, L.tab, alpha_raw); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_smooth_2d_halo(const Launch2D& L, const double* alpha_raw, const double* raw_below,
+                          const double* raw_above, double* alpha, double* alpha_halo,
+                          void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t count = L.Ex * (L.Ey + 2);
+  const unsigned blocks = (unsigned)((count + kBlockAlpha - 1) / kBlockAlpha);
+  k_alpha_smooth_2d_halo<<<blocks, kBlockAlpha, 0, s>>>(L.Ex, L.Ey, L.lim.mode, L.lim.alpha_fixed,
+                                                        alpha_raw, raw_below, raw_above, alpha,
+                                                        alpha_halo);
+  return (int)cudaGetLastError();
+}
 
 int launch_local_2d_limit(const Launch2D& L, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;

@@ -82,19 +82,38 @@ class SlabStepper:
         self.group = group
         self.send_bottom, self.send_top, self.recv_bottom, self.recv_top = solver.halo_buffers()
         self.last_dt = None
+        self._lim = None
+
+    def _limiter_buffers(self):
+        """The limiter's halo blocks of a limited 2D slab (None without the
+        limiter): the raw indicator rows and the y-face data."""
+        if self.s.limiter[0] is None:
+            return None
+        if self._lim is None:
+            self._lim = (self.s.limiter_halo_buffers(0), self.s.limiter_halo_buffers(1))
+        return self._lim
 
     def step(self, u, dt=0.0, nsteps=1):
-        """nsteps steps of u in place.  dt > 0: that step; dt <= 0: the CFL
+        """nsteps steps of u in place (with the limiter of a 2D slab when the
+        solver has one: two more exchanges per step).  dt > 0: that step; dt <= 0: the CFL
         step of the whole mesh (Sec. 5, Eq. time.step.2d), the minimum over
         ranks of each slab's own step (crkfr_compute_dt), one all-reduce and
         one host synchronisation per step.  The minimum of C / rate_r over
         slabs is C / max_r rate_r to the last bit (IEEE division is monotone),
         so the ranks take the single-domain step exactly."""
+        lim = self._limiter_buffers()
         for _ in range(nsteps):
             h = dt if dt > 0.0 else min_over_ranks(self.s.compute_dt(u), self.group)
+            if lim is not None:
+                # the limiter: the raw indicator's boundary rows before the
+                # local phase, its face data with the traces after it
+                self.s.step_indicator(u)
+                halo_exchange(*lim[0], self.group)
             self.s.step_local(u, h)
             halo_exchange(self.send_bottom, self.send_top, self.recv_bottom, self.recv_top,
                           self.group)
+            if lim is not None:
+                halo_exchange(*lim[1], self.group)
             self.s.step_faces(u)
             self.last_dt = h
         return u

@@ -1,11 +1,13 @@
-"""The domain-decomposed 2D step on CPU ranks (gloo, world sizes 2 and 3).
+"""The domain-decomposed step on CPU ranks (gloo, world sizes 2 and 3).
 
 1. halo_exchange sends each slab's bottom/top boundary traces to the right
-   ring neighbours.
-2. A step split over ranks — element-local phase per slab, one halo
+   ring neighbours, pairing messages by issue order as NCCL does.
+2. A 2D step split over ranks — element-local phase per slab, one halo
    exchange, face phase per slab — reproduces the single-domain step
-   bitwise.  The arithmetic here is the oracle's (CPU); the exchange is the
-   product's (paper_2512_08611_gb300.distributed)."""
+   bitwise; so do 1D ranges, CFL steps whose size is the minimum over ranks,
+   and the limited 2D step with two rows exchanged.  The arithmetic here is
+   the oracle's (CPU); the exchange and the reduction are the product's
+   (paper_2512_08611_gb300.distributed)."""
 import os
 import socket
 
@@ -206,6 +208,70 @@ def test_split_step_equals_single_domain(world):
         assert p.exitcode == 0
     for r in range(world):
         assert out[r][0], out[r]
+
+
+def _worker_limited(rank, world, port, out):
+    """The limited 2D step (Sec. 4, tensor-product reading) of a slab depends
+    on two element rows beyond each of its boundaries (the neighbours' raw
+    indicator for the smoothing of the row next to the slab, that row's face
+    data): each rank exchanges its two boundary rows of u with the product's
+    exchange and runs the oracle's limited step on its slab extended by
+    them (whose own results are dropped); the slab equals the single-domain
+    oracle step bitwise."""
+    from oracle.basis import Basis
+    from oracle.crkfr import Scheme2D
+    from oracle.limiter import Blending2D
+    from oracle.systems import ShallowWater2D
+    from paper_2512_08611_gb300.distributed import halo_exchange, slab_rows
+    _init(rank, world, port)
+    N, Ey, Ex, L = 2, 8, 5, 1.0
+    bs = Basis(N, "gll")
+    dx, dy = L / Ex, L / Ey
+    x = (np.arange(Ex)[None, :, None, None] + bs.xi[None, None, None, :]) * dx
+    y = (np.arange(Ey)[:, None, None, None] + bs.xi[None, None, :, None]) * dy
+    x, y = np.broadcast_arrays(x, y)
+    h = np.where((x - 0.45) ** 2 + (y - 0.52) ** 2 < 0.09, 1.0, 1e-3)
+    b = np.zeros_like(h)
+    u = np.stack([h, 0.0 * h, 0.0 * h])
+    sch = Scheme2D(ShallowWater2D(9.81), N, dx, dy, family="gll")
+    lim = Blending2D(sch)
+    dt = 0.2 * sch.compute_dt(u, b, 0.1, 1.0)
+    first, count = slab_rows(Ey, rank, world)
+    v, want = u[:, first:first + count].copy(), u.copy()
+    ok = True
+    for _ in range(3):
+        send_bottom = torch.from_numpy(np.ascontiguousarray(v[:, :2]).ravel())
+        send_top = torch.from_numpy(np.ascontiguousarray(v[:, -2:]).ravel())
+        recv_bottom, recv_top = torch.empty_like(send_top), torch.empty_like(send_bottom)
+        halo_exchange(send_bottom, send_top, recv_bottom, recv_top)
+        shape = (3, 2) + v.shape[2:]
+        ext = np.concatenate([recv_bottom.numpy().reshape(shape), v,
+                              recv_top.numpy().reshape(shape)], axis=1)
+        rows = [(first + k) % Ey for k in range(-2, count + 2)]
+        v = lim.step(ext, b[rows], dt)[:, 2:-2]
+        want = lim.step(want, b, dt)
+        ok &= bool(np.array_equal(v, want[:, first:first + count]))
+    out[rank] = (ok, float(np.max(np.abs(v - want[:, first:first + count]))),
+                 float(np.max(lim.last_alpha)))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_limited_step_equals_single_domain(world):
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_limited, args=(r, world, port, out))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert out[r][0], out[r]
+    # the indicator is active on the mesh
+    assert max(out[r][2] for r in range(world)) > 0.1
 
 
 def test_slab_rows_cover_the_mesh():

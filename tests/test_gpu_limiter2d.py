@@ -202,19 +202,121 @@ def test_limiter_configuration_errors_2d(crk):
     s = crk.Solver("swe2d", 2, gravity=G)
     s.set_mesh([4, 4], [0.0, 0.0], [1.0, 1.0])
     s.set_limiter("blend")
-    # subdomains exchange halo rows the limiter does not carry
-    with pytest.raises(crk.CrkfrError) as e:
-        s.set_subdomain(True)
-    assert e.value.status == -2
-    s.set_limiter(None)
+    # a limited slab of at least two rows, in either order of the calls
     s.set_subdomain(True)
-    with pytest.raises(crk.CrkfrError) as e:
-        s.set_limiter("fixed", 0.5)
-    assert e.value.status == -2
+    s.set_limiter(None)
+    s.set_limiter("fixed", 0.5)
     s.set_subdomain(False)
     with pytest.raises(crk.CrkfrError) as e:
         s.set_limiter("fixed", -0.1)
     assert e.value.status == -1
+    # a one-row slab cannot send the two indicator rows its neighbours need
+    t = crk.Solver("swe2d", 2, gravity=G)
+    t.set_mesh([4, 1], [0.0, 0.0], [1.0, 0.25])
+    t.set_subdomain(True)
+    with pytest.raises(crk.CrkfrError) as e:
+        t.set_limiter("blend")
+    assert e.value.status == -2
+    t.set_subdomain(False)
+    t.set_limiter("blend")
+    with pytest.raises(crk.CrkfrError) as e:
+        t.set_subdomain(True)
+    assert e.value.status == -2
+    # 1D ranges refuse the limiter; whole meshes have no limiter halo blocks
+    r = crk.Solver("swe1d", 2, gravity=G)
+    r.set_mesh([8], [0.0], [1.0])
+    r.set_subdomain(True)
+    with pytest.raises(crk.CrkfrError) as e:
+        r.set_limiter("blend")
+    assert e.value.status == -2
+    with pytest.raises(crk.CrkfrError) as e:
+        s.limiter_halo_buffers(0)
+    assert e.value.status == -6
+
+
+def limited_slab(crk, system, N, Ex, Ey, c, first, count, mode, alpha, source=None, coef=0.0):
+    cfl = golden_cfl_imex(N, "gll") if source else golden_cfl(N, "gll")
+    s = crk.Solver(system, N, nodes="gll", gravity=G, cfl_safety=0.1, cfl_number=cfl,
+                   source=source, source_coef=coef)
+    dy = 1.0 / Ey
+    s.set_mesh([Ex, count], [0.0, first * dy], [1.0, (first + count) * dy])
+    s.set_subdomain(True)
+    rows = [(first - 1) % Ey] + list(range(first, first + count)) + [(first + count) % Ey]
+    s.set_coefficients(to_dev(np.ascontiguousarray(c[rows])))
+    s.set_limiter(mode, alpha)
+    return s
+
+
+def ring(bufs):
+    """In-process exchange of one kind of halo block between slabs stacked
+    in order on a periodic ring."""
+    k_ = len(bufs)
+    for k in range(k_):
+        bufs[k][2].copy_(bufs[(k - 1) % k_][1])    # recv_bottom <- send_top of the slab below
+        bufs[k][3].copy_(bufs[(k + 1) % k_][0])    # recv_top <- send_bottom of the slab above
+
+
+@pytest.mark.parametrize("system,N,mode,alpha,source", [
+    ("swe2d", 3, "blend", 0.0, None), ("swe2d", 2, "fixed", 0.4, None),
+    ("swe2d_wb", 2, "blend", 0.0, None), ("swe2d", 3, "blend", 0.0, "chezy")])
+def test_limited_slabs_equal_single_domain(crk, system, N, mode, alpha, source):
+    """A circular dam break across three slabs (of 5, 2 and 9 rows, the
+    second only as tall as the two indicator rows a slab sends): raw
+    indicator, exchange of its boundary rows, local phase, exchange of the
+    traces and the limiter's face data, face phase.  The slabs' states and
+    blending coefficients equal the single-domain limited step bit for bit."""
+    Ex, Ey, steps = 16, 16, 4
+    u, b, dx, dy = dam(N, Ex, Ey)
+    coef = 2.0 if source else 0.0
+    m = solver(crk, system, N, "gll", Ex, Ey, b, cs=0.1, source=source, coef=coef)
+    m.set_limiter(mode, alpha)
+    want = to_dev(u)
+    dt = m.compute_dt(want)
+    m.step(want, dt, steps)
+    parts = [(0, 5), (5, 2), (7, 9)]
+    slabs = [limited_slab(crk, system, N, Ex, Ey, b, f, c, mode, alpha, source, coef)
+             for f, c in parts]
+    states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    traces = [s.halo_buffers() for s in slabs]
+    raw = [s.limiter_halo_buffers(0) for s in slabs]
+    face = [s.limiter_halo_buffers(1) for s in slabs]
+    for _ in range(steps):
+        for s, x in zip(slabs, states):
+            s.step_indicator(x)
+        ring(raw)
+        for s, x in zip(slabs, states):
+            s.step_local(x, dt)
+        ring(traces)
+        ring(face)
+        for s, x in zip(slabs, states):
+            s.step_faces(x)
+    got = np.concatenate([to_host(x) for x in states], axis=1)
+    assert np.array_equal(got, to_host(want)), rel_l2(got, to_host(want))
+    a = np.concatenate([to_host(s.limiter_alpha()) for s in slabs], axis=0)
+    a_want = to_host(m.limiter_alpha())
+    assert np.array_equal(a, a_want)
+    if mode == "blend":
+        # the dam (y in 0.30 .. 0.70) spans the slab boundaries at y = 5/16, 7/16
+        assert np.max(a_want) > 0.5 and np.min(a_want) == 0.0
+
+
+def test_single_limited_slab_through_the_stepper(crk):
+    """One limited slab, its own periodic neighbour, stepped by SlabStepper
+    (which adds the limiter's exchanges), in CFL steps."""
+    from paper_2512_08611_gb300.distributed import SlabStepper
+    N, Ex, Ey = 3, 12, 10
+    u, b, dx, dy = dam(N, Ex, Ey)
+    m = solver(crk, "swe2d", N, "gll", Ex, Ey, b, cs=0.1)
+    m.set_limiter("blend")
+    s = limited_slab(crk, "swe2d", N, Ex, Ey, b, 0, Ey, "blend", 0.0)
+    x, want = to_dev(u), to_dev(u)
+    st = SlabStepper(s)
+    for _ in range(3):
+        dt = m.compute_dt(want)
+        m.step(want, dt, 1)
+        st.step(x, 0.0, 1)
+        assert st.last_dt == dt
+    assert np.array_equal(to_host(x), to_host(want))
 
 
 def test_phased_and_adjoint_steps_refuse_the_limiter(crk):
