@@ -262,15 +262,20 @@ crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_
  * state of the element beyond it: crkfr_set_coefficients expects
  * c[E_local + 2][n] (element 0 the left neighbour element, E_local + 1 the
  * right one); crkfr_halo_buffers gives send_bottom (the state [var][n] of
- * this range's first element: the rank on the left stores it as its
- * recv_top), send_top (its last element: becomes the right rank's
- * recv_bottom), recv_bottom (the left neighbour element's state) and
- * recv_top (the right one's), `count` = vars (N+1) doubles each, in a
- * context-owned buffer allocated by crkfr_set_subdomain; crkfr_step_local
- * (dt > 0) writes the send blocks; crkfr_step_faces runs the step of the
- * range with those neighbour states and writes u_dev (through the
- * context's work buffer).  The limiter is refused on ranges
- * (CRKFR_ERR_UNSUPPORTED).
+ * this range's first element, then the raw limiter indicator of its first
+ * and second elements: the rank on the left stores it as its recv_top),
+ * send_top (its last element's state, then the raw indicator of its last
+ * and second-to-last elements: becomes the right rank's recv_bottom),
+ * recv_bottom (the left neighbour's) and recv_top (the right one's),
+ * `count` = vars (N+1) + 2 doubles each, in a context-owned buffer
+ * allocated by crkfr_set_subdomain; crkfr_step_local (dt > 0) computes the
+ * raw indicator of the range's elements when the limiter uses it and writes
+ * the send blocks (without an indicator its two slots are zero);
+ * crkfr_step_faces runs the step of the range with those neighbour states
+ * and writes u_dev (through the context's work buffer).  The limiter needs
+ * a range of at least two elements (else CRKFR_ERR_UNSUPPORTED): alpha_e of
+ * the element next to the range, which the face between two ranges blends
+ * with, takes the raw indicator of the element beyond it into account.
  *
  * The subcell blending limiter on 2D slabs (crkfr_set_limiter on a slab of
  * at least two element rows, else CRKFR_ERR_UNSUPPORTED) adds two exchanges

@@ -198,12 +198,23 @@ __global__ void k_math_check(const double* __restrict__ x, double* __restrict__ 
 }
 
 // the two end elements' states of a 1D subdomain: send[side][v][p]
-__global__ void k_pack_ends_1d(const double* __restrict__ u, double* __restrict__ send,
-                               int64_t E, int M, int n) {
+// The two end elements of a 1D range for its neighbours, per side
+// ghost_dyn_1d(M, n) doubles: u [M][n] of the end element, then the raw
+// limiter indicator of the end element and of the next one inwards (raw
+// null, no indicator: zeros; raw needs E >= 2).
+__global__ void k_pack_ends_1d(const double* __restrict__ u, const double* __restrict__ raw,
+                               double* __restrict__ send, int64_t E, int M, int n) {
+  const int per = ghost_dyn_1d(M, n);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * M * n) return;
-  const int side = i / (M * n), v = (i / n) % M, p = i % n;
-  send[i] = u[((int64_t)v * E + (side ? E - 1 : 0)) * n + p];
+  if (i >= 2 * per) return;
+  const int side = i / per, j = i - side * per;
+  if (j < M * n) {
+    const int v = j / n, p = j - v * n;
+    send[i] = u[((int64_t)v * E + (side ? E - 1 : 0)) * n + p];
+  } else {
+    const int k = j - M * n;   // 0: the end element, 1: the next one inwards
+    send[i] = raw ? raw[side ? E - 1 - k : k] : 0.0;
+  }
 }
 
 __global__ void k_set_time(DevState* st, int slot, double t) {
@@ -276,11 +287,15 @@ void fill_limit_2d(crkfr_ctx* c, Launch2D& L) {
   L.lim.alpha_halo = c->subdomain ? c->d_alpha_halo : nullptr;
 }
 
-// A 2D slab with the limiter: at least two element rows (the two rows of
-// the raw indicator each neighbour needs), and the halo rows' buffers.
+// A subdomain with the limiter: a 1D range of at least two elements, a 2D
+// slab of at least two element rows (the two elements / rows of raw
+// indicator each neighbour needs) with the halo rows' buffers.
 crkfr_status check_limited_slab(crkfr_ctx* c) {
-  if (c->dim == 1)
-    return fail(c, CRKFR_ERR_UNSUPPORTED, "the 1D limiter is built for whole periodic meshes");
+  if (c->dim == 1) {
+    // a range sends the raw indicator of its two end elements per side
+    if (c->Ex < 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "a limited range needs two elements");
+    return CRKFR_OK;
+  }
   if (c->Ey < 2) return fail(c, CRKFR_ERR_UNSUPPORTED, "a limited slab needs two element rows");
   if (c->d_araw_halo) return CRKFR_OK;
   if (cudaMalloc(&c->d_araw_halo, sizeof(double) * 4 * c->Ex) != cudaSuccess ||
@@ -770,13 +785,17 @@ crkfr_status crkfr_set_coefficients(crkfr_ctx* c, const double* coef, void* stre
     if (c->dim == 1 && c->subdomain) {
       // coef[E + 2][n]: the left neighbour element, the subdomain, the right
       // neighbour element; the neighbours' static terms go to the ghosts
-      const int n = c->basis.n, gs = ghost_stride_1d(c->M, n), mn = c->M * n;
+      const int n = c->basis.n, gs = ghost_stride_1d(c->M, n), gd = ghost_dyn_1d(c->M, n);
       int r = launch_coef_1d(c->cfg.system, c->cfg.degree, c->Ex, coef + n, c->d_snode,
                              c->d_sface, c->tab, s);
       for (int side = 0; side < 2 && !r; ++side) {
         double* g = c->d_ghost + side * gs;
-        r = launch_coef_1d(c->cfg.system, c->cfg.degree, 1, coef + (side ? c->Ex + 1 : 0) * n,
-                           g + mn, g + mn + n, c->tab, s);
+        const double* ce = coef + (side ? c->Ex + 1 : 0) * n;
+        r = launch_coef_1d(c->cfg.system, c->cfg.degree, 1, ce, g + gd, g + gd + n, c->tab, s);
+        // the nodal c of the ghost element (the limiter's first-order fluxes)
+        if (!r)
+          r = (int)cudaMemcpyAsync(g + gd + n + 2, ce, sizeof(double) * n,
+                                   cudaMemcpyDeviceToDevice, s);
       }
       return r;
     }
@@ -1000,7 +1019,7 @@ crkfr_status crkfr_set_subdomain(crkfr_ctx* c, int32_t enable) {
   if (enable && c->dim == 1 && !c->d_ghost) {
     const int n = c->basis.n;
     if (cudaMalloc(&c->d_ghost, sizeof(double) * 2 * ghost_stride_1d(c->M, n)) != cudaSuccess ||
-        cudaMalloc(&c->d_send, sizeof(double) * 2 * c->M * n) != cudaSuccess) {
+        cudaMalloc(&c->d_send, sizeof(double) * 2 * ghost_dyn_1d(c->M, n)) != cudaSuccess) {
       cudaGetLastError();
       return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
     }
@@ -1016,12 +1035,12 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* c, double** send_bottom, double** sen
   if (c->dim == 1) {
     // the end elements' states (left = bottom, right = top) and the ghosts
     if (!c->subdomain || !c->d_ghost) return fail(c, CRKFR_ERR_STATE, "not a 1D subdomain");
-    const int64_t mn = (int64_t)c->M * c->basis.n;
+    const int64_t gd = ghost_dyn_1d(c->M, c->basis.n);
     if (send_bottom) *send_bottom = c->d_send;
-    if (send_top) *send_top = c->d_send + mn;
+    if (send_top) *send_top = c->d_send + gd;
     if (recv_bottom) *recv_bottom = c->d_ghost;
     if (recv_top) *recv_top = c->d_ghost + ghost_stride_1d(c->M, c->basis.n);
-    if (count) *count = mn;
+    if (count) *count = gd;
     return CRKFR_OK;
   }
   if (c->dim != 2) return fail(c, CRKFR_ERR_STATE, "no mesh set");
@@ -1040,17 +1059,28 @@ crkfr_status crkfr_halo_buffers(crkfr_ctx* c, double** send_bottom, double** sen
 crkfr_status crkfr_step_local(crkfr_ctx* c, const double* u, double dt, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
-  if (c->limit_mode != CRKFR_LIMITER_NONE && !(c->dim == 2 && c->subdomain))
+  if (c->limit_mode != CRKFR_LIMITER_NONE && !c->subdomain)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps of a whole mesh run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->dim == 1) {
     // 1D: the fused step recomputes the neighbours' stages itself, so the
-    // local phase only packs this slab's end elements for the exchange
+    // local phase only packs this range's end elements for the exchange,
+    // with the limiter's raw indicator of the two elements at each end
     if (!c->subdomain) return fail(c, CRKFR_ERR_STATE, "phased 1D steps need a subdomain");
-    const int n = c->basis.n, total = 2 * c->M * n;
-    k_pack_ends_1d<<<(total + 127) / 128, 128, 0, s>>>(u, c->d_send, c->Ex, c->M, n);
+    const bool raw = c->limit_mode == CRKFR_LIMITER_BLEND;
+    if (raw) {
+      Launch1D L = make1d(c);
+      L.u_in = u;
+      int ea = timed(c, CRKFR_KERNEL_INDICATOR, s,
+                     [&] { return launch_alpha_1d(L, c->d_alpha_raw, s); });
+      if (ea) return cuda_fail(c, ea, "indicator kernel");
+      c->launches += 1;
+    }
+    const int n = c->basis.n, total = 2 * ghost_dyn_1d(c->M, n);
+    k_pack_ends_1d<<<(total + 127) / 128, 128, 0, s>>>(u, raw ? c->d_alpha_raw : nullptr,
+                                                       c->d_send, c->Ex, c->M, n);
     CK(c, cudaGetLastError());
     c->launches += 1;
     c->sub_dt = dt;
@@ -1135,7 +1165,7 @@ crkfr_status crkfr_limiter_halo_buffers(crkfr_ctx* c, int32_t kind, double** sen
 crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
-  if (c->limit_mode != CRKFR_LIMITER_NONE && !(c->dim == 2 && c->subdomain))
+  if (c->limit_mode != CRKFR_LIMITER_NONE && !c->subdomain)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "limited steps of a whole mesh run through crkfr_step");
   if (!u) return fail(c, CRKFR_ERR_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;

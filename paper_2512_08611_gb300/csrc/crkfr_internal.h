@@ -141,8 +141,10 @@ struct Launch1D {
   LimitArgs lim;         // mode 0: no limiter
   // subdomain of a larger 1D mesh: the element left of element 0 and the
   // element right of element E-1 come from here instead of the periodic
-  // wrap; per side ghost_stride_1d(M, n) doubles: u [M][n], the static node
-  // terms [n], the face traces of c [2] (null: periodic)
+  // wrap; per side ghost_stride_1d(M, n) doubles: u [M][n] and the raw
+  // limiter indicator of that element and of the one beyond it [2] (both
+  // exchanged every step: ghost_dyn_1d(M, n) doubles), then the static node
+  // terms [n], the face traces of c [2] and the nodal c [n] (null: periodic)
   const double* ghost;
   // threads per block of the unlimited step: 0 = chosen per mesh, else 64,
   // 96 or 128
@@ -151,7 +153,11 @@ struct Launch1D {
 #ifdef __CUDACC__
 __host__ __device__
 #endif
-constexpr int ghost_stride_1d(int M, int n) { return M * n + n + 2; }
+constexpr int ghost_dyn_1d(int M, int n) { return M * n + 2; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int ghost_stride_1d(int M, int n) { return M * n + 2 * n + 4; }
 int launch_step_1d(const Launch1D& L, void* stream);
 int launch_step_1d_limit(const Launch1D& L, void* stream);   // kernels_limit.cu
 int launch_alpha_1d(const Launch1D& L, double* alpha_raw, void* stream);

@@ -205,6 +205,7 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   double sn[n];
   double c_l, c_r;
   const bool from_ghost = ghost != nullptr && (e_raw < 0 || e_raw >= E);
+  constexpr int GD = ghost_dyn_1d(M, n);   // static part of a ghost after GD doubles
   if (from_ghost) {
     const double* gs = ghost + (e_raw < 0 ? 0 : ghost_stride_1d(M, n));
 #pragma unroll
@@ -212,9 +213,9 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
 #pragma unroll
       for (int p = 0; p < n; ++p) u0[v][p] = gs[v * n + p];
 #pragma unroll
-    for (int p = 0; p < n; ++p) sn[p] = gs[M * n + p];
-    c_l = gs[M * n + n];
-    c_r = gs[M * n + n + 1];
+    for (int p = 0; p < n; ++p) sn[p] = gs[GD + p];
+    c_l = gs[GD + n];
+    c_r = gs[GD + n + 1];
   } else {
 #pragma unroll
     for (int v = 0; v < M; ++v)
@@ -239,10 +240,28 @@ __device__ __forceinline__ void step_1d_tile(const Tables& T, double xs,
   __shared__ double sm_al[LB];
   __shared__ double sm_F[LM][LB];
   if constexpr (LIMIT) {
+    if (from_ghost) {
+      const double* gs = ghost + (e_raw < 0 ? 0 : ghost_stride_1d(M, n));
 #pragma unroll
-    for (int p = 0; p < n; ++p) cn[p] = LA.cnode[e * n + p];
+      for (int p = 0; p < n; ++p) cn[p] = gs[GD + n + 2 + p];
+    } else {
+#pragma unroll
+      for (int p = 0; p < n; ++p) cn[p] = LA.cnode[e * n + p];
+    }
     if (LA.mode == 2) {
       alpha = LA.alpha_fixed;
+    } else if (ghost) {
+      // a range of a larger mesh: the raw indicator of elements -2, -1 and
+      // E, E+1 comes with the ghosts (slot 0 the adjacent element, slot 1
+      // the one beyond it); threads past E+1 only need in-bounds reads
+      auto raw = [&](int64_t r) -> double {
+        if (r < 0) return ghost[M * n + (r < -2 ? 1 : -1 - r)];
+        if (r >= E) return ghost[ghost_stride_1d(M, n) + M * n + (r > E + 1 ? 1 : r - E)];
+        return LA.alpha_raw[r];
+      };
+      const double r0 = raw(e_raw);
+      const double rn = fmax(raw(e_raw - 1), raw(e_raw + 1));
+      alpha = fmax(r0, 0.5 * rn);
     } else {
       const int64_t em = e == 0 ? E - 1 : e - 1, ep = e == E - 1 ? 0 : e + 1;
       const double r0 = LA.alpha_raw[e];

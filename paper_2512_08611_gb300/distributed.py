@@ -87,8 +87,8 @@ class SlabStepper:
     def _limiter_buffers(self):
         """The limiter's halo blocks of a limited 2D slab (None without the
         limiter): the raw indicator rows and the y-face data."""
-        if self.s.limiter[0] is None:
-            return None
+        if self.s.limiter[0] is None or len(self.s.n_elem) == 1:
+            return None   # (a 1D range's exchange carries the indicator itself)
         if self._lim is None:
             self._lim = (self.s.limiter_halo_buffers(0), self.s.limiter_halo_buffers(1))
         return self._lim

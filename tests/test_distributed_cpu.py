@@ -274,6 +274,61 @@ def test_split_limited_step_equals_single_domain(world):
     assert max(out[r][2] for r in range(world)) > 0.1
 
 
+def _worker_limited_1d(rank, world, port, out):
+    """The limited 1D step of a range depends on two elements beyond each
+    end: ranks exchange their two end elements and run the oracle's limited
+    step on the extended range, dropping the ends' results."""
+    from oracle.basis import Basis
+    from oracle.crkfr import Scheme1D
+    from oracle.limiter import Blending1D
+    from oracle.systems import ShallowWater1D
+    from paper_2512_08611_gb300.distributed import halo_exchange, slab_rows
+    _init(rank, world, port)
+    N, E, L = 3, 30, 10.0
+    bs = Basis(N, "gll")
+    x = (np.arange(E)[:, None] + bs.xi[None, :]) * (L / E)
+    h = np.where((x > 2.61) & (x < 6.37), 1.0, 1e-3)
+    b = np.zeros_like(h)
+    u = np.stack([h, 0.0 * h])
+    sch = Scheme1D(ShallowWater1D(9.81), N, L / E, family="gll")
+    lim = Blending1D(sch)
+    dt = 0.2 * sch.compute_dt(u, b, 0.1, 1.0)
+    first, count = slab_rows(E, rank, world)
+    v, want = u[:, first:first + count].copy(), u.copy()
+    ok = True
+    for _ in range(3):
+        send_left = torch.from_numpy(np.ascontiguousarray(v[:, :2]).ravel())
+        send_right = torch.from_numpy(np.ascontiguousarray(v[:, -2:]).ravel())
+        ghost_left, ghost_right = torch.empty_like(send_right), torch.empty_like(send_left)
+        halo_exchange(send_left, send_right, ghost_left, ghost_right)
+        ext = np.concatenate([ghost_left.numpy().reshape(2, 2, N + 1), v,
+                              ghost_right.numpy().reshape(2, 2, N + 1)], axis=1)
+        el = [(first + k) % E for k in range(-2, count + 2)]
+        v = lim.step(ext, b[el], dt)[:, 2:-2]
+        want = lim.step(want, b, dt)
+        ok &= bool(np.array_equal(v, want[:, first:first + count]))
+    out[rank] = (ok, float(np.max(np.abs(v - want[:, first:first + count]))),
+                 float(np.max(lim.last_alpha)))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_limited_1d_step_equals_single_domain(world):
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_limited_1d, args=(r, world, port, out))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert out[r][0], out[r]
+    assert max(out[r][2] for r in range(world)) > 0.1
+
+
 def test_slab_rows_cover_the_mesh():
     from paper_2512_08611_gb300.distributed import slab_rows
     for G in (1, 7, 1024):

@@ -196,3 +196,114 @@ def test_config2_size_with_limiter(crk):
     s.step(du, 0.0, 1)
     assert rel_l2(to_host(du), want) < TOL_STEP
     assert np.max(np.abs(to_host(s.limiter_alpha()) - lim.last_alpha)) < 1e-12
+
+
+def dam_on(N, E, L, hR=1e-3):
+    """The dam break on [0, L] (GLL nodes), jumps inside elements 101 and 301
+    of 400."""
+    bs = Basis(N, "gll")
+    x, dx = positions_1d(bs, E, 0.0, L)
+    h = np.where((x > 0.2537 * L) & (x < 0.7537 * L), 1.0, 1e-3)
+    return np.stack([h, np.zeros_like(h)]), np.zeros_like(h), dx
+
+
+def smooth_on(N, E, L):
+    bs = Basis(N, "gll")
+    x, dx = positions_1d(bs, E, 0.0, L)
+    b = 0.1 * np.sin(2 * np.pi * x / L) ** 2
+    u = np.stack([1.0 + 0.1 * np.cos(2 * np.pi * x / L) - b, 0.3 * np.sin(2 * np.pi * x / L)])
+    return u, b, dx
+
+
+# (the dam break needs the indicator: with a fixed alpha, or at N = 2, the
+# blended step's depth goes negative within a few CFL steps of C_s = 0.1, in
+# the oracle as on the GPU)
+@pytest.mark.parametrize("system,N,mode,alpha,source,data", [
+    ("swe1d", 3, "blend", 0.0, None, "dam"), ("swe1d", 4, "blend", 0.0, None, "dam"),
+    ("swe1d", 2, "fixed", 0.4, None, "smooth"), ("swe1d_wb", 3, "blend", 0.0, None, "dam"),
+    ("swe1d", 3, "blend", 0.0, "chezy", "dam")])
+def test_limited_ranges_equal_single_domain(crk, system, N, mode, alpha, source, data):
+    """Four ranges of a 400-element mesh (100, 2, 199 and 99 elements; the
+    dam's jumps lie in elements 101 and 301, at the range ends 101 | 102 and
+    300 | 301), each exchanging its end elements' states and raw indicator
+    with its neighbours: the ranges' states and blending coefficients equal
+    the single-domain limited step bit for bit."""
+    E, L, steps = 400, 100.0, 5        # dx = 1/4: every range's 1/dx is the mesh's
+    u, b, dx = dam_on(N, E, L) if data == "dam" else smooth_on(N, E, L)
+    cfl = golden_cfl_imex(N, "gll") if source else golden_cfl(N, "gll")
+    coef = 2.0 if source else 0.0
+
+    def make(first, count):
+        s = crk.Solver(system, N, nodes="gll", gravity=G, cfl_safety=0.1, cfl_number=cfl,
+                       source=source, source_coef=coef)
+        s.set_mesh([count], [first * dx], [(first + count) * dx])
+        return s
+    m = make(0, E)
+    m.set_coefficients(to_dev(b))
+    m.set_limiter(mode, alpha)
+    want = to_dev(u)
+    parts = [(0, 100), (100, 2), (102, 199), (301, 99)]
+    ranges = []
+    for f, c in parts:
+        s = make(f, c)
+        s.set_subdomain(True)
+        el = [(f - 1) % E] + list(range(f, f + c)) + [(f + c) % E]
+        s.set_coefficients(to_dev(np.ascontiguousarray(b[el])))
+        s.set_limiter(mode, alpha)
+        ranges.append(s)
+    states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    bufs = [s.halo_buffers() for s in ranges]
+    k_ = len(parts)
+    for _ in range(steps):
+        # the CFL step of the state (the dam's speeds grow as it breaks)
+        dt = m.compute_dt(want)
+        m.step(want, dt, 1)
+        for s, x in zip(ranges, states):
+            s.step_local(x, dt)
+        for k in range(k_):
+            bufs[k][2].copy_(bufs[(k - 1) % k_][1])    # left ghost <- right end of the left range
+            bufs[k][3].copy_(bufs[(k + 1) % k_][0])    # right ghost <- left end of the right range
+        for s, x in zip(ranges, states):
+            s.step_faces(x)
+    got = np.concatenate([to_host(x) for x in states], axis=1)
+    assert np.all(np.isfinite(got)) and np.min(got[0]) > 0.0
+    assert np.array_equal(got, to_host(want)), rel_l2(got, to_host(want))
+    a = np.concatenate([to_host(s.limiter_alpha()) for s in ranges])
+    a_want = to_host(m.limiter_alpha())
+    assert np.array_equal(a, a_want)
+    if data == "dam":
+        assert np.max(a_want[[99, 100, 101, 102, 299, 300, 301, 302]]) > 0.5
+        assert np.min(a_want) == 0.0
+
+
+def test_limited_range_configuration(crk):
+    """A limited range needs two elements; the stepper runs a limited range
+    that is its own periodic neighbour, in CFL steps."""
+    from paper_2512_08611_gb300.distributed import SlabStepper
+    r = crk.Solver("swe1d", 2, gravity=G)
+    r.set_mesh([1], [0.0], [1.0])
+    r.set_subdomain(True)
+    with pytest.raises(crk.CrkfrError) as e:
+        r.set_limiter("blend")
+    assert e.value.status == -2
+    N, E, L = 3, 40, 100.0
+    u, b, dx = dam_on(N, E, L)
+    m = crk.Solver("swe1d", N, nodes="gll", gravity=G, cfl_safety=0.1,
+                   cfl_number=golden_cfl(N, "gll"))
+    m.set_mesh([E], [0.0], [L])
+    m.set_coefficients(to_dev(b))
+    m.set_limiter("blend")
+    s = crk.Solver("swe1d", N, nodes="gll", gravity=G, cfl_safety=0.1,
+                   cfl_number=golden_cfl(N, "gll"))
+    s.set_mesh([E], [0.0], [L])
+    s.set_subdomain(True)
+    s.set_coefficients(to_dev(np.ascontiguousarray(b[[E - 1] + list(range(E)) + [0]])))
+    s.set_limiter("blend")
+    x, want = to_dev(u), to_dev(u)
+    st = SlabStepper(s)
+    for _ in range(3):
+        dt = m.compute_dt(want)
+        m.step(want, dt, 1)
+        st.step(x, 0.0, 1)
+        assert st.last_dt == dt
+    assert np.array_equal(to_host(x), to_host(want))
