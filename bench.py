@@ -354,8 +354,6 @@ def run_ours(args, wl):
     # the slab (1D: range) path of the multi-GPU runs; --split runs it on one
     # GPU, where the slab is its own periodic neighbour
     split = world > 1 or args.split
-    if split and wl.limiter and wl.dim == 1:
-        raise SystemExit("split 1D runs use the unlimited workload")
     s = crkfr.Solver(wl.system, wl.N, gravity=G, cfl_safety=0.5, source=wl.source,
                      source_coef=wl.source_coef)
     if split and wl.dim == 2:
