@@ -413,16 +413,19 @@ int launch_local_t(const Launch2D& L, cudaStream_t s) {
     // the step: twice as many blocks as fit the GPU at once, each taking
     // element groups in turn, so that no block starts cold after the first
     // ones (1.5 % faster than one block per group at 1024^2)
-    static int resident = -1;
-    if (resident < 0) {
+    // (resident blocks on the GPU, asked once; 0 if the query failed: then
+    // one block per group)
+    static const int resident = [] {
       int nb = 0, dev = 0, sms = 0;
       if (cudaGetDevice(&dev) != cudaSuccess ||
           cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &nb, k_local_2d<N, GLL, false, IMEX, WB>, kBlockLocal, 0) != cudaSuccess)
-        return (int)cudaGetLastError();
-      resident = nb * sms;
-    }
+              &nb, k_local_2d<N, GLL, false, IMEX, WB>, kBlockLocal, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb * sms;
+    }();
     const int64_t grid = resident > 0 && 2 * (int64_t)resident < blocks ? 2 * resident : blocks;
     k_local_2d<N, GLL, false, IMEX, WB><<<(unsigned)grid, kBlockLocal, 0, s>>>(L);
   }

@@ -731,23 +731,31 @@ int launch_step_t(const Launch1D& L, cudaStream_t s) {
     k_step_1d<SYS, N, GLL, true, IMEX><<<(unsigned)blocks, kBlock1D, 0, s>>>(L);
     return (int)cudaGetLastError();
   }
-  // resident blocks per SM of each block size (the occupancy API, once)
-  static int sms = -1;
-  static int resident[3];
-  if (sms < 0) {
-    int dev = 0, n = 0;
+  // SMs and resident blocks per SM of each block size (the occupancy API,
+  // asked once; if the query failed, 128-thread tiles)
+  struct Occ {
+    int sms = 0;
+    int resident[3] = {0, 0, 0};
+  };
+  static const Occ occ = [] {
+    Occ o;
+    int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &resident[0], k_step_1d<SYS, N, GLL, false, IMEX, false, 64>, 64, 0) != cudaSuccess ||
+            &o.resident[0], k_step_1d<SYS, N, GLL, false, IMEX, false, 64>, 64, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &resident[1], k_step_1d<SYS, N, GLL, false, IMEX, false, 96>, 96, 0) != cudaSuccess ||
+            &o.resident[1], k_step_1d<SYS, N, GLL, false, IMEX, false, 96>, 96, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &resident[2], k_step_1d<SYS, N, GLL, false, IMEX, false, 128>, 128, 0) != cudaSuccess)
-      return (int)cudaGetLastError();
-    sms = n > 0 ? n : 1;
-  }
-  switch (L.tile_threads > 0 ? L.tile_threads : pick_tile_block(L.E, sms, resident)) {
+            &o.resident[2], k_step_1d<SYS, N, GLL, false, IMEX, false, 128>, 128, 0) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      o.sms = 0;
+    }
+    return o;
+  }();
+  if (L.tile_threads <= 0 && occ.sms <= 0) return launch_step_block<SYS, N, GLL, IMEX, 128>(L, s);
+  switch (L.tile_threads > 0 ? L.tile_threads : pick_tile_block(L.E, occ.sms, occ.resident)) {
     case 64: return launch_step_block<SYS, N, GLL, IMEX, 64>(L, s);
     case 96: return launch_step_block<SYS, N, GLL, IMEX, 96>(L, s);
   }
