@@ -309,7 +309,7 @@ crkfr_status crkfr_limiter_halo_buffers(crkfr_ctx* ctx, int32_t kind, double** s
 /* Adjoint of the step of Sec. 3, Eq. crkfr.non.cons.final (the paper has
  * no adjoint; it is this library's differentiation path).
  * Adjoint of one 2D shallow-water step with fixed dt > 0 (standard form,
- * GL nodes, no source term, context not in subdomain mode; otherwise
+ * GL nodes, no source term, context not in subdomain mode (slabs: the phased form below); otherwise
  * CRKFR_ERR_UNSUPPORTED or CRKFR_ERR_STATE).  With u^{n+1} = S(u^n; b) the step of crkfr_step
  * and a scalar J: given ubar1 = dJ/du^{n+1} (device, state layout), writes
  * ubar0 = (dS/du^n)^T ubar1 and adds (dS/db)^T ubar1 to bbar (device,
@@ -322,6 +322,30 @@ crkfr_status crkfr_limiter_halo_buffers(crkfr_ctx* ctx, int32_t kind, double** s
  * first call. */
 crkfr_status crkfr_step_adjoint(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
                                 double* ubar0_dev, double* bbar_dev, double dt, void* stream);
+
+/* The same adjoint step on a 2D slab (crkfr_set_subdomain; the contexts
+ * crkfr_step_adjoint takes otherwise), in phases.  The slab computes the face
+ * adjoints of both its boundary faces itself, so a step is:
+ * crkfr_adjoint_local (the forward traces of u^n, as crkfr_step_local writes
+ * them, and the y-correction sums of ubar1 the neighbouring slabs need);
+ * exchange of the traces (crkfr_halo_buffers) and of the sums
+ * (crkfr_adjoint_halo_buffers: send_bottom the sums of the slab's bottom
+ * row's columns with g_L', which the slab below stores as its recv_top;
+ * send_top those of its top row with g_R', the slab above's recv_bottom;
+ * count = 3 Ex (N+1) doubles each, context-owned, valid until the next
+ * crkfr_set_mesh, available after the first crkfr_adjoint_local);
+ * crkfr_adjoint_faces (writes ubar0 of the slab's elements and adds the
+ * gradient of their bathymetry to bbar, [Ey_local][Ex][n][n]: the halo rows
+ * of the coefficient field get none here, their own slab adds it).  Equal
+ * bit for bit to crkfr_step_adjoint on the whole mesh, row for row.  Both
+ * phases return CRKFR_ERR_STATE on a context that is not a 2D slab. */
+crkfr_status crkfr_adjoint_local(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
+                                 double dt, void* stream);
+crkfr_status crkfr_adjoint_halo_buffers(crkfr_ctx* ctx, double** send_bottom, double** send_top,
+                                        double** recv_bottom, double** recv_top,
+                                        int64_t* count);
+crkfr_status crkfr_adjoint_faces(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
+                                 double* ubar0_dev, double* bbar_dev, double dt, void* stream);
 
 /* Recorded steps for the adjoint of Sec. 3, Eq. crkfr.non.cons.final (the
  * paper has no adjoint; this is this library's differentiation path).  A

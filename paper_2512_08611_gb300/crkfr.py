@@ -85,6 +85,10 @@ SIGNATURES = {
                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _PI64]),
     "crkfr_step_faces": (_I32, [_P, _P, _P]),
     "crkfr_step_adjoint": (_I32, [_P, _P, _P, _P, _P, _D, _P]),
+    "crkfr_adjoint_local": (_I32, [_P, _P, _P, _D, _P]),
+    "crkfr_adjoint_halo_buffers": (_I32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                          ctypes.POINTER(_P), ctypes.POINTER(_P), _PI64]),
+    "crkfr_adjoint_faces": (_I32, [_P, _P, _P, _P, _P, _D, _P]),
     "crkfr_record_size": (_I32, [_P, _PI64]),
     "crkfr_step_record": (_I32, [_P, _P, _D, _P, _I32, _P]),
     "crkfr_step_adjoint_recorded": (_I32, [_P, _P, _P, _P, _P, _P, _D, _P]),
@@ -413,6 +417,40 @@ class Solver:
                                           u_out.ctypes.data_as(ctypes.c_void_p), float(dt),
                                           int(nsteps), _stream()))
         return u_out
+
+    def adjoint_local(self, u, ubar1, dt):
+        """2D slab, first phase of the adjoint step: forward traces of u and
+        the correction sums of ubar1 the neighbouring slabs need."""
+        self._check(lib().crkfr_adjoint_local(self.h, self._dev(u, self.shape),
+                                              self._dev(ubar1, self.shape), float(dt), _stream()))
+
+    def adjoint_halo_buffers(self):
+        """2D slab: (send_bottom, send_top, recv_bottom, recv_top) of the
+        adjoint's correction sums (after the first adjoint_local)."""
+        import torch
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        cnt = ctypes.c_int64()
+        self._check(lib().crkfr_adjoint_halo_buffers(self.h, *[ctypes.byref(p) for p in ptrs],
+                                                     ctypes.byref(cnt)))
+        return tuple(torch.as_tensor(_DeviceBlock(p.value, cnt.value), device="cuda")
+                     for p in ptrs)
+
+    def adjoint_faces(self, u, ubar1, dt, ubar0=None, bbar=None):
+        """2D slab, second phase (after both exchanges): ubar0 of the slab
+        and its bathymetry gradient added to bbar.  Returns (ubar0, bbar)."""
+        import torch
+        if ubar0 is None:
+            ubar0 = torch.empty_like(ubar1)
+        if bbar is None:
+            bbar = torch.zeros((self.n_elem[1], self.n_elem[0], self.n, self.n),
+                               dtype=torch.float64, device=u.device)
+        self._check(lib().crkfr_adjoint_faces(self.h, self._dev(u, self.shape),
+                                              self._dev(ubar1, self.shape),
+                                              self._dev(ubar0, self.shape),
+                                              self._dev(bbar, (self.n_elem[1], self.n_elem[0],
+                                                               self.n, self.n)),
+                                              float(dt), _stream()))
+        return ubar0, bbar
 
     def step_adjoint(self, u, ubar1, dt, ubar0=None, bbar=None):
         """ubar0 = (dS/du)^T ubar1; bbar += (dS/db)^T ubar1 for one 2D step of

@@ -51,6 +51,8 @@ struct crkfr_ctx {
   double* d_araw_halo = nullptr;  // 2D slab with the limiter: the neighbours' raw indicator,
                                   // rows -2, -1 (below) and Ey, Ey + 1 (above), [4][Ex]
   double* d_alpha_halo = nullptr; // 2D slab with the limiter: smoothed rows -1, Ey, [2][Ex]
+  double* d_adj_send = nullptr;   // 2D slab adjoint: y-correction sums of ubar1 for the
+  double* d_adj_recv = nullptr;   // neighbours / from them, [2][3][Ex][n] each
   double sub_dt = 0.0;            // 1D subdomain: dt of the step between local and faces
   int limit_mode = CRKFR_LIMITER_NONE;
   int tile_1d = 0;                // crkfr_set_tile_1d
@@ -119,7 +121,10 @@ void free_buffers(crkfr_ctx* c) {
   cudaFree(c->d_send);
   cudaFree(c->d_araw_halo);
   cudaFree(c->d_alpha_halo);
+  cudaFree(c->d_adj_send);
+  cudaFree(c->d_adj_recv);
   c->d_ghost = c->d_send = c->d_araw_halo = c->d_alpha_halo = nullptr;
+  c->d_adj_send = c->d_adj_recv = nullptr;
   c->d_cnode = c->d_alpha_raw = c->d_alpha = c->d_ulo = c->d_lx = c->d_ly = nullptr;
   c->d_atrx = c->d_atry = c->d_gbar = nullptr;
   c->d_snode = c->d_sface = c->d_work = c->d_trx = c->d_try = c->d_stage = nullptr;
@@ -1216,7 +1221,7 @@ crkfr_status crkfr_step_faces(crkfr_ctx* c, double* u, void* stream) {
 namespace {
 
 // The contexts the adjoint (and the recorded step) support.
-crkfr_status adjoint_context(crkfr_ctx* c) {
+crkfr_status adjoint_context(crkfr_ctx* c, bool slab = false) {
   crkfr_status st = ready(c);
   if (st != CRKFR_OK) return st;
   if (c->dim != 2 || c->cfg.system != CRKFR_SYS_SWE_2D)
@@ -1225,7 +1230,9 @@ crkfr_status adjoint_context(crkfr_ctx* c) {
   if (c->cfg.nodes != CRKFR_NODES_GL) return fail(c, CRKFR_ERR_UNSUPPORTED, "GL nodes only");
   if (c->cfg.source != CRKFR_SRC_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step has no source term");
-  if (c->subdomain) return fail(c, CRKFR_ERR_STATE, "no adjoint in subdomain mode");
+  if (c->subdomain != slab)
+    return fail(c, CRKFR_ERR_STATE, slab ? "the phased adjoint is a step of a 2D slab"
+                                         : "subdomain: use crkfr_adjoint_local / faces");
   if (c->limit_mode != CRKFR_LIMITER_NONE)
     return fail(c, CRKFR_ERR_UNSUPPORTED, "the adjoint step has no limiter");
   return CRKFR_OK;
@@ -1262,6 +1269,10 @@ crkfr_status launch_adjoint(crkfr_ctx* c, const double* u, const double* ubar1, 
   A.atry = c->d_atry;
   A.gbar = c->d_gbar;
   A.stages = stages;
+  if (c->subdomain) {
+    A.sums_below = c->d_adj_recv;
+    A.sums_above = c->d_adj_recv + 3 * c->Ex * c->basis.n;
+  }
   A.tab = c->tab;
   int e = timed(c, CRKFR_KERNEL_ADJOINT_2D, s, [&] { return launch_adjoint_2d(A, s); });
   if (e) return cuda_fail(c, e, "2D adjoint kernels");
@@ -1281,7 +1292,7 @@ crkfr_status adjoint_args(crkfr_ctx* c, const double* u, const double* ubar1, do
     const size_t tr = (size_t)7 * 2 * Ne * n;
     if (cudaMalloc(&c->d_atrx, sizeof(double) * tr) != cudaSuccess ||
         cudaMalloc(&c->d_atry, sizeof(double) * tr) != cudaSuccess ||
-        cudaMalloc(&c->d_gbar, sizeof(double) * 2 * Ne * n) != cudaSuccess) {
+        cudaMalloc(&c->d_gbar, sizeof(double) * (2 * Ne + c->Ex) * n) != cudaSuccess) {
       cudaGetLastError();
       return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
     }
@@ -1311,6 +1322,71 @@ crkfr_status crkfr_step_adjoint(crkfr_ctx* c, const double* u, const double* uba
   if (e) return cuda_fail(c, e, "2D local kernel");
   c->launches += 1;
   return launch_adjoint(c, u, ubar1, ubar0, bbar, dt, c->d_trx, c->d_try, nullptr, s);
+}
+
+// The adjoint step of a 2D slab in phases.  Each slab recomputes the face
+// adjoints of both its boundary faces (the slab below has the same face at
+// its top), so what crosses a slab boundary is the forward traces (the
+// exchange of crkfr_halo_buffers) and the y-correction sums of ubar1 of the
+// rows next to the slab; the bathymetry gradient of a slab's elements stays
+// with that slab.
+crkfr_status crkfr_adjoint_local(crkfr_ctx* c, const double* u, const double* ubar1, double dt,
+                                 void* stream) {
+  crkfr_status st = adjoint_context(c, true);
+  if (st != CRKFR_OK) return st;
+  if (!u || !ubar1) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
+  const int64_t sums = (int64_t)2 * 3 * c->Ex * c->basis.n;
+  if (!c->d_adj_send) {
+    if (cudaMalloc(&c->d_adj_send, sizeof(double) * sums) != cudaSuccess ||
+        cudaMalloc(&c->d_adj_recv, sizeof(double) * sums) != cudaSuccess) {
+      cudaFree(c->d_adj_send);
+      cudaFree(c->d_adj_recv);
+      c->d_adj_send = c->d_adj_recv = nullptr;
+      cudaGetLastError();
+      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // forward traces of u^n (the local kernel in its residual form) and the
+  // sums the neighbouring slabs need
+  StepCtl ctl{};
+  ctl.dt_fixed = dt;
+  ctl.residual = 1;
+  Launch2D L = make2d(c);
+  L.ctl = ctl;
+  L.u_in = u;
+  int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d(L, s); });
+  if (e) return cuda_fail(c, e, "2D local kernel");
+  e = launch_adjoint_sums_2d(c->cfg.degree, c->Ex, c->Ey, ubar1, c->tab, c->d_adj_send, s);
+  if (e) return cuda_fail(c, e, "adjoint sums kernel");
+  c->launches += 2;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_adjoint_halo_buffers(crkfr_ctx* c, double** send_bottom, double** send_top,
+                                        double** recv_bottom, double** recv_top,
+                                        int64_t* count) {
+  if (!c) return CRKFR_ERR_ARG;
+  if (c->dim != 2 || !c->subdomain) return fail(c, CRKFR_ERR_STATE, "not a 2D slab");
+  if (!c->d_adj_send) return fail(c, CRKFR_ERR_STATE, "crkfr_adjoint_local first");
+  const int64_t per = 3 * c->Ex * c->basis.n;
+  if (send_bottom) *send_bottom = c->d_adj_send;
+  if (send_top) *send_top = c->d_adj_send + per;
+  if (recv_bottom) *recv_bottom = c->d_adj_recv;
+  if (recv_top) *recv_top = c->d_adj_recv + per;
+  if (count) *count = per;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_adjoint_faces(crkfr_ctx* c, const double* u, const double* ubar1,
+                                 double* ubar0, double* bbar, double dt, void* stream) {
+  crkfr_status st = adjoint_context(c, true);
+  if (st == CRKFR_OK) st = adjoint_args(c, u, ubar1, ubar0, bbar, dt);
+  if (st != CRKFR_OK) return st;
+  if (!c->d_adj_send) return fail(c, CRKFR_ERR_STATE, "crkfr_adjoint_local first");
+  return launch_adjoint(c, u, ubar1, ubar0, bbar, dt, c->d_trx, c->d_try, nullptr,
+                        (cudaStream_t)stream);
 }
 
 crkfr_status crkfr_record_size(const crkfr_ctx* c, int64_t* count) {

@@ -269,8 +269,19 @@ struct Launch2DAdj {
   // stage values 1..S-1 of the step from u^n, [S-1][3][Ey][Ex][n][n], as the
   // forward local kernel stored them (crkfr_step_record); null: recompute
   const double* stages;
+  // slab of a larger mesh (null: periodic in y): the y-correction sums of
+  // ubar1 of the element rows next to the slab, [3][Ex][n] each: below, the
+  // sums of its top row's columns with g_R'; above, of its bottom row's
+  // columns with g_L' (the face adjoint then covers the slab's Ey + 1 rows of
+  // y faces, its top face included, and gbar holds Ey + 1 rows of y faces)
+  const double* sums_below;
+  const double* sums_above;
   Tables tab;
 };
+// The sums the neighbouring slabs need, [2][3][Ex][n]: the slab's bottom row
+// with g_L' (for the slab below), its top row with g_R' (for the slab above).
+int launch_adjoint_sums_2d(int N, int64_t Ex, int64_t Ey, const double* ubar1, const Tables& T,
+                           double* send, void* stream);
 // the forward local kernel (standard form, GL or GLL, no source) that also
 // stores the inner stage values into L.stages (kernels_adj2d.cu)
 int launch_local_2d_stages(const Launch2D& L, void* stream);

@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) k_face_adj_2d(const Launch2DAdj A) {
   const Tables& T = A.tab;
   const int64_t Ex = A.Ex, Ey = A.Ey, Ne = Ex * Ey, ts = Ne * n, plane = Ex * n;
   const double dtb0 = A.dt * tab_b(N, 0);
-  const int64_t total = 2 * Ne * n;
+  const bool slab = A.sums_below != nullptr;
+  const int64_t total = Ne * n + (slab ? Ey + 1 : Ey) * plane;   // x faces, y faces
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
        f += (int64_t)gridDim.x * blockDim.x) {
     const bool xdir = f < Ne * n;
@@ -137,17 +138,27 @@ __global__ void __launch_bounds__(256) k_face_adj_2d(const Launch2DAdj A) {
       }
       A.gbar[e * n + k] = gbar;
     } else {
-      const int64_t rowm = ey == 0 ? Ey - 1 : ey - 1;
-      const int64_t em = rowm * Ex + ex;
+      // the face below element row ey (on a slab ey = 0 .. Ey: rows -1 and
+      // Ey are the neighbouring slabs', whose sums came with the exchange)
+      const int64_t rowm = slab ? ey - 1 : (ey == 0 ? Ey - 1 : ey - 1);
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        const double* um = A.ubar1 + (v * Ne + em) * nn + k;   // column k of the lower element
-        const double* up = A.ubar1 + (v * Ne + e) * nn + k;
-        double sm = um[0] * T.gRy[0], sp = up[0] * T.gLy[0];
+        double sm, sp;
+        if (rowm >= 0) {
+          const double* um = A.ubar1 + (v * Ne + rowm * Ex + ex) * nn + k;   // column k, lower
+          sm = um[0] * T.gRy[0];
 #pragma unroll
-        for (int q = 1; q < n; ++q) {
-          sm = fma(um[q * n], T.gRy[q], sm);
-          sp = fma(up[q * n], T.gLy[q], sp);
+          for (int q = 1; q < n; ++q) sm = fma(um[q * n], T.gRy[q], sm);
+        } else {
+          sm = A.sums_below[(v * Ex + ex) * n + k];
+        }
+        if (ey < Ey) {
+          const double* up = A.ubar1 + (v * Ne + ey * Ex + ex) * nn + k;     // column k, upper
+          sp = up[0] * T.gLy[0];
+#pragma unroll
+          for (int q = 1; q < n; ++q) sp = fma(up[q * n], T.gLy[q], sp);
+        } else {
+          sp = A.sums_above[(v * Ex + ex) * n + k];
         }
         Tbm[v] = -dtb0 * sm;
         Tbp[v] = -dtb0 * sp;
@@ -160,11 +171,12 @@ __global__ void __launch_bounds__(256) k_face_adj_2d(const Launch2DAdj A) {
       }
       face_terms_adj(tm, tp, 2, A.sface[Ne * n + ey * plane + ex * n + k], T.sqrt_gravity, Tbm,
                      Tbp, am, ap, &gbar);
-      // adjoint y traces: [row][side][field][ex][node], no halo rows
+      // adjoint y traces: [row][side][field][ex][node], no halo rows (the
+      // sides of a neighbouring slab's elements are that slab's to compute)
 #pragma unroll
       for (int fi = 0; fi < kTr; ++fi) {
-        A.atry[((rowm * 2 + 1) * kTr + fi) * plane + ex * n + k] = am[fi];
-        A.atry[((ey * 2 + 0) * kTr + fi) * plane + ex * n + k] = ap[fi];
+        if (rowm >= 0) A.atry[((rowm * 2 + 1) * kTr + fi) * plane + ex * n + k] = am[fi];
+        if (ey < Ey) A.atry[((ey * 2 + 0) * kTr + fi) * plane + ex * n + k] = ap[fi];
       }
       A.gbar[Ne * n + ey * plane + ex * n + k] = gbar;
     }
@@ -465,13 +477,15 @@ __global__ void __launch_bounds__(kBlockAdj) k_local_adj_2d(const Launch2DAdj A)
   // y faces of each column
   {
     const int64_t exr = ex == Ex - 1 ? 0 : ex + 1;
-    const int64_t rowt = ey + 1;   // jump row of the top face (row Ey is the periodic top)
+    // jump row of the top face: row Ey is the periodic top, or on a slab the
+    // top face itself
+    const int64_t rowt = (ey + 1 == Ey && !A.sums_below) ? 0 : ey + 1;
     const double gl = A.gbar[ge * n + q];
     const double gr = A.gbar[(ey * Ex + exr) * n + q];
 #pragma unroll
     for (int p = 0; p < n; ++p) {
       const double gb = A.gbar[Ne * n + ey * plane + ex * n + p];
-      const double gt = A.gbar[Ne * n + (rowt == Ey ? 0 : rowt) * plane + ex * n + p];
+      const double gt = A.gbar[Ne * n + rowt * plane + ex * n + p];
       double s = fma(T.l0[p], gl, -T.l1[p] * gr);
       s = fma(T.l0[q], gb, s);
       s = fma(-T.l1[q], gt, s);
@@ -506,13 +520,44 @@ int launch_local_stages_t(const Launch2D& L, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+// The y-correction sums of ubar1 a neighbouring slab's face adjoint needs:
+// side 0 the slab's bottom row with g_L' (for the slab below), side 1 its
+// top row with g_R' (for the slab above); send [2][3][Ex][n].  The same
+// products in the same order as the face adjoint kernel forms them.
+__global__ void k_adjoint_sums_2d(int n, int64_t Ex, int64_t Ey, const double* __restrict__ ubar1,
+                                  const Tables T, double* __restrict__ send) {
+  const int64_t per = 3 * Ex * n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * per) return;
+  const int side = (int)(i / per);
+  const int64_t j = i - side * per;
+  const int v = (int)(j / (Ex * n));
+  const int64_t ex = (j / n) % Ex;
+  const int k = (int)(j % n);
+  const int64_t Ne = Ex * Ey, nn = (int64_t)n * n;
+  const int64_t row = side ? Ey - 1 : 0;
+  const double* u = ubar1 + (v * Ne + row * Ex + ex) * nn + k;
+  const double* g = side ? T.gRy : T.gLy;
+  double sum = u[0] * g[0];
+  for (int q = 1; q < n; ++q) sum = fma(u[q * n], g[q], sum);
+  send[i] = sum;
+}
+
 }  // namespace
+
+int launch_adjoint_sums_2d(int N, int64_t Ex, int64_t Ey, const double* ubar1, const Tables& T,
+                           double* send, void* stream) {
+  const int64_t total = 2 * 3 * Ex * (N + 1);
+  k_adjoint_sums_2d<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      N + 1, Ex, Ey, ubar1, T, send);
+  return (int)cudaGetLastError();
+}
 
 int launch_adjoint_2d(const Launch2DAdj& A, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t Ne = A.Ex * A.Ey;
   const int n = A.N + 1;
-  const int64_t faces = 2 * Ne * n;
+  const int64_t faces = Ne * n + (A.sums_below ? A.Ey + 1 : A.Ey) * A.Ex * n;
   const unsigned fblocks = (unsigned)std::min<int64_t>((faces + 255) / 256, 152 * 16);
   const int per_block = kWarpsAdj * (32 / n);
   const unsigned lblocks = (unsigned)((Ne + per_block - 1) / per_block);

@@ -119,6 +119,21 @@ class SlabStepper:
         return u
 
 
+def slab_adjoint(stepper, u, ubar1, dt, ubar0=None, bbar=None):
+    """Adjoint of one step of a 2D slab (crkfr_adjoint_local, the exchange
+    of the forward traces and of ubar1's correction sums, crkfr_adjoint_faces):
+    ubar0 of the slab's elements and their bathymetry gradient added to bbar.
+    ``stepper`` is the slab's SlabStepper (its trace buffers and group)."""
+    s = stepper.s
+    s.adjoint_local(u, ubar1, dt)
+    halo_exchange(stepper.send_bottom, stepper.send_top, stepper.recv_bottom, stepper.recv_top,
+                  stepper.group)
+    if getattr(stepper, "_adj", None) is None:
+        stepper._adj = s.adjoint_halo_buffers()
+    halo_exchange(*stepper._adj, stepper.group)
+    return s.adjoint_faces(u, ubar1, dt, ubar0, bbar)
+
+
 def slab_rows(global_rows, rank, world):
     """(first row, row count) of a rank's slab: contiguous, sizes differ by at
     most one."""

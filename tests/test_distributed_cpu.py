@@ -329,6 +329,68 @@ def test_split_limited_1d_step_equals_single_domain(world):
     assert max(out[r][2] for r in range(world)) > 0.1
 
 
+def _worker_adjoint(rank, world, port, out):
+    """The adjoint of a slab step (the oracle's exact discrete adjoint:
+    autograd through its step) needs one element row beyond the slab, of u
+    and of ubar1: the outputs next to the slab depend on the slab's rows only
+    through the face between them, which the two rows fix.  Ranks exchange
+    one boundary row of u and of ubar1, differentiate the oracle step of their
+    slab extended by those rows, and keep their own rows of ubar0 and of the
+    bathymetry gradient, which equal the whole mesh's (the library exchanges
+    the same: the forward traces and the correction sums of that row)."""
+    from oracle.crkfr import Scheme2D
+    from oracle.systems import ShallowWater2D
+    from paper_2512_08611_gb300.distributed import halo_exchange, slab_rows
+    _init(rank, world, port)
+    N, Ey, Ex = 2, 9, 5
+    u, b, dx, dy = _case(Ey, Ex, N)
+    sch = Scheme2D(ShallowWater2D(9.81), N, dx, dy)
+    dt = 0.5 * sch.compute_dt(u, b, 0.2, 0.5)
+    w = np.random.default_rng(11).standard_normal(u.shape)
+    first, count = slab_rows(Ey, rank, world)
+    own = slice(first, first + count)
+
+    def swap(a, depth):
+        sb = torch.from_numpy(np.ascontiguousarray(a[:, :depth]).ravel())
+        st = torch.from_numpy(np.ascontiguousarray(a[:, -depth:]).ravel())
+        rb, rt = torch.empty_like(st), torch.empty_like(sb)
+        halo_exchange(sb, st, rb, rt)
+        shape = (a.shape[0], depth) + a.shape[2:]
+        return rb.numpy().reshape(shape), rt.numpy().reshape(shape)
+    ub_, ut_ = swap(u[:, own], 1)
+    wb_, wt_ = swap(w[:, own], 1)
+    u_ext = np.concatenate([ub_, u[:, own], ut_], axis=1)
+    w_ext = np.concatenate([wb_, w[:, own], wt_], axis=1)
+    b_ext = b[[(first + k) % Ey for k in range(-1, count + 1)]]
+    uu = torch.tensor(u_ext, requires_grad=True)
+    bb = torch.tensor(b_ext, requires_grad=True)
+    (sch.step(uu, bb, dt) * torch.tensor(w_ext)).sum().backward()
+    ug = torch.tensor(u, requires_grad=True)
+    bg = torch.tensor(b, requires_grad=True)
+    (sch.step(ug, bg, dt) * torch.tensor(w)).sum().backward()
+    du = np.abs(uu.grad.numpy()[:, 1:-1] - ug.grad.numpy()[:, own]).max()
+    db = np.abs(bb.grad.numpy()[1:-1] - bg.grad.numpy()[own]).max()
+    scale = max(np.abs(ug.grad.numpy()).max(), np.abs(bg.grad.numpy()).max())
+    out[rank] = (bool(du <= 1e-14 * scale and db <= 1e-14 * scale), float(du), float(db))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_adjoint_equals_single_domain(world):
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = free_port()
+    procs = [ctx.Process(target=_worker_adjoint, args=(r, world, port, out))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert out[r][0], out[r]
+
+
 def test_slab_rows_cover_the_mesh():
     from paper_2512_08611_gb300.distributed import slab_rows
     for G in (1, 7, 1024):

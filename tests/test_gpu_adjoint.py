@@ -249,3 +249,70 @@ def test_gradient_config5_against_finite_differences():
     directions."""
     crk = load()
     _assert_gradient(_gradient_check(crk, 3, 256, 200, 20, 32))
+
+
+def adjoint_slab(crk, N, Ex, Ey, b, first, count, L=100.0):
+    dy = L / Ey
+    s = crk.Solver("swe2d", N, gravity=G, cfl_number=golden_cfl(N, "gl"))
+    s.set_mesh([Ex, count], [0.0, first * dy], [L, (first + count) * dy])
+    s.set_subdomain(True)
+    rows = [(first - 1) % Ey] + list(range(first, first + count)) + [(first + count) % Ey]
+    s.set_coefficients(to_dev(np.ascontiguousarray(b[rows])))
+    return s
+
+
+@pytest.mark.parametrize("N,parts", [(3, [(0, 7), (7, 9)]), (2, [(0, 1), (1, 10), (11, 5)]),
+                                     (1, [(0, 16)])])
+def test_slab_adjoint_equals_whole_mesh_adjoint(N, parts):
+    """The adjoint step on slabs (crkfr_adjoint_local, exchange of the
+    forward traces and of ubar1's correction sums, crkfr_adjoint_faces),
+    with a one-row slab and a slab that is its own neighbour among the
+    cases: ubar0 and the bathymetry gradient of every slab equal the rows
+    of crkfr_step_adjoint on the whole mesh bit for bit."""
+    crk = load()
+    Ex, Ey = 16, 16
+    u, b, dx, dy = case(N, Ex, Ey)
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal(u.shape)
+    m = solver(crk, N, Ex, Ey, b)
+    dt = 0.5 * m.compute_dt(to_dev(u))
+    ub_want, bb_want = m.step_adjoint(to_dev(u), to_dev(w), dt)
+    slabs = [adjoint_slab(crk, N, Ex, Ey, b, f, c) for f, c in parts]
+    us = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    ws = [to_dev(np.ascontiguousarray(w[:, f:f + c])) for f, c in parts]
+    for s, x, y in zip(slabs, us, ws):
+        s.adjoint_local(x, y, dt)
+    k_ = len(parts)
+    for bufs in ([s.halo_buffers() for s in slabs], [s.adjoint_halo_buffers() for s in slabs]):
+        for k in range(k_):
+            bufs[k][2].copy_(bufs[(k - 1) % k_][1])   # recv_bottom <- send_top of the slab below
+            bufs[k][3].copy_(bufs[(k + 1) % k_][0])   # recv_top <- send_bottom of the slab above
+    outs = [s.adjoint_faces(x, y, dt) for s, x, y in zip(slabs, us, ws)]
+    ub = np.concatenate([to_host(o[0]) for o in outs], axis=1)
+    bb = np.concatenate([to_host(o[1]) for o in outs], axis=0)
+    assert np.array_equal(ub, to_host(ub_want)), rel_l2(ub, to_host(ub_want))
+    assert np.array_equal(bb, to_host(bb_want)), rel_l2(bb, to_host(bb_want))
+
+
+def test_slab_adjoint_through_the_distributed_helper_and_errors():
+    from paper_2512_08611_gb300.distributed import SlabStepper, slab_adjoint
+    crk = load()
+    N, Ex, Ey = 3, 12, 8
+    u, b, dx, dy = case(N, Ex, Ey)
+    w = np.random.default_rng(2).standard_normal(u.shape)
+    m = solver(crk, N, Ex, Ey, b)
+    dt = 0.5 * m.compute_dt(to_dev(u))
+    ub_want, bb_want = m.step_adjoint(to_dev(u), to_dev(w), dt)
+    s = adjoint_slab(crk, N, Ex, Ey, b, 0, Ey)
+    with pytest.raises(crk.CrkfrError) as e:
+        s.adjoint_halo_buffers()          # before the first adjoint_local
+    assert e.value.status == -6
+    with pytest.raises(crk.CrkfrError) as e:
+        s.step_adjoint(to_dev(u), to_dev(w), dt)
+    assert e.value.status == -6
+    with pytest.raises(crk.CrkfrError) as e:
+        m.adjoint_local(to_dev(u), to_dev(w), dt)
+    assert e.value.status == -6
+    ub, bb = slab_adjoint(SlabStepper(s), to_dev(u), to_dev(w), dt)
+    assert np.array_equal(to_host(ub), to_host(ub_want))
+    assert np.array_equal(to_host(bb), to_host(bb_want))
