@@ -490,6 +490,9 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
       ctl.slot_write = (int)((c->nstep + 1) % 3);
       ctl.slot_reset = (int)((c->nstep + 2) % 3);
       ctl.tslot = (int)(c->nstep % 2);
+      // (the last step's rate would go unread: every call starts from the
+      // rate of its input)
+      ctl.want_rate = cfl_mode && k + 1 < nsteps ? 1 : 0;
       L.ctl = ctl;
       L.u_in = bufs[cur];
       L.u_out = bufs[cur ^ 1];
@@ -513,6 +516,7 @@ crkfr_status run_steps(crkfr_ctx* c, double* u, double dt, int64_t nsteps, doubl
       ctl.slot_write = (int)((c->nstep + 1) % 3);
       ctl.slot_reset = (int)((c->nstep + 2) % 3);
       ctl.tslot = (int)(c->nstep % 2);
+      ctl.want_rate = cfl_mode && k + 1 < nsteps ? 1 : 0;
       L.ctl = ctl;
       L.u_in = u;
       L.u_out = u;
