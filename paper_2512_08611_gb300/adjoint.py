@@ -17,6 +17,8 @@ held at a time) and the adjoint steps read them back
 ``BathymetryToState`` is a torch.autograd.Function, so any differentiable
 torch expression of u_T and b can serve as J; ``surface_misfit`` is the
 L2 misfit of the free surface h + b at the final time.
+``SlabBathymetryToState`` is the same for one rank's slab of a mesh split
+over ranks (the slab adjoint step, states recomputed, not recorded).
 """
 import torch
 
@@ -91,6 +93,61 @@ class BathymetryToState(torch.autograd.Function):
         # initial condition h0 = eta0 - b
         bbar -= ubar[0]
         return bbar, None, None, None, None, None, None
+
+
+class SlabBathymetryToState(torch.autograd.Function):
+    """u_T(b) of one rank's slab of a 2D mesh split into slabs (a
+    distributed.SlabStepper over a Solver in subdomain mode, fixed dt): b and
+    eta0 are the slab's own rows, [Ey_local][Ex][n][n].  Every rank calls
+    forward and backward together (both exchange with the neighbouring
+    slabs).  The forward pass gets the element rows of b next to the slab
+    from the neighbours; the backward pass runs the slab adjoint step
+    (distributed.slab_adjoint) over states recomputed from checkpoints, and
+    the gradient it returns is complete for the slab's own rows: the
+    gradient of a neighbour's bathymetry at a shared face is formed by that
+    neighbour."""
+
+    @staticmethod
+    def forward(ctx, b, stepper, eta0, dt, nsteps, every):
+        from .distributed import halo_exchange
+        bd = b.detach().contiguous()
+        below, above = torch.empty_like(bd[-1:]), torch.empty_like(bd[:1])
+        halo_exchange(bd[:1].contiguous(), bd[-1:].contiguous(), below, above, stepper.group)
+        coef = torch.cat([below, bd, above]).contiguous()
+        stepper.s.set_coefficients(coef)
+        u = initial_state(eta0, bd).contiguous()
+        checkpoints = [u.clone()]
+        done = 0
+        while done < nsteps:
+            k = min(every, nsteps - done)
+            stepper.step(u, dt, k)
+            done += k
+            if done < nsteps:
+                checkpoints.append(u.clone())
+        ctx.stepper, ctx.dt, ctx.nsteps, ctx.every = stepper, dt, nsteps, every
+        ctx.checkpoints, ctx.coef, ctx.b = checkpoints, coef, bd
+        return u
+
+    @staticmethod
+    def backward(ctx, ubar):
+        from .distributed import slab_adjoint
+        st, dt, nsteps, every = ctx.stepper, ctx.dt, ctx.nsteps, ctx.every
+        st.s.set_coefficients(ctx.coef)
+        ubar = ubar.contiguous().clone()
+        bbar = torch.zeros_like(ctx.b)
+        other = torch.empty_like(ubar)
+        for seg, start in reversed(list(enumerate(range(0, nsteps, every)))):
+            k = min(every, nsteps - start)
+            states = [ctx.checkpoints[seg].clone()]
+            for _ in range(k - 1):
+                x = states[-1].clone()
+                st.step(x, dt, 1)
+                states.append(x)
+            for x in reversed(states):
+                slab_adjoint(st, x, ubar, dt, ubar0=other, bbar=bbar)
+                ubar, other = other, ubar
+        bbar -= ubar[0]
+        return bbar, None, None, None, None, None
 
 
 def surface_misfit(u, b, target, weights):

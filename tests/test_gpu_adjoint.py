@@ -316,3 +316,31 @@ def test_slab_adjoint_through_the_distributed_helper_and_errors():
     ub, bb = slab_adjoint(SlabStepper(s), to_dev(u), to_dev(w), dt)
     assert np.array_equal(to_host(ub), to_host(ub_want))
     assert np.array_equal(to_host(bb), to_host(bb_want))
+
+
+def test_slab_autograd_function_equals_whole_mesh():
+    """SlabBathymetryToState on a slab that is its own periodic neighbour
+    (one rank) gives the final state and the bathymetry gradient of a surface
+    misfit of BathymetryToState on the whole mesh, bit for bit."""
+    from paper_2512_08611_gb300.adjoint import (BathymetryToState, SlabBathymetryToState,
+                                                quadrature_weights, surface_misfit)
+    from paper_2512_08611_gb300.distributed import SlabStepper
+    crk = load()
+    N, Ex, Ey, nsteps, every = 3, 12, 10, 7, 3
+    _, b, dx, dy = case(N, Ex, Ey, flow=0.0)
+    x, y, _, _ = positions_2d(Basis(N), Ex, Ey, 100.0)
+    eta0 = to_dev(1.0 + 0.01 * SWE2DInput(seed=0, L=100.0).bump(x, y))
+    m = solver(crk, N, Ex, Ey, b)
+    dt = 0.5 * m.compute_dt(torch.stack([eta0 - to_dev(b), 0 * eta0, 0 * eta0]))
+    target = eta0.flip(0).contiguous()
+    W = quadrature_weights(m)
+    b1 = to_dev(b).requires_grad_(True)
+    u1 = BathymetryToState.apply(b1, m, eta0, dt, nsteps, every, False)
+    surface_misfit(u1, b1, target, W).backward()
+    s = adjoint_slab(crk, N, Ex, Ey, b, 0, Ey)
+    b2 = to_dev(b).requires_grad_(True)
+    u2 = SlabBathymetryToState.apply(b2, SlabStepper(s), eta0, dt, nsteps, every)
+    surface_misfit(u2, b2, target, W).backward()
+    assert torch.equal(u1.detach(), u2.detach())
+    assert torch.equal(b1.grad, b2.grad)
+    assert float(b1.grad.abs().max()) > 0.0
