@@ -236,9 +236,10 @@ def test_limiter_configuration_errors_2d(crk):
     assert e.value.status == -6
 
 
-def limited_slab(crk, system, N, Ex, Ey, c, first, count, mode, alpha, source=None, coef=0.0):
-    cfl = golden_cfl_imex(N, "gll") if source else golden_cfl(N, "gll")
-    s = crk.Solver(system, N, nodes="gll", gravity=G, cfl_safety=0.1, cfl_number=cfl,
+def limited_slab(crk, system, N, Ex, Ey, c, first, count, mode, alpha, source=None, coef=0.0,
+                 family="gll", cs=0.1):
+    cfl = golden_cfl_imex(N, family) if source else golden_cfl(N, family)
+    s = crk.Solver(system, N, nodes=family, gravity=G, cfl_safety=cs, cfl_number=cfl,
                    source=source, source_coef=coef)
     dy = 1.0 / Ey
     s.set_mesh([Ex, count], [0.0, first * dy], [1.0, (first + count) * dy])
@@ -302,6 +303,43 @@ def test_limited_slabs_equal_single_domain(crk, system, N, mode, alpha, source):
     if mode == "blend":
         # the dam (y in 0.30 .. 0.70) spans the slab boundaries at y = 5/16, 7/16
         assert np.max(a_want) > 0.5 and np.min(a_want) == 0.0
+
+
+@pytest.mark.parametrize("system,N,mode,alpha", [("swe2d", 3, "fixed", 0.4),
+                                                ("swe2d_wb", 2, "blend", 0.0),
+                                                ("swe2d", 4, "blend", 0.0)])
+def test_limited_slabs_gl_nodes(crk, system, N, mode, alpha):
+    """GL nodes (traces through l(0), l(1), Radau corrections at every node)
+    on the smooth flow over a varying bottom, split into slabs of 3 and 5
+    rows through SlabStepper-like phases: bit for bit the single domain
+    (dy = 1/8, so that every slab's bounds and 1/dy are exact)."""
+    Ex, Ey, steps = 9, 8, 3
+    u, b, dx, dy = flow(N, "gl", Ex, Ey)
+    m = solver(crk, system, N, "gl", Ex, Ey, b)
+    m.set_limiter(mode, alpha)
+    want = to_dev(u)
+    parts = [(0, 3), (3, 5)]
+    slabs = [limited_slab(crk, system, N, Ex, Ey, b, f, c, mode, alpha, family="gl", cs=0.5)
+             for f, c in parts]
+    states = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    traces = [s.halo_buffers() for s in slabs]
+    raw = [s.limiter_halo_buffers(0) for s in slabs]
+    face = [s.limiter_halo_buffers(1) for s in slabs]
+    for _ in range(steps):
+        dt = m.compute_dt(want)
+        m.step(want, dt, 1)
+        for s, x in zip(slabs, states):
+            s.step_indicator(x)
+        ring(raw)
+        for s, x in zip(slabs, states):
+            s.step_local(x, dt)
+        ring(traces)
+        ring(face)
+        for s, x in zip(slabs, states):
+            s.step_faces(x)
+    got = np.concatenate([to_host(x) for x in states], axis=1)
+    assert np.all(np.isfinite(got))
+    assert np.array_equal(got, to_host(want)), rel_l2(got, to_host(want))
 
 
 def test_single_limited_slab_through_the_stepper(crk):
