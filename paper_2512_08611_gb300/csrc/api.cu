@@ -1032,6 +1032,7 @@ crkfr_status crkfr_set_subdomain(crkfr_ctx* c, int32_t enable) {
       cudaGetLastError();
       return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
     }
+    CK(c, cudaMemset(c->d_ghost, 0, sizeof(double) * 2 * ghost_stride_1d(c->M, n)));
   }
   c->subdomain = enable != 0;
   c->coef_set = false;
@@ -1350,6 +1351,7 @@ crkfr_status crkfr_adjoint_local(crkfr_ctx* c, const double* u, const double* ub
       cudaGetLastError();
       return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
     }
+    CK(c, cudaMemset(c->d_adj_recv, 0, sizeof(double) * sums));
   }
   cudaStream_t s = (cudaStream_t)stream;
   // forward traces of u^n (the local kernel in its residual form) and the
