@@ -347,6 +347,34 @@ crkfr_status crkfr_adjoint_halo_buffers(crkfr_ctx* ctx, double** send_bottom, do
 crkfr_status crkfr_adjoint_faces(crkfr_ctx* ctx, const double* u_dev, const double* ubar1_dev,
                                  double* ubar0_dev, double* bbar_dev, double dt, void* stream);
 
+/* Recorded steps of a 2D slab (the slab form of crkfr_step_record and
+ * crkfr_step_adjoint_recorded; records of crkfr_record_size doubles).
+ * crkfr_step_local_record: the local phase of the step from u_dev with dt,
+ * writing the face traces and the inner stage values into the record
+ * (advance 1: a step, whose crkfr_step_faces_record follows; advance 0:
+ * the record of the state only, u_dev and the time unchanged); then the
+ * record's boundary blocks of y traces are exchanged with the neighbouring
+ * slabs (crkfr_record_halo_buffers: pointers into `record`, laid out and
+ * paired as those of crkfr_halo_buffers); crkfr_step_faces_record: the
+ * face phase reading the traces from the record, writing u_dev.  The
+ * adjoint of a recorded step: crkfr_adjoint_sums (the y-correction sums of
+ * ubar1, exchanged as after crkfr_adjoint_local), then
+ * crkfr_adjoint_faces_recorded, which reads the traces and stage values
+ * from the record.  Equal bit for bit to the unrecorded slab step and
+ * adjoint.  CRKFR_ERR_STATE on a context that is not a 2D slab. */
+crkfr_status crkfr_step_local_record(crkfr_ctx* ctx, const double* u_dev, double dt,
+                                     double* record, int32_t advance, void* stream);
+crkfr_status crkfr_record_halo_buffers(crkfr_ctx* ctx, double* record, double** send_bottom,
+                                       double** send_top, double** recv_bottom, double** recv_top,
+                                       int64_t* count);
+crkfr_status crkfr_step_faces_record(crkfr_ctx* ctx, double* u_dev, const double* record,
+                                     void* stream);
+crkfr_status crkfr_adjoint_sums(crkfr_ctx* ctx, const double* ubar1_dev, void* stream);
+crkfr_status crkfr_adjoint_faces_recorded(crkfr_ctx* ctx, const double* u_dev,
+                                          const double* record, const double* ubar1_dev,
+                                          double* ubar0_dev, double* bbar_dev, double dt,
+                                          void* stream);
+
 /* Recorded steps for the adjoint of Sec. 3, Eq. crkfr.non.cons.final (the
  * paper has no adjoint; this is this library's differentiation path).  A
  * reverse pass that recomputes a segment of forward steps from a checkpoint

@@ -18,7 +18,7 @@ held at a time) and the adjoint steps read them back
 torch expression of u_T and b can serve as J; ``surface_misfit`` is the
 L2 misfit of the free surface h + b at the final time.
 ``SlabBathymetryToState`` is the same for one rank's slab of a mesh split
-over ranks (the slab adjoint step, states recomputed, not recorded).
+over ranks (the slab adjoint step, recorded or recomputing).
 """
 import torch
 
@@ -102,13 +102,15 @@ class SlabBathymetryToState(torch.autograd.Function):
     forward and backward together (both exchange with the neighbouring
     slabs).  The forward pass gets the element rows of b next to the slab
     from the neighbours; the backward pass runs the slab adjoint step
-    (distributed.slab_adjoint) over states recomputed from checkpoints, and
+    (distributed.slab_adjoint) over states recomputed from checkpoints, with
+    recorded steps (distributed.slab_step_record) unless ``recorded`` is
+    false, and
     the gradient it returns is complete for the slab's own rows: the
     gradient of a neighbour's bathymetry at a shared face is formed by that
     neighbour."""
 
     @staticmethod
-    def forward(ctx, b, stepper, eta0, dt, nsteps, every):
+    def forward(ctx, b, stepper, eta0, dt, nsteps, every, recorded=True):
         from .distributed import halo_exchange
         bd = b.detach().contiguous()
         below, above = torch.empty_like(bd[-1:]), torch.empty_like(bd[:1])
@@ -126,28 +128,36 @@ class SlabBathymetryToState(torch.autograd.Function):
                 checkpoints.append(u.clone())
         ctx.stepper, ctx.dt, ctx.nsteps, ctx.every = stepper, dt, nsteps, every
         ctx.checkpoints, ctx.coef, ctx.b = checkpoints, coef, bd
+        ctx.recorded = recorded
         return u
 
     @staticmethod
     def backward(ctx, ubar):
-        from .distributed import slab_adjoint
+        from .distributed import slab_adjoint, slab_step_record
         st, dt, nsteps, every = ctx.stepper, ctx.dt, ctx.nsteps, ctx.every
         st.s.set_coefficients(ctx.coef)
         ubar = ubar.contiguous().clone()
         bbar = torch.zeros_like(ctx.b)
         other = torch.empty_like(ubar)
+        records = st.s.new_records(min(every, nsteps)) if ctx.recorded else None
         for seg, start in reversed(list(enumerate(range(0, nsteps, every)))):
             k = min(every, nsteps - start)
             states = [ctx.checkpoints[seg].clone()]
-            for _ in range(k - 1):
+            for j in range(k - 1):
                 x = states[-1].clone()
-                st.step(x, dt, 1)
+                if records is None:
+                    st.step(x, dt, 1)
+                else:
+                    slab_step_record(st, x, dt, records[j])
                 states.append(x)
-            for x in reversed(states):
-                slab_adjoint(st, x, ubar, dt, ubar0=other, bbar=bbar)
+            if records is not None:
+                slab_step_record(st, states[-1], dt, records[k - 1], advance=False)
+            for j in reversed(range(k)):
+                slab_adjoint(st, states[j], ubar, dt, ubar0=other, bbar=bbar,
+                             record=None if records is None else records[j])
                 ubar, other = other, ubar
         bbar -= ubar[0]
-        return bbar, None, None, None, None, None
+        return bbar, None, None, None, None, None, None
 
 
 def surface_misfit(u, b, target, weights):

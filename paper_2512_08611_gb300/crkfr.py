@@ -92,6 +92,12 @@ SIGNATURES = {
     "crkfr_record_size": (_I32, [_P, _PI64]),
     "crkfr_step_record": (_I32, [_P, _P, _D, _P, _I32, _P]),
     "crkfr_step_adjoint_recorded": (_I32, [_P, _P, _P, _P, _P, _P, _D, _P]),
+    "crkfr_step_local_record": (_I32, [_P, _P, _D, _P, _I32, _P]),
+    "crkfr_record_halo_buffers": (_I32, [_P, _P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                         ctypes.POINTER(_P), ctypes.POINTER(_P), _PI64]),
+    "crkfr_step_faces_record": (_I32, [_P, _P, _P, _P]),
+    "crkfr_adjoint_sums": (_I32, [_P, _P, _P]),
+    "crkfr_adjoint_faces_recorded": (_I32, [_P, _P, _P, _P, _P, _P, _D, _P]),
     "crkfr_get_time": (_I32, [_P, _PD, _PD, _P]),
     "crkfr_set_time": (_I32, [_P, _D, _P]),
     "crkfr_get_status": (_I32, [_P, _P]),
@@ -499,6 +505,49 @@ class Solver:
             self.h, self._dev(u, self.shape), self._dev(record, (self.record_size(),)),
             self._dev(ubar1, self.shape), self._dev(ubar0, self.shape),
             self._dev(bbar, self.coef_shape), float(dt), _stream()))
+        return ubar0, bbar
+
+    def step_local_record(self, u, dt, record, advance=True):
+        """2D slab: local phase of a recorded step (crkfr_step_local_record)."""
+        self._check(lib().crkfr_step_local_record(self.h, self._dev(u, self.shape), float(dt),
+                                                  self._dev(record, (self.record_size(),)),
+                                                  1 if advance else 0, _stream()))
+
+    def record_halo_buffers(self, record):
+        """2D slab: the boundary blocks of a record's y traces to exchange,
+        (send_bottom, send_top, recv_bottom, recv_top) viewing the record."""
+        import torch
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        cnt = ctypes.c_int64()
+        self._check(lib().crkfr_record_halo_buffers(
+            self.h, self._dev(record, (self.record_size(),)), *[ctypes.byref(p) for p in ptrs],
+            ctypes.byref(cnt)))
+        return tuple(torch.as_tensor(_DeviceBlock(p.value, cnt.value), device="cuda")
+                     for p in ptrs)
+
+    def step_faces_record(self, u, record):
+        """2D slab: face phase of a recorded step (crkfr_step_faces_record)."""
+        self._check(lib().crkfr_step_faces_record(self.h, self._dev(u, self.shape),
+                                                  self._dev(record, (self.record_size(),)),
+                                                  _stream()))
+
+    def adjoint_sums(self, ubar1):
+        """2D slab: the correction sums of ubar1 of a recorded adjoint step."""
+        self._check(lib().crkfr_adjoint_sums(self.h, self._dev(ubar1, self.shape), _stream()))
+
+    def adjoint_faces_recorded(self, u, record, ubar1, dt, ubar0=None, bbar=None):
+        """2D slab: the recorded adjoint step after the exchange of the sums.
+        Returns (ubar0, bbar)."""
+        import torch
+        if ubar0 is None:
+            ubar0 = torch.empty_like(ubar1)
+        bshape = (self.n_elem[1], self.n_elem[0], self.n, self.n)
+        if bbar is None:
+            bbar = torch.zeros(bshape, dtype=torch.float64, device=u.device)
+        self._check(lib().crkfr_adjoint_faces_recorded(
+            self.h, self._dev(u, self.shape), self._dev(record, (self.record_size(),)),
+            self._dev(ubar1, self.shape), self._dev(ubar0, self.shape), self._dev(bbar, bshape),
+            float(dt), _stream()))
         return ubar0, bbar
 
     def time(self):

@@ -1252,6 +1252,22 @@ void record_parts(const crkfr_ctx* c, int64_t* ntx, int64_t* nty, int64_t* nst) 
   *nst = (int64_t)(tab_stages(c->cfg.degree) - 1) * 3 * Ne * n * n;
 }
 
+// A 2D slab's buffers of the adjoint's y-correction sums (sent and received).
+crkfr_status ensure_adjoint_sums(crkfr_ctx* c) {
+  if (c->d_adj_send) return CRKFR_OK;
+  const int64_t sums = (int64_t)2 * 3 * c->Ex * c->basis.n;
+  if (cudaMalloc(&c->d_adj_send, sizeof(double) * sums) != cudaSuccess ||
+      cudaMalloc(&c->d_adj_recv, sizeof(double) * sums) != cudaSuccess) {
+    cudaFree(c->d_adj_send);
+    cudaFree(c->d_adj_recv);
+    c->d_adj_send = c->d_adj_recv = nullptr;
+    cudaGetLastError();
+    return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
+  }
+  CK(c, cudaMemset(c->d_adj_recv, 0, sizeof(double) * sums));
+  return CRKFR_OK;
+}
+
 // The adjoint kernels of one step whose forward traces of u^n are in
 // (trx, try_) and whose stage values are in `stages` (null: recomputed).
 crkfr_status launch_adjoint(crkfr_ctx* c, const double* u, const double* ubar1, double* ubar0,
@@ -1341,18 +1357,8 @@ crkfr_status crkfr_adjoint_local(crkfr_ctx* c, const double* u, const double* ub
   if (st != CRKFR_OK) return st;
   if (!u || !ubar1) return fail(c, CRKFR_ERR_ARG, "null argument");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
-  const int64_t sums = (int64_t)2 * 3 * c->Ex * c->basis.n;
-  if (!c->d_adj_send) {
-    if (cudaMalloc(&c->d_adj_send, sizeof(double) * sums) != cudaSuccess ||
-        cudaMalloc(&c->d_adj_recv, sizeof(double) * sums) != cudaSuccess) {
-      cudaFree(c->d_adj_send);
-      cudaFree(c->d_adj_recv);
-      c->d_adj_send = c->d_adj_recv = nullptr;
-      cudaGetLastError();
-      return fail(c, CRKFR_ERR_ALLOC, "device allocation failed");
-    }
-    CK(c, cudaMemset(c->d_adj_recv, 0, sizeof(double) * sums));
-  }
+  st = ensure_adjoint_sums(c);
+  if (st != CRKFR_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   // forward traces of u^n (the local kernel in its residual form) and the
   // sums the neighbouring slabs need
@@ -1392,6 +1398,117 @@ crkfr_status crkfr_adjoint_faces(crkfr_ctx* c, const double* u, const double* ub
   if (st != CRKFR_OK) return st;
   if (!c->d_adj_send) return fail(c, CRKFR_ERR_STATE, "crkfr_adjoint_local first");
   return launch_adjoint(c, u, ubar1, ubar0, bbar, dt, c->d_trx, c->d_try, nullptr,
+                        (cudaStream_t)stream);
+}
+
+// Recorded steps of a 2D slab: the local phase writes the face traces and
+// the inner stage values into the record, the record's halo rows of y traces
+// are exchanged, and the face phase reads the traces from the record.
+crkfr_status crkfr_step_local_record(crkfr_ctx* c, const double* u, double dt, double* record,
+                                     int32_t advance, void* stream) {
+  crkfr_status st = adjoint_context(c, true);
+  if (st != CRKFR_OK) return st;
+  if (!u || !record) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CRKFR_ERR_ARG, "dt must be positive");
+  if (advance != 0 && advance != 1) return fail(c, CRKFR_ERR_ARG, "advance must be 0 or 1");
+  int64_t tx, ty, ns;
+  record_parts(c, &tx, &ty, &ns);
+  const size_t rbytes = sizeof(double) * (size_t)(tx + ty + ns);
+  const size_t ubytes = sizeof(double) * c->n_state;
+  const char *a = (const char*)u, *r = (const char*)record;
+  if (a < r + rbytes && r < a + ubytes) return fail(c, CRKFR_ERR_ARG, "u and record overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  Launch2D L = make2d(c);
+  L.trx = record;
+  L.try_ = record + tx;
+  L.stages = record + tx + ty;
+  L.u_in = u;
+  L.u_out = nullptr;
+  StepCtl ctl{};
+  ctl.dt_fixed = dt;
+  ctl.cs_cfl = c->cfg.cfl_safety * c->cfl;
+  ctl.t_end = std::numeric_limits<double>::infinity();
+  if (!advance) {
+    ctl.residual = 1;   // traces and stages only, no time bookkeeping
+  } else {
+    ctl.slot_read = (int)(c->nstep % 3);
+    ctl.slot_write = (int)((c->nstep + 1) % 3);
+    ctl.slot_reset = (int)((c->nstep + 2) % 3);
+    ctl.tslot = (int)(c->nstep % 2);
+  }
+  L.ctl = ctl;
+  int e = timed(c, CRKFR_KERNEL_LOCAL_2D, s, [&] { return launch_local_2d_stages(L, s); });
+  if (e) return cuda_fail(c, e, "2D local kernel");
+  c->launches += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_record_halo_buffers(crkfr_ctx* c, double* record, double** send_bottom,
+                                       double** send_top, double** recv_bottom, double** recv_top,
+                                       int64_t* count) {
+  if (!c || !record) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (c->dim != 2 || !c->subdomain) return fail(c, CRKFR_ERR_STATE, "not a 2D slab");
+  int64_t tx, ty, ns;
+  record_parts(c, &tx, &ty, &ns);
+  const int64_t block = 7 * c->Ex * c->basis.n;   // as crkfr_halo_buffers, in the record
+  auto at = [&](int64_t row, int side) { return record + tx + (row * 2 + side) * block; };
+  if (send_bottom) *send_bottom = at(1, 0);
+  if (send_top) *send_top = at(c->Ey, 1);
+  if (recv_bottom) *recv_bottom = at(0, 1);
+  if (recv_top) *recv_top = at(c->Ey + 1, 0);
+  if (count) *count = block;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_step_faces_record(crkfr_ctx* c, double* u, const double* record,
+                                     void* stream) {
+  crkfr_status st = adjoint_context(c, true);
+  if (st != CRKFR_OK) return st;
+  if (!u || !record) return fail(c, CRKFR_ERR_ARG, "null argument");
+  int64_t tx, ty, ns;
+  record_parts(c, &tx, &ty, &ns);
+  cudaStream_t s = (cudaStream_t)stream;
+  StepCtl ctl{};
+  ctl.dt_fixed = 1.0;   // the face kernel reads the step size the local phase stored
+  ctl.slot_write = (int)((c->nstep + 1) % 3);
+  ctl.want_rate = 0;
+  Launch2D L = make2d(c);
+  L.trx = const_cast<double*>(record);
+  L.try_ = const_cast<double*>(record) + tx;
+  L.ctl = ctl;
+  L.u_in = u;
+  L.u_out = u;
+  int e = timed(c, CRKFR_KERNEL_FACE_2D, s, [&] { return launch_face_2d(L, s); });
+  if (e) return cuda_fail(c, e, "2D face kernel");
+  c->launches += 1;
+  c->nstep += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_adjoint_sums(crkfr_ctx* c, const double* ubar1, void* stream) {
+  crkfr_status st = adjoint_context(c, true);
+  if (st != CRKFR_OK) return st;
+  if (!ubar1) return fail(c, CRKFR_ERR_ARG, "null argument");
+  st = ensure_adjoint_sums(c);
+  if (st != CRKFR_OK) return st;
+  int e = launch_adjoint_sums_2d(c->cfg.degree, c->Ex, c->Ey, ubar1, c->tab, c->d_adj_send,
+                                 (cudaStream_t)stream);
+  if (e) return cuda_fail(c, e, "adjoint sums kernel");
+  c->launches += 1;
+  return CRKFR_OK;
+}
+
+crkfr_status crkfr_adjoint_faces_recorded(crkfr_ctx* c, const double* u, const double* record,
+                                          const double* ubar1, double* ubar0, double* bbar,
+                                          double dt, void* stream) {
+  crkfr_status st = adjoint_context(c, true);
+  if (st == CRKFR_OK) st = adjoint_args(c, u, ubar1, ubar0, bbar, dt);
+  if (st != CRKFR_OK) return st;
+  if (!record) return fail(c, CRKFR_ERR_ARG, "null argument");
+  if (!c->d_adj_send) return fail(c, CRKFR_ERR_STATE, "crkfr_adjoint_sums first");
+  int64_t tx, ty, ns;
+  record_parts(c, &tx, &ty, &ns);
+  return launch_adjoint(c, u, ubar1, ubar0, bbar, dt, record, record + tx, record + tx + ty,
                         (cudaStream_t)stream);
 }
 

@@ -119,19 +119,39 @@ class SlabStepper:
         return u
 
 
-def slab_adjoint(stepper, u, ubar1, dt, ubar0=None, bbar=None):
-    """Adjoint of one step of a 2D slab (crkfr_adjoint_local, the exchange
-    of the forward traces and of ubar1's correction sums, crkfr_adjoint_faces):
-    ubar0 of the slab's elements and their bathymetry gradient added to bbar.
-    ``stepper`` is the slab's SlabStepper (its trace buffers and group)."""
+def slab_step_record(stepper, u, dt, record, advance=True):
+    """One recorded step of a 2D slab (advance) or the record of its state
+    only: local phase into the record, exchange of the record's boundary
+    blocks of y traces, face phase from the record."""
     s = stepper.s
-    s.adjoint_local(u, ubar1, dt)
-    halo_exchange(stepper.send_bottom, stepper.send_top, stepper.recv_bottom, stepper.recv_top,
-                  stepper.group)
+    s.step_local_record(u, dt, record, advance)
+    halo_exchange(*s.record_halo_buffers(record), stepper.group)
+    if advance:
+        s.step_faces_record(u, record)
+    return u
+
+
+def slab_adjoint(stepper, u, ubar1, dt, ubar0=None, bbar=None, record=None):
+    """Adjoint of one step of a 2D slab: ubar0 of the slab's elements and
+    their bathymetry gradient added to bbar.  Without a record:
+    crkfr_adjoint_local, the exchange of the forward traces and of ubar1's
+    correction sums, crkfr_adjoint_faces; with the record of the step
+    (slab_step_record): the sums and their exchange, then
+    crkfr_adjoint_faces_recorded.  ``stepper`` is the slab's SlabStepper
+    (its trace buffers and group)."""
+    s = stepper.s
+    if record is None:
+        s.adjoint_local(u, ubar1, dt)
+        halo_exchange(stepper.send_bottom, stepper.send_top, stepper.recv_bottom,
+                      stepper.recv_top, stepper.group)
+    else:
+        s.adjoint_sums(ubar1)
     if getattr(stepper, "_adj", None) is None:
         stepper._adj = s.adjoint_halo_buffers()
     halo_exchange(*stepper._adj, stepper.group)
-    return s.adjoint_faces(u, ubar1, dt, ubar0, bbar)
+    if record is None:
+        return s.adjoint_faces(u, ubar1, dt, ubar0, bbar)
+    return s.adjoint_faces_recorded(u, record, ubar1, dt, ubar0, bbar)
 
 
 def slab_rows(global_rows, rank, world):

@@ -318,10 +318,12 @@ def test_slab_adjoint_through_the_distributed_helper_and_errors():
     assert np.array_equal(to_host(bb), to_host(bb_want))
 
 
-def test_slab_autograd_function_equals_whole_mesh():
+@pytest.mark.parametrize("recorded", [True, False])
+def test_slab_autograd_function_equals_whole_mesh(recorded):
     """SlabBathymetryToState on a slab that is its own periodic neighbour
     (one rank) gives the final state and the bathymetry gradient of a surface
-    misfit of BathymetryToState on the whole mesh, bit for bit."""
+    misfit of BathymetryToState on the whole mesh, bit for bit, with
+    recorded and with recomputing adjoint steps."""
     from paper_2512_08611_gb300.adjoint import (BathymetryToState, SlabBathymetryToState,
                                                 quadrature_weights, surface_misfit)
     from paper_2512_08611_gb300.distributed import SlabStepper
@@ -339,8 +341,53 @@ def test_slab_autograd_function_equals_whole_mesh():
     surface_misfit(u1, b1, target, W).backward()
     s = adjoint_slab(crk, N, Ex, Ey, b, 0, Ey)
     b2 = to_dev(b).requires_grad_(True)
-    u2 = SlabBathymetryToState.apply(b2, SlabStepper(s), eta0, dt, nsteps, every)
+    u2 = SlabBathymetryToState.apply(b2, SlabStepper(s), eta0, dt, nsteps, every, recorded)
     surface_misfit(u2, b2, target, W).backward()
     assert torch.equal(u1.detach(), u2.detach())
     assert torch.equal(b1.grad, b2.grad)
     assert float(b1.grad.abs().max()) > 0.0
+
+
+def ring_exchange(bufs):
+    k_ = len(bufs)
+    for k in range(k_):
+        bufs[k][2].copy_(bufs[(k - 1) % k_][1])   # recv_bottom <- send_top of the slab below
+        bufs[k][3].copy_(bufs[(k + 1) % k_][0])   # recv_top <- send_bottom of the slab above
+
+
+def test_slab_recorded_step_and_adjoint():
+    """Recorded slab steps (crkfr_step_local_record, exchange of the
+    record's y-trace blocks, crkfr_step_faces_record) and the recorded slab
+    adjoint (crkfr_adjoint_sums, exchange, crkfr_adjoint_faces_recorded),
+    with a one-row slab: the step and the adjoint of the whole mesh, bit for
+    bit."""
+    crk = load()
+    N, Ex, Ey = 3, 16, 16
+    u, b, dx, dy = case(N, Ex, Ey)
+    w = np.random.default_rng(9).standard_normal(u.shape)
+    m = solver(crk, N, Ex, Ey, b)
+    dt = 0.5 * m.compute_dt(to_dev(u))
+    step_want = to_dev(u)
+    m.step(step_want, dt, 1)
+    ub_want, bb_want = m.step_adjoint(to_dev(u), to_dev(w), dt)
+    parts = [(0, 5), (5, 1), (6, 10)]
+    slabs = [adjoint_slab(crk, N, Ex, Ey, b, f, c) for f, c in parts]
+    us = [to_dev(np.ascontiguousarray(u[:, f:f + c])) for f, c in parts]
+    ws = [to_dev(np.ascontiguousarray(w[:, f:f + c])) for f, c in parts]
+    recs = [s.new_records(1)[0] for s in slabs]
+    xs = [x.clone() for x in us]
+    for s, x, r in zip(slabs, xs, recs):
+        s.step_local_record(x, dt, r)
+    ring_exchange([s.record_halo_buffers(r) for s, r in zip(slabs, recs)])
+    for s, x, r in zip(slabs, xs, recs):
+        s.step_faces_record(x, r)
+    got = np.concatenate([to_host(x) for x in xs], axis=1)
+    assert np.array_equal(got, to_host(step_want))
+    for s, y in zip(slabs, ws):
+        s.adjoint_sums(y)
+    ring_exchange([s.adjoint_halo_buffers() for s in slabs])
+    outs = [s.adjoint_faces_recorded(x, r, y, dt) for s, x, r, y in zip(slabs, us, recs, ws)]
+    ub = np.concatenate([to_host(o[0]) for o in outs], axis=1)
+    bb = np.concatenate([to_host(o[1]) for o in outs], axis=0)
+    assert np.array_equal(ub, to_host(ub_want)), rel_l2(ub, to_host(ub_want))
+    assert np.array_equal(bb, to_host(bb_want)), rel_l2(bb, to_host(bb_want))
