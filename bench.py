@@ -718,17 +718,26 @@ def run_ensemble(args):
         "gpu_launches": launches, "clocks": clk}))
 
 
-def measure_adjoint(crkfr, E=256, N=3, L=100.0, nsteps=200, every=20):
+def measure_adjoint(crkfr, E=256, N=3, L=100.0, nsteps=200, every=20, split=False):
     """Gradient of the final surface misfit w.r.t. the bathymetry on the 2D
     E x E, N = 3 mesh: nsteps fixed steps, checkpoints every `every` steps,
     the backward pass recomputing each segment with recorded steps.  Returns
-    the forward and backward times (CUDA events) and the per-step costs."""
+    the forward and backward times (CUDA events) and the per-step costs.
+    split: the slab path of the multi-GPU runs (one slab, its own periodic
+    neighbour: SlabBathymetryToState over a SlabStepper)."""
     import torch
-    from paper_2512_08611_gb300.adjoint import (BathymetryToState, quadrature_weights,
-                                                surface_misfit)
+    from paper_2512_08611_gb300.adjoint import (BathymetryToState, SlabBathymetryToState,
+                                                quadrature_weights, surface_misfit)
+    from paper_2512_08611_gb300.distributed import SlabStepper
     from paper_2512_08611_gb300.workloads import SWE2DInput, accept_seed
     s = crkfr.Solver("swe2d", N, gravity=G, cfl_safety=0.5)
     s.set_mesh([E, E], [0.0, 0.0], [L, L])
+    if split:
+        s.set_subdomain(True)
+        stepper = SlabStepper(s)
+        apply = lambda bb: SlabBathymetryToState.apply(bb, stepper, eta0, dt, nsteps, every)
+    else:
+        apply = lambda bb: BathymetryToState.apply(bb, s, eta0, dt, nsteps, every)
     x, y = s.positions()
     inp, _ = accept_seed(lambda k: SWE2DInput(seed=k, L=L), (x, y), 0)
     _, b = inp.state(x, y)
@@ -736,20 +745,20 @@ def measure_adjoint(crkfr, E=256, N=3, L=100.0, nsteps=200, every=20):
     _, b2 = inp2.state(x, y)
     eta0 = torch.tensor(inp.eta(x, y), device="cuda")
     bt, b2t = torch.tensor(b, device="cuda"), torch.tensor(b2, device="cuda")
-    s.set_coefficients(b2t)
+    s.set_coefficients(torch.cat([b2t[-1:], b2t, b2t[:1]]).contiguous() if split else b2t)
     dt = 0.5 * s.compute_dt(torch.stack([eta0 - b2t, 0 * b2t, 0 * b2t]).contiguous())
     W = quadrature_weights(s)
     with torch.no_grad():
-        target = BathymetryToState.apply(b2t, s, eta0, dt, nsteps, every)[0] + b2t
+        target = apply(b2t)[0] + b2t
     # warm-up of both directions
     bb = bt.clone().requires_grad_(True)
-    surface_misfit(BathymetryToState.apply(bb, s, eta0, dt, nsteps, every), bb, target, W).backward()
+    surface_misfit(apply(bb), bb, target, W).backward()
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     bb = bt.clone().requires_grad_(True)
     s.profile(True)
     ev[0].record()
-    J = surface_misfit(BathymetryToState.apply(bb, s, eta0, dt, nsteps, every), bb, target, W)
+    J = surface_misfit(apply(bb), bb, target, W)
     ev[1].record()
     J.backward()
     ev[2].record()
@@ -758,7 +767,8 @@ def measure_adjoint(crkfr, E=256, N=3, L=100.0, nsteps=200, every=20):
     s.profile(False)
     fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     n_adj, ms_adj = prof.get("adjoint_2d", (0, 0.0))
-    return {"workload": f"adjoint-swe2d-{E}x{E}-N{N}-{nsteps}steps-ckpt{every}",
+    return {"workload": f"adjoint-swe2d-{E}x{E}-N{N}-{nsteps}steps-ckpt{every}"
+                        + ("-slab" if split else ""),
             "loss": "1/2 sum w (h + b - target)^2 at T", "dt": dt,
             "forward_ms": fwd, "backward_ms": bwd,
             "backward_over_forward": bwd / fwd,
@@ -780,7 +790,7 @@ def run_adjoint(args):
     from paper_2512_08611_gb300 import crkfr
     torch.cuda.set_device(0)
     nsteps = 200
-    a = measure_adjoint(crkfr, nsteps=nsteps)
+    a = measure_adjoint(crkfr, nsteps=nsteps, split=args.split)
     print(json.dumps({
         "metric": METRIC, "value": a["dof"] * nsteps / (a["backward_ms"] / 1e3),
         "unit": "DoF-updates/s (adjoint)",
