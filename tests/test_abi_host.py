@@ -88,6 +88,30 @@ def test_scheme_switches_accept_only_the_built_readings(crk):
     assert "nc_face_mode" in crk.lib().crkfr_last_error(None).decode()
 
 
+def test_split_entry_points_refuse_contexts_they_do_not_serve(crk):
+    """The limiter's and the adjoint's slab entry points and the record's
+    halo blocks answer CRKFR_ERR_ARG for null arguments and
+    CRKFR_ERR_STATE on a context that is not a 2D slab (no mesh here),
+    before any GPU work."""
+    from paper_2512_08611_gb300.crkfr import Solver
+    s = Solver("swe2d", 2)
+    L = crk.lib()
+    ptrs = [ctypes.c_void_p() for _ in range(4)]
+    refs = [ctypes.byref(x) for x in ptrs]
+    cnt = ctypes.c_int64()
+    fake = ctypes.c_void_p(16)
+    assert L.crkfr_limiter_halo_buffers(None, 0, *refs, ctypes.byref(cnt)) == -1
+    assert L.crkfr_limiter_halo_buffers(s.h, 0, *refs, ctypes.byref(cnt)) == -6
+    assert L.crkfr_adjoint_halo_buffers(s.h, *refs, ctypes.byref(cnt)) == -6
+    assert L.crkfr_record_halo_buffers(s.h, None, *refs, ctypes.byref(cnt)) == -1
+    assert L.crkfr_record_halo_buffers(s.h, fake, *refs, ctypes.byref(cnt)) == -6
+    assert L.crkfr_step_indicator(s.h, fake, None) == -6
+    assert L.crkfr_adjoint_sums(s.h, fake, None) == -6
+    assert L.crkfr_adjoint_local(s.h, fake, fake, 0.1, None) == -6
+    assert L.crkfr_step_local_record(s.h, fake, 0.1, fake, 1, None) == -6
+    assert all(p.value is None for p in ptrs)
+
+
 def test_tile_size_setting(crk):
     """crkfr_set_tile_1d takes 0 (per mesh), 64, 96 or 128 threads on a 1D
     context; other values are argument errors, a 2D context refuses it."""
