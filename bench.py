@@ -179,6 +179,25 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def host_link_gbs(host, dev):
+    """Copy bandwidth of this process's pinned host buffer to and from the
+    device (after the end-to-end timing; torch copies of the whole state,
+    best of three): the link bounds the end-to-end step, and the rate a
+    process gets varies between processes on this pool's virtual machines."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    best = {"h2d": 0.0, "d2h": 0.0}
+    for _ in range(3):
+        for key, (dst, src) in (("h2d", (dev, host)), ("d2h", (host, dev))):
+            torch.cuda.synchronize()
+            ev[0].record()
+            dst.copy_(src, non_blocking=True)
+            ev[1].record()
+            torch.cuda.synchronize()
+            best[key] = max(best[key], host.numel() * 8 / (ev[0].elapsed_time(ev[1]) * 1e6))
+    return best
+
+
 def l2_note(wl):
     """How the timed steps stand to the 129 MB L2 (no flush between steps):
     the state, its copy and, in 2D, the face traces and work buffers."""
@@ -471,7 +490,8 @@ def run_ours(args, wl):
             s.step_host(h, h, dt=0.0, nsteps=1)
         e2e_s = time.perf_counter() - t0
         e2e = {"value": wl.dof * e2e_steps / e2e_s, "unit": "DoF-updates/s",
-               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+               "host_link_gbs": host_link_gbs(host, u)}
 
     # roofline of the dominant kernel
     peaks = load_peaks()

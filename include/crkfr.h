@@ -221,8 +221,8 @@ crkfr_status crkfr_advance(crkfr_ctx* ctx, double* u_dev, double t_end, int64_t 
 /* The step of crkfr_step (Sec. 3, Eq. crkfr.non.cons.final) on host memory;
  * the host transfers have no counterpart in the paper.  Copies u_in_host to a context-owned
  * device state, steps, and copies the result to u_out_host (the two may be
- * the same buffer).  In 2D the last step's kernels run in up to 8 parts of
- * element rows, and each part's rows are copied back on a context-owned
+ * the same buffer).  In 2D the last step's kernels run in up to 5 parts of
+ * element rows, of decreasing size, and each part's rows are copied back on a context-owned
  * stream while the later parts compute (u_out_host should be pinned for the
  * copies to overlap).  Synchronises the stream. */
 crkfr_status crkfr_step_host(crkfr_ctx* ctx, const double* u_in_host, double* u_out_host,

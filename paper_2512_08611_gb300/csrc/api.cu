@@ -334,8 +334,8 @@ crkfr_status launch_rate(crkfr_ctx* c, const double* u, int slot, cudaStream_t s
   return CRKFR_OK;
 }
 
-// The local and face kernels of a 2D step in up to kHostChunks parts of
-// element rows, each part's rows of u (contiguous per variable) copied to
+// The local and face kernels of a 2D step in up to 5 parts of element rows,
+// each part's rows of u (contiguous per variable) copied to
 // host_out on the copy stream as soon as its face kernel has finished, while
 // the later parts compute; the stream s then waits for the last copy.  The
 // face kernel of part k needs the local kernel of the rows next to it, so the
@@ -359,11 +359,19 @@ crkfr_status step_with_readback(crkfr_ctx* c, Launch2D L, const double* u, doubl
   if (sc != CRKFR_OK) return sc;
   const int64_t Ey = c->Ey, Ne = c->Ex * c->Ey;
   const int64_t nn = (int64_t)c->basis.n * c->basis.n;
-  int64_t rows = (Ey + kHostChunks - 1) / kHostChunks;
-  rows = (rows + 7) / 8 * 8;
-  const int parts = (int)((Ey + rows - 1) / rows);
-  auto r_begin = [&](int k) { return (int64_t)k * rows; };
-  auto r_end = [&](int k) { return (int64_t)(k + 1) * rows < Ey ? (int64_t)(k + 1) * rows : Ey; };
+  // parts of decreasing size, 6:4:3:2:1 of the rows in multiples of 8 rows:
+  // each part's read-back overlaps the compute of the later ones, and only
+  // the last, smallest part's read-back ends the step (fewer launches than
+  // equal parts with as short a tail)
+  static constexpr int kCum[5] = {6, 10, 13, 15, 16};
+  int64_t ends[5];
+  int parts = 0;
+  for (int i = 0; i < 5; ++i) {
+    const int64_t e = i == 4 ? Ey : (Ey * kCum[i] / 16) / 8 * 8;
+    if (e > (parts ? ends[parts - 1] : 0)) ends[parts++] = e;
+  }
+  auto r_begin = [&](int k) { return k == 0 ? (int64_t)0 : ends[k - 1]; };
+  auto r_end = [&](int k) { return ends[k]; };
   bool first = true;
   auto local_part = [&](int k) -> crkfr_status {
     Launch2D P = L;
