@@ -381,7 +381,9 @@ crkfr_status crkfr_adjoint_faces_recorded(crkfr_ctx* ctx, const double* u_dev,
  * can keep, for each step, what the adjoint step would otherwise recompute:
  * the face traces of u^n (the Riemann problems' inputs, Eqs. numflux.cons,
  * good.numflux.non.cons) and the inner stage values 1..S-1 of Eq.
- * crkfr.non.cons.final.  Same contexts as crkfr_step_adjoint.
+ * crkfr.non.cons.final.  Same contexts as crkfr_step_adjoint (2D slabs:
+ * crkfr_step_local_record and its siblings, below; crkfr_record_size serves
+ * both).
  *
  * crkfr_record_size: *count = doubles of one step record (x- and y-face
  * traces and stage values: 14 n (2 Ex Ey + 2 Ex) + 3 (S-1) Ex Ey n^2 with
