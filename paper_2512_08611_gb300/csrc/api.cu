@@ -1481,6 +1481,7 @@ crkfr_status crkfr_step_faces_record(crkfr_ctx* c, double* u, const double* reco
   ctl.slot_write = (int)((c->nstep + 1) % 3);
   ctl.want_rate = 0;
   Launch2D L = make2d(c);
+  // (the face kernel only reads the traces)
   L.trx = const_cast<double*>(record);
   L.try_ = const_cast<double*>(record) + tx;
   L.ctl = ctl;
