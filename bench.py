@@ -184,7 +184,7 @@ def host_link_gbs(host, dev):
     device (after the end-to-end timing; torch copies of the whole state,
     best of three, overwriting the device state, which nothing reads
     afterwards): the link bounds the end-to-end step, and the rate a process
-    gets varies between processes on this pool's virtual machines."""
+    gets can vary between processes on the same machine."""
     import torch
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     best = {"h2d": 0.0, "d2h": 0.0}
